@@ -1,0 +1,358 @@
+"""Benchmark of the momentum-loop RHS engine on one GB300 (or N replicas).
+
+Workload (one "step"): one full right-hand side of the d=4 vertex-expansion
+model -- 3 dressing tables on 128-point log grids, 1281 external points
+(128 |p| for the propagator flow + p = 0, 128 |p| x 8 angles for the
+three-point flow, 128 |p| for the four-point flow) x 131072 quadrature nodes
+(128 radial x 64 Gauss-Chebyshev-II x 16 Gauss-Legendre) = 1.68e8 integrand
+evaluations, in the mixed-precision path.  Inputs stay resident; L2 is
+flushed between timed steps.  Extra keys: the plain FP64 path on the same
+workload, the end-to-end call with host buffers, full RG flows (d=3 two-point
+flow k: 10 -> 0.01, FP64 vs mixed, endpoint error), the roofline of the
+dominant kernel, clocks, and the CPU oracle on the host cores.
+
+Multi-GPU: replicas only (every rank evaluates its own RHS; no collective on
+the data path); value = all ranks' evaluations / max-over-ranks time.
+`--impl reference` times the CPU oracle on the same workload (a bounded
+sample of external points per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "integrand evals/s & flows/s vs plain FP64 GPU at 1e-8 endpoint err; p50/p99 latency"
+WORKLOAD = "d4 vertex-expansion RHS: 3 tables x 128 pts, 1281 ext x (128 rad x 64 GC-II x 16 GL) nodes"
+
+# Special-function evaluations per integrand term of the mixed d=4 kernel
+# (from the integrand's formula, not from the compiled code): inner term of the
+# three-point diagram: 3 table coordinates (log) + 1 regulator exp + 2
+# reciprocals (regulator shape, propagator); per (radial, c1) row: 2 logs +
+# 1 exp + 2 reciprocals for the |q+p1| leg (all three diagram classes).
+SFU_INNER = 6
+SFU_ROW = 5
+SFU_PER_CLK_SM = 16      # MUFU results per clock per SM
+FP32_PER_CLK_SM = 128    # FP32 FMA lanes per SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ffrg", choices=["ffrg", "reference"])
+    ap.add_argument("--no-flows", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def sfu_ops_per_launch(pb):
+    """Algorithmic special-function evaluations of one d=4 RHS launch."""
+    n_p, n_psi = pb.n_ext_p, pb.n_ext_ang
+    rows = pb.n_rad * pb.n_ang1
+    inner = n_p * n_psi * rows * pb.n_ang2               # three-point diagram terms
+    row_ops = (2 * n_p + 1 + n_p * n_psi) * rows * SFU_ROW
+    extra_rows = (n_p + 1) * rows * 2                    # two vertex lookups per row (Z and lambda4 blocks)
+    return inner * SFU_INNER + row_ops + extra_rows
+
+
+class ClockSampler:
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        busy = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except ValueError:
+            return {}
+    return {}
+
+
+def cpu_baseline(wl, stride: int):
+    """The CPU oracle, as it stands, on every `stride`-th external point."""
+    import oracle
+    pb = wl.problem
+    sel = list(range(0, pb.n_ext(), stride))
+    t = time.perf_counter()
+    oracle.rhs_subset(pb, wl.tables, 1.0, sel)
+    dt = time.perf_counter() - t
+    ev = len(sel) * pb.n_nodes()
+    return {"value": ev / dt, "unit": "integrand evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(sel)} of {pb.n_ext()} external points (every {stride}th) of the d4 RHS at k=1, "
+                      f"{ev:.3g} evals, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import ffrg_inputs as fi
+    import oracle
+    wl = fi.make_d4(seed=2)
+    pb = wl.problem
+    stride = 16
+    sel = list(range(0, pb.n_ext(), stride))
+    for _ in range(args.warmup):
+        oracle.rhs_subset(pb, wl.tables, 1.0, sel[:8])
+    times = []
+    for s in range(args.steps):
+        sub = [e for e in range((s % stride), pb.n_ext(), stride)]
+        t = time.perf_counter()
+        oracle.rhs_subset(pb, wl.tables, 1.0, sub)
+        times.append((time.perf_counter() - t, len(sub) * pb.n_nodes()))
+    tot_t = sum(t for t, _ in times)
+    tot_ev = sum(e for _, e in times)
+    val = tot_ev / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "integrand evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (CPU oracle, 1/16 of the external points per step)",
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": val, "unit": "integrand evals/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"each step: every 16th external point, offset by step"},
+            "e2e": {"value": val, "unit": "integrand evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    import ffrg_inputs as fi
+    import paper_2412_13043_gb300 as ffrg
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = ffrg.Context(local)
+    wl = fi.make_d4(seed=2 + rank)
+    pb = wl.problem
+    evals = float(pb.evals())
+    tabs = ctx.tables(pb, wl.tables)
+    out = torch.empty(pb.n_ext(), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(prec, k=1.0):
+        ctx.rhs(pb, tabs, k, out=out, precision=prec)
+
+    # warm-up (also builds the launch plan)
+    for _ in range(max(3, args.warmup)):
+        step(ffrg.MIXED)
+        step(ffrg.FP64)
+    torch.cuda.synchronize()
+    assert ctx.status_read() == ffrg.OK
+
+    # ---------------- main timed region: mixed-precision RHS ----------------
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(local)
+    ctx.set_profiling(True)
+    barrier()
+    sampler.start()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()
+        starts[i].record(stream)
+        step(ffrg.MIXED)
+        stops[i].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    main_ms, launches = ctx.profile_read()
+    ctx.set_profiling(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
+    t_tot = sum(step_ms) / 1e3
+    t_max = t_tot
+    if dist is not None:
+        tt = torch.tensor([t_tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * evals * K / t_max
+    assert ctx.status_read() == ffrg.OK
+
+    # ---------------- FP64 path on the same workload ----------------
+    K64 = max(2, K // 5)
+    s64 = [torch.cuda.Event(enable_timing=True) for _ in range(K64)]
+    e64 = [torch.cuda.Event(enable_timing=True) for _ in range(K64)]
+    barrier()
+    for i in range(K64):
+        flush.zero_()
+        s64[i].record(stream)
+        step(ffrg.FP64)
+        e64[i].record(stream)
+    barrier()
+    fp64_ms = sum(s.elapsed_time(e) for s, e in zip(s64, e64)) / K64
+    ref64 = out.cpu().numpy().copy()
+    step(ffrg.MIXED)
+    mixed_out = out.cpu().numpy()
+    mixed_err = float(np.max(np.abs(mixed_out - ref64) / np.abs(ref64)))
+
+    # ---------------- end to end: public API with host buffers ----------------
+    host_tab = torch.tensor(wl.tables, dtype=torch.float64).pin_memory()
+    host_out = torch.empty(pb.n_ext(), dtype=torch.float64).pin_memory()
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ee = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier()
+    for i in range(K):
+        flush.zero_()
+        es[i].record(stream)
+        tabs.update(host_tab)            # pinned host -> device, stream-ordered
+        step(ffrg.MIXED)
+        host_out.copy_(out, non_blocking=True)
+        ee[i].record(stream)
+    barrier()
+    e2e_t = sum(s.elapsed_time(e) for s, e in zip(es, ee)) / 1e3
+    e2e_val = world * evals * K / e2e_t
+
+    # ---------------- roofline of the dominant kernel ----------------
+    peaks = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sfu_peak = SFU_PER_CLK_SM * n_sm * sm_mhz * 1e6
+    kern_s = (main_ms / 1e3) / max(1, launches)
+    sfu_ops = sfu_ops_per_launch(pb)
+    achieved = sfu_ops / kern_s
+    roofline = {"bound": "alu", "pipe": "MUFU (special-function unit)", "achieved": achieved / 1e12,
+                "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": achieved / sfu_peak, "traffic": None,
+                "peak_source": f"{SFU_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock of measured)",
+                "kernel": "d4_main<float>", "kernel_ms": kern_s * 1e3, "ops_per_launch": sfu_ops,
+                "kernel_share_of_step": (main_ms / max(1, launches)) / (sum(step_ms) / K)}
+
+    # ---------------- full flows (d=3 two-point flow k: 10 -> 0.01) ----------------
+    flows = None
+    if not args.no_flows:
+        wf = fi.make_d3(seed=1)
+        tf = ctx.tables(wf.problem, wf.tables)
+        t1 = math.log(wf.Lambda / wf.k_end)
+
+        def run_flow(prec, rtol, atol):
+            y = torch.tensor(wf.y0, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            st = ctx.flow(wf.problem, tf, y, wf.Lambda, t1, precision=prec, rtol=rtol, atol=atol)
+            torch.cuda.synchronize()
+            return y.cpu().numpy(), time.perf_counter() - t, st
+        truth, _, _ = run_flow(ffrg.FP64, 1e-13, 1e-16)
+        res = {}
+        for name, prec in (("fp64", ffrg.FP64), ("mixed", ffrg.MIXED)):
+            y, dt, st = run_flow(prec, 1e-10, 1e-13)
+            res[name] = {"flows_per_s": 1.0 / dt, "s_per_flow": dt, "steps": st["steps"],
+                         "rhs_evals": st["rhs_evals"],
+                         "endpoint_rel_err": float(np.max(np.abs(y - truth) / np.abs(truth)))}
+        flows = {"workload": "d3 two-point flow, 64 ext x (64 x 32) nodes, k: 10 -> 0.01, rtol 1e-10",
+                 **res}
+        tf.free()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl, stride=4)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "integrand evals/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": sum(step_ms) / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 integrand + f64 accumulation", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "evals_per_step": evals, "precision": "mixed",
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
+            "wall_s_timed_region": wall,
+            "fp64_path": {"value": evals / (fp64_ms / 1e3), "unit": "integrand evals/s", "ms_per_step": fp64_ms,
+                          "speedup_mixed_over_fp64": (value / world) / (evals / (fp64_ms / 1e3))},
+            "mixed_vs_fp64_max_rel_err": mixed_err,
+            "e2e": {"value": e2e_val, "unit": "integrand evals/s",
+                    "h2d_bytes_per_step": int(wl.tables.size * 8), "d2h_bytes_per_step": int(pb.n_ext() * 8)},
+            "gpu_launches": 3 * K,
+            "roofline": roofline,
+            "clocks": clocks,
+            "flows": flows,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    tabs.free()
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

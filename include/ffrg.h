@@ -1,0 +1,227 @@
+/*
+ * ffrg.h -- C ABI of the GB300 (sm_103a) library that evaluates the loop-
+ * momentum integrals on the right-hand side of functional-RG vertex-expansion
+ * flows and integrates those flows in RG time (DiFfRG, arXiv:2412.13043).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - a per-flow integrator "get(k, args...)" that returns the momentum
+ *     integral for a scale k (App. G, model code calling the integrators);
+ *   - the variable assembler's residual dt_variables(residual, data), i.e.
+ *     d_t v + R(v, t) = 0 with R = Flow (Sec. 5.2.2, Eqs. assVar, flowVar);
+ *   - a stepper run(&ic, t0, t1) with dt / minimal_dt / maximal_dt / abs_tol /
+ *     rel_tol semantics (Sec. 5.2.1 and App. C, "timestepping" parameters);
+ *   - kernel descriptors with Type / Angles / d / ctype (Sec. 5.3.2, App. F).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an ffrg_status; nothing throws across the ABI.
+ *   - Pointers marked "device" must be device memory of the context's GPU;
+ *     "host" pointers are ordinary host memory.  Caller-owned buffers are
+ *     never retained after a call returns (serving copies its inputs).
+ *   - Device work is ordered on the CUDA stream passed as `stream`
+ *     (a cudaStream_t cast to void*, NULL = legacy default stream).  Calls
+ *     that launch work return before it finishes; errors raised on the device
+ *     (non-finite results, bounded-wait timeouts) accumulate in a per-context
+ *     status word read by ffrg_status_read().
+ *   - A context's scratch memory is shared by its calls: issue the calls of
+ *     one context on one stream (or serialise them); use one context per
+ *     concurrent stream.
+ *   - RG time: ffrg_rhs returns k d_k of the target quantity (the literature
+ *     convention t_- = ln(k/Lambda)); ffrg_flow integrates in
+ *     t = t_+ = ln(Lambda/k), so d_t y = -Flow (Sec. 2.1, t_+ convention).
+ *
+ * Synthetic models (the paper's Yang-Mills and four-Fermi systems need input
+ * data that is not published with it; these models keep the same structure
+ * "regulator derivative x propagators x vertices from interpolated dressing
+ * tables", Eq. GenfRG, Eq. FlowGamman, App. G):
+ *   FFRG_MODEL_D3        d=3, T=0:  I(p) = pref lam^2 int d^3q/(2pi)^3
+ *                                         dR(q) G(q)^2 G(|q+p|)
+ *   FFRG_MODEL_D4_VERTEX d=4, T=0, tables Z, lambda3, lambda4 (Sec. 3.3
+ *                        average-momentum vertices): propagator, three- and
+ *                        four-point diagrams
+ *   FFRG_MODEL_FINITE_T  d=3 + bosonic Matsubara sum |n| <= N (Sec. 5.3.2
+ *                        "Quadratureq0"), tables stacked over |n|
+ * with R = Z(q) k^2 r(q^2/k^2), r(x) = x/(e^x-1) (exponential) or
+ * (1-x)Theta(1-x) (flat), dR = k d_k R at fixed Z, and
+ * G = 1/(Z (omega^2 + q^2) + m^2 + R), m^2 = m2_over_k2 k^2 + m2_shift.
+ */
+#ifndef FFRG_H
+#define FFRG_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define FFRG_API __attribute__((visibility("default")))
+#else
+#define FFRG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffrg_ctx ffrg_ctx;       /* library-owned; one per device and stream */
+typedef struct ffrg_tables ffrg_tables; /* library-owned device dressing tables */
+
+typedef enum {
+  FFRG_OK = 0,
+  FFRG_EINVAL = 1,          /* bad argument, shape or pointer */
+  FFRG_ENOMEM = 2,          /* allocation failed or the context's HBM budget is exceeded */
+  FFRG_ENONFINITE = 3,      /* a result or flow state became NaN/Inf */
+  FFRG_ESTEP_UNDERFLOW = 4, /* step rejected at minimal_dt (App. C: evolution aborted) */
+  FFRG_EMAXSTEPS = 5,       /* step budget exhausted before t1 */
+  FFRG_ETIMEOUT = 6,        /* a bounded device wait gave up */
+  FFRG_EPENDING = 7,        /* serving: request not finished yet */
+  FFRG_EBUSY = 8,           /* serving: queue full */
+  FFRG_ECUDA = 9,           /* a CUDA runtime call failed (see ffrg_last_error) */
+  FFRG_ENOTFOUND = 10       /* serving: unknown ticket */
+} ffrg_status;
+
+typedef enum { FFRG_FP64 = 0, FFRG_MIXED = 1 } ffrg_precision;
+typedef enum { FFRG_RULE_GL = 0, FFRG_RULE_GC2 = 1 } ffrg_rule;
+typedef enum { FFRG_MODEL_D3 = 1, FFRG_MODEL_D4_VERTEX = 2, FFRG_MODEL_FINITE_T = 3 } ffrg_model;
+typedef enum { FFRG_REG_EXP = 0, FFRG_REG_LITIM = 1 } ffrg_regulator;
+
+/* One right-hand-side problem (kernel descriptor: Type/Angles/d of App. F).
+ * Quadrature: radial Gauss-Legendre with n_rad nodes on [0, qmax_over_k k];
+ * D3/FINITE_T: n_ang1 GL nodes in cos(theta); D4: n_ang1 Gauss-Chebyshev-II
+ * nodes in cos1 (weight sqrt(1-c1^2)) x n_ang2 GL nodes in cos2 (App. F angle
+ * names).  External momenta p_i = p_min (p_max/p_min)^(i/(n_ext_p-1)).
+ * External-point layout of the output (row-major):
+ *   D3:       [p_0 .. p_{n_ext_p-1}] then, if include_p0, the point p = 0
+ *   D4:       [Z: p_0..p_{n-1}, p=0][lambda3: p_i x psi_j][lambda4: p_i],
+ *             psi_j = n_ext_ang GL nodes in cos(psi) between the two legs
+ *   FINITE_T: [p_i][m], m = 0..n_ext_ang-1 external bosonic frequencies
+ *             p0_m = 2 pi T m; Matsubara sum over |n| <= n_matsubara. */
+typedef struct {
+  int model;        /* ffrg_model */
+  int regulator;    /* ffrg_regulator */
+  int n_rad, n_ang1, n_ang2;
+  int n_ext_p, n_ext_ang, n_matsubara, include_p0;
+  int reserved0;
+  double m2_over_k2, m2_shift; /* m^2 = m2_over_k2 k^2 + m2_shift */
+  double lam;                  /* coupling: lam^2 multiplies D3 and FINITE_T */
+  double T;                    /* temperature (FINITE_T) */
+  double p_min, p_max;         /* external log grid */
+  double qmax_over_k;          /* radial domain [0, qmax_over_k k] */
+  double prefactor;            /* overall multiplier */
+} ffrg_problem;
+
+/* Dressing tables values[table][stack][pt] (doubles, row-major) on the log grid
+ * x_j = x_min (x_max/x_min)^(j/(n_pts-1)) (App. F LogarithmicCoordinates1D);
+ * stack = |n| for FINITE_T (App. F BosonicCoordinates1DFiniteT), clamped to
+ * n_stack-1; lookups are linear in the value between nodes in ln s and clamp
+ * at both ends.  D3 needs 1 table (Z), D4 3 (Z, lambda3, lambda4), FINITE_T 2
+ * (Z, lam).  n_pts in [2, 4096]. */
+typedef struct {
+  int n_tables, n_stack, n_pts, reserved0;
+  double x_min, x_max;
+} ffrg_table_desc;
+
+/* App. C explicit time-stepping parameters (t in t_+). */
+typedef struct {
+  double t0, t1;          /* integrate from t0 to t1 >= t0 */
+  double dt0;             /* initial step ("dt") */
+  double dt_min, dt_max;  /* "minimal_dt", "maximal_dt" */
+  double atol, rtol;      /* "abs_tol", "rel_tol" */
+  long long max_steps;    /* accepted + rejected attempts */
+} ffrg_step_opts;
+
+typedef struct {
+  long long steps, rejects, rhs_evals;
+  double integrand_evals; /* rhs_evals x (external points x quadrature nodes) */
+  double t_reached;
+} ffrg_flow_stats;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * library's own device allocations (0 = no cap).  Owns *out until destroy. */
+FFRG_API int ffrg_create(ffrg_ctx **out, int device, size_t hbm_budget_bytes);
+FFRG_API int ffrg_destroy(ffrg_ctx *ctx);
+
+/* Quadrature rule on the host (Sec. 5.3.2 "quadrature rules of arbitrary
+ * order").  FFRG_RULE_GL: Gauss-Legendre on [a,b], ascending nodes.
+ * FFRG_RULE_GC2: Gauss-Chebyshev of the second kind on [-1,1] for the weight
+ * sqrt(1-x^2) (a, b ignored).  x, w: caller-owned host arrays of n doubles.
+ * Errors: FFRG_EINVAL for n < 1 or n > 65536 or NULL arrays. */
+FFRG_API int ffrg_quad_nodes(int rule, int n, double a, double b, double *x, double *w);
+
+/* Upload dressing tables (App. F interpolator objects).  values: n_tables x
+ * n_stack x n_pts doubles, host memory (values_on_device = 0) or device memory
+ * (1); copied, not retained.  *out is library-owned until ffrg_tables_free.
+ * Errors: FFRG_EINVAL (shape), FFRG_ENOMEM (budget). */
+FFRG_API int ffrg_tables_upload(ffrg_ctx *ctx, const ffrg_table_desc *desc, const double *values, int values_on_device,
+                       ffrg_tables **out, void *stream);
+/* Overwrite the values of existing tables (same shape), stream-ordered. */
+FFRG_API int ffrg_tables_update(ffrg_ctx *ctx, ffrg_tables *tables, const double *values, int values_on_device,
+                       void *stream);
+FFRG_API int ffrg_tables_free(ffrg_ctx *ctx, ffrg_tables *tables);
+/* Device pointer to the FP64 table values (library-owned, for zero-copy use). */
+FFRG_API int ffrg_tables_device_ptr(const ffrg_tables *tables, double **dev_values);
+
+/* Number of external points (output length) and integrand evaluations
+ * (external points x quadrature nodes) of one RHS; -1 / <0 on a bad problem. */
+FFRG_API int ffrg_n_ext(const ffrg_problem *pb);
+FFRG_API double ffrg_evals(const ffrg_problem *pb);
+
+/* One right-hand side at scale k (Eq. GenfRG projected onto the truncation,
+ * Eq. FlowGamman): out_dev[e] = k d_k of the target at external point e (raw
+ * loop integrals; the D4 Z-block holds the propagator-diagram sum D2(p), see
+ * the layout above).  out_dev: caller-owned device array of ffrg_n_ext()
+ * doubles.  precision: FFRG_FP64 (all arithmetic FP64) or FFRG_MIXED (FP32
+ * integrand, FP64 per-radial-node factors and cross-node accumulation, FP64
+ * propagator near the pole).  Asynchronous; non-finite outputs set
+ * FFRG_ENONFINITE in the status word. */
+FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_dev,
+             int precision, void *stream);
+
+/* Vector-Jacobian product of ffrg_rhs with respect to the table values
+ * (the paper forms Jacobians by forward-mode AD, Sec. 5.2.2; this is the
+ * reverse-mode counterpart): tbar_dev[j] = sum_e gbar_dev[e] d out_e / d T_j,
+ * j over all n_tables x n_stack x n_pts values.  gbar_dev: device, ffrg_n_ext
+ * doubles; tbar_dev: device, overwritten.  Models FFRG_MODEL_D3 and
+ * FFRG_MODEL_D4_VERTEX, precision FFRG_FP64 (FFRG_EINVAL otherwise), tables
+ * up to ~2400 values.  Reproducible run to run on a given GPU (fixed
+ * reduction order, no floating-point atomics). */
+FFRG_API int ffrg_rhs_adjoint(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
+                     const double *gbar_dev, double *tbar_dev, int precision, void *stream);
+
+/* Flow of a state vector in RG time t_+ with an adaptive Dormand-Prince 5(4)
+ * stepper whose stage combination, error norm and step control run on the
+ * device in FP64 (Sec. 5.2.1 explicit RK45 stepper; App. C parameters; abort
+ * below minimal_dt).  State layouts (state_dev, device, in: y(t0), out: y(t1)):
+ *   feedback = 0 (frozen tables, any model): y_e, d_t y_e = -out_e
+ *   feedback = 1, D3: [m^2, Z_0..Z_{n-1}]; tables := Z, m^2 := y_0;
+ *       d_t m^2 = -I(0), d_t Z_i = -(I(p_i) - I(0)) / p_i^2
+ *   feedback = 1, D4: [Z, lambda3, lambda4] (3 n values) = the tables;
+ *       d_t Z_i = -(D2(p_i) - D2(0))/p_i^2, d_t lambda3_i = -sum_j (w_j/2)
+ *       Flow3(p_i, psi_j), d_t lambda4_i = -Flow4(p_i)
+ * Feedback requires the external grid to equal the table grid.  k(t) = Lambda
+ * exp(-t).  tables: frozen tables (feedback = 0) or the grid/shape template
+ * (feedback = 1).  Synchronous: returns when the flow ends; stats (host) may be
+ * NULL.  Errors: FFRG_ESTEP_UNDERFLOW, FFRG_EMAXSTEPS, FFRG_ENONFINITE. */
+FFRG_API int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, int feedback, double Lambda,
+              double *state_dev, const ffrg_step_opts *opts, int precision, ffrg_flow_stats *stats,
+              void *stream);
+/* Length of the flow state for (pb, feedback); -1 on a bad combination. */
+FFRG_API int ffrg_flow_state_size(const ffrg_problem *pb, const ffrg_table_desc *desc, int feedback);
+
+/* Kernel timing for benchmarks: while enabled, every ffrg_rhs call records a
+ * CUDA event pair around its main (integrand) kernel on the call's stream (up
+ * to 4096 pairs).  ffrg_profile_read synchronises those events and returns the
+ * summed main-kernel time in milliseconds and the number of launches, then
+ * clears the record.  Enabling clears it too. */
+FFRG_API int ffrg_set_profiling(ffrg_ctx *ctx, int enable);
+FFRG_API int ffrg_profile_read(ffrg_ctx *ctx, double *main_ms, long long *launches);
+
+/* Wait for the stream and return (then clear) the device status word:
+ * FFRG_OK, FFRG_ENONFINITE or FFRG_ETIMEOUT; FFRG_ECUDA on a CUDA error. */
+FFRG_API int ffrg_status_read(ffrg_ctx *ctx, void *stream);
+
+/* Text for a status code; the last CUDA error text of a context. */
+FFRG_API const char *ffrg_strerror(int status);
+FFRG_API const char *ffrg_last_error(const ffrg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFRG_H */

@@ -95,6 +95,7 @@ def _load():
         pp = P(_Problem)
         lib.orc_n_ext.argtypes = [pp]
         lib.orc_rhs.argtypes = [pp, dp, D, dp]
+        lib.orc_rhs_subset.argtypes = [pp, dp, D, P(I), I, dp]
         lib.orc_rhs_jvp.argtypes = [pp, dp, dp, D, dp, dp]
         lib.orc_rhs_jacobian.argtypes = [pp, dp, D, dp]
         lib.orc_flow.argtypes = [pp, dp, I, D, dp, P(_StepOpts), P(_Stats)]
@@ -182,6 +183,18 @@ def rhs(pb, tables, k: float) -> np.ndarray:
     t = _f64(tables)
     out = np.empty(pb.n_ext())
     _check(lib.orc_rhs(ctypes.byref(c), _ptr(t), k, _ptr(out)), "rhs")
+    return out
+
+
+def rhs_subset(pb, tables, k: float, sel) -> np.ndarray:
+    """The RHS at the external points listed in sel only."""
+    lib = _load()
+    c = _problem(pb)
+    t = _f64(tables)
+    idx = np.ascontiguousarray(np.asarray(sel, dtype=np.int32))
+    out = np.empty(idx.size)
+    _check(lib.orc_rhs_subset(ctypes.byref(c), _ptr(t), k, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                              idx.size, _ptr(out)), "rhs_subset")
     return out
 
 

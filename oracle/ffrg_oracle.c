@@ -312,7 +312,7 @@ static dual d3_summand_dual(const orc_problem *pb, const double *tab, const doub
 }
 
 static int rhs_d3(const orc_problem *pb, const double *tab, const double *dtab, double k, double *out,
-                  double *dout) {
+                  double *dout, const int *sel, int nsel) {
   int nr = pb->n_rad, na = pb->n_ang1, ne = orc_n_ext(pb);
   double *xr = malloc(sizeof(double) * nr), *wr = malloc(sizeof(double) * nr);
   double *xa = malloc(sizeof(double) * na), *wa = malloc(sizeof(double) * na);
@@ -320,8 +320,10 @@ static int rhs_d3(const orc_problem *pb, const double *tab, const double *dtab, 
   orc_gauss_legendre(nr, 0.0, pb->qmax_over_k * k, xr, wr);
   orc_gauss_legendre(na, -1.0, 1.0, xa, wa);
   double norm = pb->prefactor * pb->lam * pb->lam / (4.0 * ORC_PI * ORC_PI);
+  int nloop = sel ? nsel : ne;
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int e = 0; e < ne; ++e) {
+  for (int ie = 0; ie < nloop; ++ie) {
+    int e = sel ? sel[ie] : ie;
     double p = (e < pb->n_ext_p) ? ext_p(pb, e) : 0.0;
     acc_t acc = {0, 0}, dacc = {0, 0};
     for (int i = 0; i < nr; ++i) {
@@ -338,8 +340,8 @@ static int rhs_d3(const orc_problem *pb, const double *tab, const double *dtab, 
         }
       }
     }
-    out[e] = norm * acc_get(&acc);
-    if (dout) dout[e] = norm * acc_get(&dacc);
+    out[ie] = norm * acc_get(&acc);
+    if (dout) dout[ie] = norm * acc_get(&dacc);
   }
   free(xr); free(wr); free(xa); free(wa);
   return ORC_OK;
@@ -441,7 +443,7 @@ static dual d4_summand_dual(int block, const orc_problem *pb, const double *tab,
 }
 
 static int rhs_d4(const orc_problem *pb, const double *tab, const double *dtab, double k, double *out,
-                  double *dout) {
+                  double *dout, const int *sel, int nsel) {
   int nr = pb->n_rad, n1 = pb->n_ang1, n2 = pb->n_ang2, np = pb->n_ext_p, npsi = pb->n_ext_ang;
   int ne = orc_n_ext(pb);
   double *xr = malloc(sizeof(double) * nr), *wr = malloc(sizeof(double) * nr);
@@ -457,8 +459,10 @@ static int rhs_d4(const orc_problem *pb, const double *tab, const double *dtab, 
   orc_gauss_legendre(n2, -1.0, 1.0, x2, w2);
   orc_gauss_legendre(npsi, -1.0, 1.0, xp, wp);
   double norm = pb->prefactor / (8.0 * ORC_PI * ORC_PI * ORC_PI);
+  int nloop = sel ? nsel : ne;
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int e = 0; e < ne; ++e) {
+  for (int ie = 0; ie < nloop; ++ie) {
+    int e = sel ? sel[ie] : ie;
     /* external-point layout: [Z: p_0..p_{np-1}, p=0][lambda3: p x psi][lambda4: p] */
     int block;
     double p, cpsi = 1.0, spsi = 0.0;
@@ -502,8 +506,8 @@ static int rhs_d4(const orc_problem *pb, const double *tab, const double *dtab, 
         }
       }
     }
-    out[e] = norm * acc_get(&acc);
-    if (dout) dout[e] = norm * acc_get(&dacc);
+    out[ie] = norm * acc_get(&acc);
+    if (dout) dout[ie] = norm * acc_get(&dacc);
   }
   free(xr); free(wr); free(x1); free(w1); free(x2); free(w2); free(xp); free(wp);
   return ORC_OK;
@@ -538,7 +542,7 @@ double orc_ft_summand(const orc_problem *pb, const double *tab, double k, int n,
   return dR * Gq * Gq * Lq * Ls * Gs;
 }
 
-static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *out) {
+static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *out, const int *sel, int nsel) {
   int nr = pb->n_rad, na = pb->n_ang1, N = pb->n_matsubara, nm = pb->n_ext_ang;
   int ne = orc_n_ext(pb);
   double *xr = malloc(sizeof(double) * nr), *wr = malloc(sizeof(double) * nr);
@@ -547,8 +551,10 @@ static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *ou
   orc_gauss_legendre(nr, 0.0, pb->qmax_over_k * k, xr, wr);
   orc_gauss_legendre(na, -1.0, 1.0, xa, wa);
   double norm = pb->prefactor * pb->lam * pb->lam * pb->T / (4.0 * ORC_PI * ORC_PI);
+  int nloop = sel ? nsel : ne;
 #pragma omp parallel for schedule(dynamic, 1)
-  for (int e = 0; e < ne; ++e) {
+  for (int ie = 0; ie < nloop; ++ie) {
+    int e = sel ? sel[ie] : ie;
     int ip = e / nm, m = e % nm;
     double p = ext_p(pb, ip);
     acc_t acc = {0, 0};
@@ -561,7 +567,7 @@ static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *ou
         }
       }
     }
-    out[e] = norm * acc_get(&acc);
+    out[ie] = norm * acc_get(&acc);
   }
   free(xr); free(wr); free(xa); free(wa);
   return ORC_OK;
@@ -575,9 +581,26 @@ int orc_rhs(const orc_problem *pb, const double *tables, double k, double *out) 
   if (st) return st;
   if (!(k > 0.0) || !tables || !out) return ORC_EINVAL;
   switch (pb->model) {
-  case ORC_D3: return rhs_d3(pb, tables, NULL, k, out, NULL);
-  case ORC_D4_VERTEX: return rhs_d4(pb, tables, NULL, k, out, NULL);
-  case ORC_FINITE_T: return rhs_ft(pb, tables, k, out);
+  case ORC_D3: return rhs_d3(pb, tables, NULL, k, out, NULL, NULL, 0);
+  case ORC_D4_VERTEX: return rhs_d4(pb, tables, NULL, k, out, NULL, NULL, 0);
+  case ORC_FINITE_T: return rhs_ft(pb, tables, k, out, NULL, 0);
+  }
+  return ORC_EINVAL;
+}
+
+/* The same sums restricted to the external points sel[0..nsel-1]
+ * (out[i] belongs to sel[i]); used to sample full-size problems. */
+int orc_rhs_subset(const orc_problem *pb, const double *tables, double k, const int *sel, int nsel, double *out) {
+  int st = check_problem(pb);
+  if (st) return st;
+  if (!(k > 0.0) || !tables || !out || !sel || nsel < 0) return ORC_EINVAL;
+  int ne = orc_n_ext(pb);
+  for (int i = 0; i < nsel; ++i)
+    if (sel[i] < 0 || sel[i] >= ne) return ORC_EINVAL;
+  switch (pb->model) {
+  case ORC_D3: return rhs_d3(pb, tables, NULL, k, out, NULL, sel, nsel);
+  case ORC_D4_VERTEX: return rhs_d4(pb, tables, NULL, k, out, NULL, sel, nsel);
+  case ORC_FINITE_T: return rhs_ft(pb, tables, k, out, sel, nsel);
   }
   return ORC_EINVAL;
 }
@@ -590,8 +613,8 @@ int orc_rhs_jvp(const orc_problem *pb, const double *tables, const double *dtabl
   if (st) return st;
   if (!(k > 0.0) || !tables || !dtables || !out || !dout) return ORC_EINVAL;
   switch (pb->model) {
-  case ORC_D3: return rhs_d3(pb, tables, dtables, k, out, dout);
-  case ORC_D4_VERTEX: return rhs_d4(pb, tables, dtables, k, out, dout);
+  case ORC_D3: return rhs_d3(pb, tables, dtables, k, out, dout, NULL, 0);
+  case ORC_D4_VERTEX: return rhs_d4(pb, tables, dtables, k, out, dout, NULL, 0);
   default: return ORC_EINVAL;
   }
 }

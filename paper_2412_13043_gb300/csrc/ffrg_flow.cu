@@ -1,0 +1,396 @@
+// Device-resident adaptive Dormand-Prince 5(4) flow in RG time t = t_+ =
+// ln(Lambda/k) (Sec. 2.1), with the variable-assembler residual d_t y = -Flow
+// (Sec. 5.2.2, Eqs. assVar / flowVar) and the explicit-stepper parameters dt,
+// minimal_dt, maximal_dt, abs_tol, rel_tol (Sec. 5.2.1 RK45, App. C).
+//
+// One step = six stages of [stage state -> RHS (precompute / main / finalize)
+// -> derivative map], then one single-CTA control kernel that forms the FP64
+// error norm, accepts or rejects, updates the step size and decides the next
+// step (or that the flow is done).  All of it reads its scalars (t, h, k, m^2,
+// done) from a device control block, so one step is captured once into a CUDA
+// graph and relaunched; the host looks at the done flag only every few steps.
+// Launches after the flow has finished return at once (skip flag).
+#include <math.h>
+
+#include <algorithm>
+
+#include "ffrg_internal.cuh"
+
+namespace ffrg {
+
+// Dormand & Prince (1980) coefficients, from the published tableau.
+__constant__ double kDpC[7] = {0.0, 0.2, 0.3, 0.8, 8.0 / 9.0, 1.0, 1.0};
+__constant__ double kDpA[7][6] = {
+    {0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {0.2, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {3.0 / 40.0, 9.0 / 40.0, 0.0, 0.0, 0.0, 0.0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0.0, 0.0, 0.0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0.0, 0.0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0.0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+// fifth-order minus embedded fourth-order weights
+__constant__ double kDpE[7] = {35.0 / 384.0 - 5179.0 / 57600.0,
+                               0.0,
+                               500.0 / 1113.0 - 7571.0 / 16695.0,
+                               125.0 / 192.0 - 393.0 / 640.0,
+                               -2187.0 / 6784.0 + 92097.0 / 339200.0,
+                               11.0 / 84.0 - 187.0 / 2100.0,
+                               -1.0 / 40.0};
+
+struct FlowCtl {
+  double t, dt, h, t0, t1, dt_min, dt_max, atol, rtol, end_tol, Lambda;
+  double k_stage, m2_stage, err;
+  long long steps, rejects, max_steps;
+  int last_rejected, done, status, pad;
+};
+
+struct FlowArgs {
+  int ny, mode;       // mode: 0 frozen, 1 D3 feedback, 2 D4 feedback
+  int n, npsi;        // table points / external angles (feedback)
+  int tab_off, tab_len;
+  double p_min, p_step;
+  const double *psi_w;
+  double *y, *ys, *K, *raw, *tabbuf;
+  FlowCtl *ctl;
+};
+
+enum { kModeFrozen = 0, kModeD3Feedback = 1, kModeD4Feedback = 2 };
+
+__device__ __forceinline__ double ext_p(const FlowArgs &f, int i) { return f.p_min * exp((double)i * f.p_step); }
+
+// d_t y_i = -Flow_i from the raw loop integrals.
+__device__ __forceinline__ double deriv_component(const FlowArgs &f, int i) {
+  const double *raw = f.raw;
+  if (f.mode == kModeFrozen) return -raw[i];
+  if (f.mode == kModeD3Feedback) {
+    const int n = f.n;
+    if (i == 0) return -raw[n];
+    const double p = ext_p(f, i - 1);
+    return -(raw[i - 1] - raw[n]) / (p * p);
+  }
+  const int n = f.n, npsi = f.npsi;
+  if (i < n) {
+    const double p = ext_p(f, i);
+    return -(raw[i] - raw[n]) / (p * p);
+  }
+  if (i < 2 * n) {
+    const int ip = i - n;
+    double s = 0.0;
+    for (int j = 0; j < npsi; ++j) s += 0.5 * f.psi_w[j] * raw[n + 1 + ip * npsi + j];
+    return -s;
+  }
+  return -raw[n + 1 + n * npsi + (i - 2 * n)];
+}
+
+// Stage state for stage s (1..6): ys = y + h sum_{r<s} A[s][r] K_r; s = 0: ys = y.
+// Also publishes k and m^2 of the stage and the feedback tables.
+__device__ __forceinline__ void write_stage_state(const FlowArgs &f, int s, int i, double h) {
+  double v = f.y[i];
+  for (int r = 0; r < s; ++r) v += h * kDpA[s][r] * f.K[(size_t)r * f.ny + i];
+  f.ys[i] = v;
+  if (f.tabbuf && i >= f.tab_off && i < f.tab_off + f.tab_len) f.tabbuf[i - f.tab_off] = v;
+  if (i == 0 && f.mode == kModeD3Feedback) f.ctl->m2_stage = v;
+}
+
+__global__ void flow_prep_kernel(FlowArgs f, int s) {
+  const FlowCtl *c = f.ctl;
+  if (*(volatile const int *)&c->done) return;
+  const double h = c->h;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) f.ctl->k_stage = c->Lambda * exp(-(c->t + kDpC[s] * h));
+  if (i < f.ny) write_stage_state(f, s, i, h);
+}
+
+// K_s from the RHS, then (s < 6) the state of stage s+1.
+__global__ void flow_deriv_kernel(FlowArgs f, int s) {
+  const FlowCtl *c = f.ctl;
+  if (*(volatile const int *)&c->done) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double h = c->h;
+  if (i < f.ny) f.K[(size_t)s * f.ny + i] = deriv_component(f, i);
+  if (s >= 1 && s < 6) {
+    if (i == 0) f.ctl->k_stage = c->Lambda * exp(-(c->t + kDpC[s + 1] * h));
+    if (i < f.ny) write_stage_state(f, s + 1, i, h);
+  }
+}
+
+__device__ __forceinline__ void decide_next_step(FlowCtl *c) {
+  const double remaining = c->t1 - c->t;
+  if (!(remaining > c->end_tol)) {
+    c->done = 1;
+    return;
+  }
+  if (c->steps + c->rejects >= c->max_steps) {
+    c->status = FFRG_EMAXSTEPS;
+    c->done = 1;
+    return;
+  }
+  c->h = fmin(c->dt, remaining);
+}
+
+__global__ void flow_start_kernel(FlowCtl *c) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) decide_next_step(c);
+}
+
+// Error norm max_i |h sum_r E_r K_r,i| / (atol + rtol max(|y_i|, |y5_i|)),
+// accept / reject, step-size update (same controller as the CPU oracle).
+__global__ void __launch_bounds__(1024) flow_control_kernel(FlowArgs f) {
+  FlowCtl *c = f.ctl;
+  __shared__ double red[32];
+  __shared__ int bad_s[32];
+  __shared__ int accept_s;
+  if (*(volatile const int *)&c->done) return;
+  const double h = c->h, atol = c->atol, rtol = c->rtol;
+  double emax = 0.0;
+  int bad = 0;
+  for (int i = threadIdx.x; i < f.ny; i += blockDim.x) {
+    double e = 0.0;
+    for (int r = 0; r < 7; ++r) e += kDpE[r] * f.K[(size_t)r * f.ny + i];
+    e *= h;
+    const double y5 = f.ys[i];
+    const double sc = atol + rtol * fmax(fabs(f.y[i]), fabs(y5));
+    const double ei = fabs(e) / sc;
+    if (!isfinite(ei) || !isfinite(y5)) bad = 1;
+    else emax = fmax(emax, ei);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
+    bad |= __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[warp] = emax;
+    bad_s[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double err = 0.0;
+    int anybad = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      err = fmax(err, red[w]);
+      anybad |= bad_s[w];
+    }
+    c->err = err;
+    int acc = 0;
+    if (anybad) {
+      c->status = FFRG_ENONFINITE;
+      c->done = 1;
+    } else if (err <= 1.0) {
+      acc = 1;
+      c->t += h;
+      c->steps += 1;
+      double fac = (err == 0.0) ? 5.0 : 0.9 * pow(err, -0.2);
+      fac = fmin(fmax(fac, 0.2), 5.0);
+      if (c->last_rejected) fac = fmin(fac, 1.0);
+      c->last_rejected = 0;
+      c->dt = h * fac;
+    } else {
+      c->rejects += 1;
+      if (h <= c->dt_min) {
+        c->status = FFRG_ESTEP_UNDERFLOW;
+        c->done = 1;
+      } else {
+        c->dt = h * fmax(0.9 * pow(err, -0.2), 0.2);
+        c->last_rejected = 1;
+      }
+    }
+    c->dt = fmin(fmax(c->dt, c->dt_min), c->dt_max);
+    accept_s = acc;
+  }
+  __syncthreads();
+  if (accept_s) {
+    for (int i = threadIdx.x; i < f.ny; i += blockDim.x) {
+      f.y[i] = f.ys[i];
+      f.K[i] = f.K[(size_t)6 * f.ny + i];  // first-same-as-last
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !c->done) decide_next_step(c);
+}
+
+static int flow_mode(const ffrg_problem *pb, int feedback) {
+  if (!feedback) return kModeFrozen;
+  if (pb->model == FFRG_MODEL_D3) return kModeD3Feedback;
+  if (pb->model == FFRG_MODEL_D4_VERTEX) return kModeD4Feedback;
+  return -1;
+}
+
+}  // namespace ffrg
+
+using namespace ffrg;
+
+extern "C" int ffrg_flow_state_size(const ffrg_problem *pb, const ffrg_table_desc *desc, int feedback) {
+  if (!pb || validate_problem(pb, desc) != FFRG_OK) return -1;
+  int mode = flow_mode(pb, feedback);
+  if (mode < 0) return -1;
+  if (mode == kModeFrozen) return ffrg_n_ext(pb);
+  if (!desc) return -1;
+  if (mode == kModeD3Feedback) return 1 + desc->n_pts;
+  return 3 * desc->n_pts;
+}
+
+extern "C" int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_tables *tables, int feedback,
+                         double Lambda, double *state_dev, const ffrg_step_opts *o, int precision,
+                         ffrg_flow_stats *stats, void *stream) {
+  if (!ctx || !pb_in || !tables || !state_dev || !o) return FFRG_EINVAL;
+  if (precision != FFRG_FP64 && precision != FFRG_MIXED) return FFRG_EINVAL;
+  if (!(Lambda > 0.0) || !isfinite(Lambda)) return FFRG_EINVAL;
+  if (!(o->t1 >= o->t0) || !isfinite(o->t1) || !isfinite(o->t0) || !(o->dt0 > 0.0) || !(o->dt_min > 0.0) ||
+      !(o->dt_max >= o->dt_min) || !(o->atol >= 0.0) || !(o->rtol >= 0.0) || !(o->atol + o->rtol > 0.0) ||
+      o->max_steps < 1)
+    return FFRG_EINVAL;
+  ffrg_problem pb = *pb_in;
+  const ffrg_table_desc *td = &tables->desc;
+  int st = validate_problem(&pb, td);
+  if (st) return st;
+  const int mode = flow_mode(&pb, feedback);
+  if (mode < 0) return FFRG_EINVAL;
+  if (mode != kModeFrozen) {
+    // feedback: the external grid is the table grid
+    if (pb.n_ext_p != td->n_pts || pb.p_min != td->x_min || pb.p_max != td->x_max || td->n_stack != 1)
+      return FFRG_EINVAL;
+  }
+  if (mode == kModeD3Feedback) pb.include_p0 = 1;  // I(0) enters d_t m^2 and d_t Z
+  const int ny = ffrg_flow_state_size(&pb, td, feedback);
+  if (ny < 1) return FFRG_EINVAL;
+  cudaSetDevice(ctx->device);
+  Plan *pl = nullptr;
+  st = get_plan(ctx, &pb, td, &pl);
+  if (st) return st;
+  const int n_ext = pl->n_ext;
+
+  // device buffers of this flow
+  FlowCtl *ctl = nullptr;
+  double *ys = nullptr, *K = nullptr, *raw = nullptr, *tabbuf = nullptr;
+  FlowCtl *ctl_host = nullptr;
+  const size_t tab_bytes = ((size_t)pl->tab_count * sizeof(double) + 255) & ~(size_t)255;
+  st = dev_alloc(ctx, (void **)&ctl, sizeof(FlowCtl));
+  if (!st) st = dev_alloc(ctx, (void **)&ys, (size_t)ny * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&K, (size_t)7 * ny * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&raw, (size_t)n_ext * sizeof(double));
+  if (!st && mode != kModeFrozen) st = dev_alloc(ctx, (void **)&tabbuf, tab_bytes);
+  if (!st) st = set_cuda_error(ctx, cudaMallocHost((void **)&ctl_host, sizeof(FlowCtl)), "cudaMallocHost");
+  cudaStream_t user = (cudaStream_t)stream, fs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (!st) st = set_cuda_error(ctx, cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!st) st = set_cuda_error(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+
+  FlowCtl hc;
+  memset(&hc, 0, sizeof(hc));
+  hc.t = o->t0;
+  hc.t0 = o->t0;
+  hc.t1 = o->t1;
+  hc.dt = fmin(fmax(o->dt0, o->dt_min), o->dt_max);
+  hc.dt_min = o->dt_min;
+  hc.dt_max = o->dt_max;
+  hc.atol = o->atol;
+  hc.rtol = o->rtol;
+  hc.end_tol = 1e-13 * fmax(fabs(o->t1 - o->t0), 1.0);
+  hc.Lambda = Lambda;
+  hc.max_steps = o->max_steps;
+  hc.status = FFRG_OK;
+
+  FlowArgs f;
+  memset(&f, 0, sizeof(f));
+  f.ny = ny;
+  f.mode = mode;
+  f.n = td->n_pts;
+  f.npsi = pb.n_ext_ang;
+  f.tab_off = mode == kModeD3Feedback ? 1 : 0;
+  f.tab_len = mode == kModeFrozen ? 0 : pl->tab_count;
+  f.p_min = pb.p_min;
+  f.p_step = pb.n_ext_p > 1 ? log(pb.p_max / pb.p_min) / (pb.n_ext_p - 1) : 0.0;
+  f.psi_w = pl->psi_w;
+  f.y = state_dev;
+  f.ys = ys;
+  f.K = K;
+  f.raw = raw;
+  f.tabbuf = tabbuf;
+  f.ctl = ctl;
+
+  RhsArgs a;
+  fill_args(pl, &pb, td, mode == kModeFrozen ? tables->dev : tabbuf, Lambda, a);
+  a.out = raw;
+  a.status = ctx->status_dev;
+  a.k_dev = &ctl->k_stage;
+  a.m2_dev = mode == kModeD3Feedback ? &ctl->m2_stage : nullptr;
+  a.skip = &ctl->done;
+
+  const int eb = 256, eg = (ny + eb - 1) / eb;
+  long long attempts_done = 0;
+  if (!st) {
+    // order after the caller's stream, initialise, first derivative (FSAL stage 0)
+    st = set_cuda_error(ctx, cudaEventRecord(ev, user), "cudaEventRecord");
+    if (!st) st = set_cuda_error(ctx, cudaStreamWaitEvent(fs, ev, 0), "cudaStreamWaitEvent");
+    if (!st) st = set_cuda_error(ctx, cudaMemcpyAsync(ctl, &hc, sizeof(FlowCtl), cudaMemcpyHostToDevice, fs),
+                                 "cudaMemcpyAsync(ctl)");
+    if (!st) {
+      flow_prep_kernel<<<eg, eb, 0, fs>>>(f, 0);
+      st = launch_rhs(ctx, pl, a, precision, fs);
+    }
+    if (!st) {
+      flow_deriv_kernel<<<eg, eb, 0, fs>>>(f, 0);
+      flow_start_kernel<<<1, 32, 0, fs>>>(ctl);
+      st = set_cuda_error(ctx, cudaGetLastError(), "flow init");
+    }
+    // make sure the persistent grids are known before capture (no attribute calls inside)
+    if (!st) st = set_cuda_error(ctx, cudaStreamSynchronize(fs), "flow init sync");
+  }
+  if (!st) {
+    // capture one adaptive step
+    st = set_cuda_error(ctx, cudaStreamBeginCapture(fs, cudaStreamCaptureModeThreadLocal), "BeginCapture");
+    if (!st) {
+      int cst = FFRG_OK;
+      flow_prep_kernel<<<eg, eb, 0, fs>>>(f, 1);
+      for (int s = 1; s <= 6 && !cst; ++s) {
+        cst = launch_rhs(ctx, pl, a, precision, fs);
+        flow_deriv_kernel<<<eg, eb, 0, fs>>>(f, s);
+      }
+      flow_control_kernel<<<1, 1024, 0, fs>>>(f);
+      cudaError_t ce = cudaStreamEndCapture(fs, &graph);
+      st = cst ? cst : set_cuda_error(ctx, ce, "EndCapture");
+    }
+    if (!st) st = set_cuda_error(ctx, cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+  }
+  if (!st) {
+    int batch = 2;
+    for (;;) {
+      for (int b = 0; b < batch && !st; ++b)
+        st = set_cuda_error(ctx, cudaGraphLaunch(exec, fs), "cudaGraphLaunch");
+      if (st) break;
+      st = set_cuda_error(ctx, cudaMemcpyAsync(ctl_host, ctl, sizeof(FlowCtl), cudaMemcpyDeviceToHost, fs),
+                          "cudaMemcpyAsync(ctl)");
+      if (!st) st = set_cuda_error(ctx, cudaStreamSynchronize(fs), "flow sync");
+      if (st) break;
+      attempts_done = ctl_host->steps + ctl_host->rejects;
+      if (ctl_host->done) break;
+      batch = std::min(batch * 2, 32);
+    }
+  }
+  if (!st) {
+    if (stats) {
+      stats->steps = ctl_host->steps;
+      stats->rejects = ctl_host->rejects;
+      stats->rhs_evals = 1 + 6 * attempts_done;
+      stats->integrand_evals = (double)stats->rhs_evals * ffrg_evals(&pb);
+      stats->t_reached = ctl_host->t;
+    }
+    st = ctl_host->status;
+    // order the caller's stream after the flow
+    if (cudaEventRecord(ev, fs) == cudaSuccess) cudaStreamWaitEvent(user, ev, 0);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (fs) cudaStreamSynchronize(fs);
+  if (ev) cudaEventDestroy(ev);
+  if (fs) cudaStreamDestroy(fs);
+  if (ctl_host) cudaFreeHost(ctl_host);
+  dev_free(ctx, ctl, sizeof(FlowCtl));
+  dev_free(ctx, ys, (size_t)ny * sizeof(double));
+  dev_free(ctx, K, (size_t)7 * ny * sizeof(double));
+  dev_free(ctx, raw, (size_t)n_ext * sizeof(double));
+  dev_free(ctx, tabbuf, tab_bytes);
+  return st;
+}

@@ -1,0 +1,304 @@
+// Internal declarations of the ffrg CUDA library (not part of the C ABI).
+//
+// Device-side pieces of the momentum-loop right-hand side (DiFfRG,
+// arXiv:2412.13043): regulator shape and scale derivative (Sec. 5.3.1),
+// log-grid table lookup (App. F interpolators), propagators with a
+// Z-dressed regulator (App. G propagator form), and the argument block that
+// every RHS kernel receives by value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ffrg.h"
+
+namespace ffrg {
+
+constexpr int kThreads = 256;          // threads per CTA of the RHS kernels
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device wait
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int kMaxPts = 4096;
+constexpr int kMaxNodes = 65536;
+
+// ---------------------------------------------------------------------------
+// Kernel argument block (passed by value).
+// ---------------------------------------------------------------------------
+struct RhsArgs {
+  int model, reg;
+  int nr, na1, na2;
+  int n_ext_p, n_ext_ang, N, include_p0, n_ext;
+  int n_tables, n_stack, n_pts, tab_count;
+  int cr;          // outer rows (radial, or Matsubara x radial) per work item
+  int n_chunks;    // work items per external point
+  int n_items;     // n_ext * n_chunks
+  int jb;          // angle nodes per row (D3 / FINITE_T)
+  double k, m2_over_k2, m2_shift, T;
+  double p_min, p_ratio_step;  // p_i = p_min * exp(i * p_ratio_step)
+  double qmax_over_k;
+  double norm;                 // overall factor applied in finalize
+  double u_scale, u_off;       // u = u_scale ln(s^2) + u_off
+  double x_min2;               // lookups clamp s^2 below x_min^2
+  double sum_w2;               // sum of the second-angle weights (D4)
+  const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
+  float *tab32;                // FP32 mirror written by the precompute kernel
+  const double *rad_x, *rad_w; // unit-interval GL rule on [0, 1]
+  const double *a1_x, *a1_w;   // first angle rule
+  const double *a2_x, *a2_w;   // second angle rule (D4)
+  const double *psi_x;         // external angles cos(psi) (D4)
+  const double *k_dev;         // optional device scale k (flow stages)
+  const double *m2_dev;        // optional device m2_shift (feedback flows)
+  const int *skip;             // optional device flag: when non-zero every kernel returns at once
+  double *radD;                // optional: d radF / d Z(q) (adjoint)
+  double *radF;                // per-(n, r) factor
+  double *radq;                // per-r momentum q
+  double *partial;             // [n_ext][n_chunks]
+  double *out;                 // [n_ext]
+  unsigned *status;
+};
+
+// ---------------------------------------------------------------------------
+// Regulator r(x) = R / (Z k^2) and rdot(x) = k d_k R / (Z k^2), x = q^2/k^2.
+// Exponential shape x/(e^x - 1) with dR-shape 2 x^2 e^{-x}/(1-e^{-x})^2;
+// flat shape (1-x) Theta(1-x) with dR-shape 2 Theta(1-x).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double reg_r(int reg, double x) {
+  if (reg == FFRG_REG_LITIM) return x < 1.0 ? 1.0 - x : 0.0;
+  if (x > 700.0) return 0.0;
+  if (x < 1e-100) return 1.0;
+  return x / expm1(x);
+}
+
+__device__ __forceinline__ double reg_rdot(int reg, double x) {
+  if (reg == FFRG_REG_LITIM) return x < 1.0 ? 2.0 : 0.0;
+  if (x > 700.0) return 0.0;
+  if (x < 1e-100) return 2.0;
+  double em = expm1(-x);
+  return 2.0 * x * x * exp(-x) / (em * em);
+}
+
+__device__ __forceinline__ float reg_r(int reg, float x) {
+  if (reg == FFRG_REG_LITIM) return x < 1.f ? 1.f - x : 0.f;
+  if (x > 80.f) return 0.f;
+  if (x < 1e-30f) return 1.f;
+  return x / expm1f(x);
+}
+
+// ---------------------------------------------------------------------------
+// Log-grid lookup: u = (n-1) ln(s/x_min)/ln(x_max/x_min) = u_scale ln(s^2) + u_off,
+// clamped to [0, n-1]; linear in the value between nodes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void lerp_pos(double s2, double x_min2, double u_scale, double u_off, int n, int &i0,
+                                         double &w) {
+  double u = u_scale * log(fmax(s2, x_min2)) + u_off;
+  u = fmin(fmax(u, 0.0), (double)(n - 1));
+  int i = (int)u;
+  i = min(i, n - 2);
+  i0 = i;
+  w = u - (double)i;
+}
+
+__device__ __forceinline__ void lerp_pos(float s2, float x_min2, float u_scale, float u_off, int n, int &i0,
+                                         float &w) {
+  float u = u_scale * __logf(fmaxf(s2, x_min2)) + u_off;
+  u = fminf(fmaxf(u, 0.f), (float)(n - 1));
+  int i = (int)u;
+  i = min(i, n - 2);
+  i0 = i;
+  w = u - (float)i;
+}
+
+template <typename T>
+__device__ __forceinline__ T lerp_at(const T *tab, int i0, T w) {
+  T a = tab[i0], b = tab[i0 + 1];
+  return a + w * (b - a);
+}
+
+template <typename T>
+__device__ __forceinline__ T lerp(const T *tab, T s2, T x_min2, T u_scale, T u_off, int n) {
+  int i0;
+  T w;
+  lerp_pos(s2, x_min2, u_scale, u_off, n, i0, w);
+  return lerp_at(tab, i0, w);
+}
+
+// Propagator denominator Z (omega^2 + s^2 + k^2 r(s^2/k^2)) + m^2, FP64.
+__device__ __forceinline__ double prop_den(int reg, double Z, double om2, double s2, double m2, double k2,
+                                           double inv_k2) {
+  return Z * (om2 + s2 + k2 * reg_r(reg, s2 * inv_k2)) + m2;
+}
+
+// Device-wide status word (sticky bits).
+__device__ __forceinline__ void raise_status(unsigned *status, unsigned bit) {
+  if (status) atomicOr(status, bit);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk staging (cp.async.bulk global -> shared, completion on an mbarrier)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// Stage `count` elements from global memory into shared memory.  The 16-byte
+// aligned prefix goes through one bulk copy issued by thread 0; the rest (or
+// everything, when the source is not 16-byte aligned) through plain loads.
+// Every wait is bounded; on timeout the status word gets kStatusTimeout, the
+// CTA waits once more (bounded) for its own copy in flight, and returns false.
+template <typename T>
+__device__ bool stage_to_smem(T *sdst, const T *gsrc, int count, uint64_t *bar, unsigned *status) {
+  size_t bytes = (size_t)count * sizeof(T);
+  uint32_t bulk = 0;
+  if ((((uintptr_t)gsrc) & 15u) == 0 && (((uintptr_t)sdst) & 15u) == 0 && bytes < (1u << 20))
+    bulk = (uint32_t)(bytes & ~(size_t)15);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (bulk) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bulk)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(sdst)),
+          "l"(gsrc), "r"(bulk), "r"(smem_u32(bar))
+          : "memory");
+    } else {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    }
+  }
+  for (int i = (int)(bulk / sizeof(T)) + threadIdx.x; i < count; i += blockDim.x) sdst[i] = gsrc[i];
+  bool ok = true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, 0)) {
+    if (clock64() - t0 > kWaitCycles) {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok) {
+    raise_status(status, kStatusTimeout);
+    long long t1 = clock64();
+    while (!mbar_try_wait(bar, 0) && clock64() - t1 < kWaitCycles) {
+    }
+  }
+  int bad = __syncthreads_or(ok ? 0 : 1);
+  return bad == 0;
+}
+
+// ---------------------------------------------------------------------------
+// Shared helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  }
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double scale_k(const RhsArgs &a) { return a.k_dev ? *a.k_dev : a.k; }
+__device__ __forceinline__ double mass2(const RhsArgs &a, double k) {
+  return a.m2_over_k2 * k * k + (a.m2_dev ? *a.m2_dev : a.m2_shift);
+}
+
+__device__ __forceinline__ double ext_momentum(const RhsArgs &a, int ip) {
+  return a.p_min * exp((double)ip * a.p_ratio_step);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side objects.
+// ---------------------------------------------------------------------------
+struct Plan;
+
+}  // namespace ffrg
+
+struct ffrg_tables {
+  ffrg_table_desc desc;
+  double *dev;       // FP64 values
+  size_t count;      // n_tables * n_stack * n_pts
+  size_t bytes;      // allocated bytes (padded)
+};
+
+struct ffrg_ctx {
+  int device;
+  int num_sms;
+  size_t budget;
+  size_t used;
+  unsigned *status_dev;     // sticky device status word
+  unsigned *status_host;    // pinned mirror
+  std::string last_error;
+  std::map<std::vector<long long>, ffrg::Plan *> plans;
+  std::vector<void *> owned;  // misc allocations freed at destroy
+  int profiling;
+  std::vector<cudaEvent_t> prof_events;  // start/stop pairs
+  int prof_used;                         // pairs recorded
+};
+
+namespace ffrg {
+
+// Reusable launch plan for one problem shape: quadrature rules on the device,
+// scratch buffers and the launch geometry.
+struct Plan {
+  std::vector<long long> key;
+  int model;
+  int nr, na1, na2, n_ext_ang, n_ext_p, N, include_p0, n_ext;
+  int n_tables, n_stack, n_pts, tab_count;
+  int cr, n_chunks, n_items, jb;
+  int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
+  size_t smem64, smem32;    // dynamic shared memory bytes
+  double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;
+  double sum_w2;
+  double *radF, *radq, *partial;
+  float *tab32;
+  double *radD, *gpart;     // adjoint scratch (allocated on first use)
+  int adj_grid;
+  size_t adj_smem;
+  std::vector<double> psi_w_host;
+};
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
+// lowers it: plans of different sizes share the kernel).
+int ensure_smem_limit(ffrg_ctx *ctx, const void *func, size_t bytes);
+
+// helpers implemented in ffrg_api.cu
+int set_cuda_error(ffrg_ctx *ctx, cudaError_t e, const char *what);
+int dev_alloc(ffrg_ctx *ctx, void **p, size_t bytes);
+void dev_free(ffrg_ctx *ctx, void *p, size_t bytes);
+int validate_problem(const ffrg_problem *pb, const ffrg_table_desc *td);
+int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out);
+void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td, const double *tab, double k,
+               RhsArgs &a);
+int host_gauss_legendre(int n, double a, double b, double *x, double *w);
+int host_gauss_chebyshev2(int n, double *x, double *w);
+
+// kernels launched from several translation units (ffrg_rhs.cu)
+int launch_rhs(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s);
+int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s);
+
+}  // namespace ffrg

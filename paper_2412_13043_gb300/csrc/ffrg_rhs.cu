@@ -1,0 +1,418 @@
+// Momentum-loop right-hand side on sm_103a: for every external point a sum
+// over radial x angular (x Matsubara) quadrature nodes of regulator
+// derivative x propagators x vertices read from dressing tables (Sec. 2.1
+// Eq. GenfRG / FlowGamman; Sec. 5.3.2 quadrature integrators; App. F
+// interpolators).
+//
+// Kernel sequence per RHS (one stream):
+//   1. precompute: per radial node (and Matsubara index) the p-independent
+//      factor F = w q^{d-1} dR(q) G(q)^2 [lam(n,q)] in FP64 (the paper's
+//      generated kernels hoist repeated regulator/interpolator calls the same
+//      way, Sec. 5.3.2), plus the FP32 mirror of the tables;
+//   2. main: persistent CTAs walk work items (external point x chunk of
+//      radial rows); tables are staged into shared memory by a TMA bulk copy
+//      (cp.async.bulk + mbarrier, bounded wait); threads take angular rows,
+//      accumulate in FP64 (FP64 path) or sum a row in FP32 and add it into an
+//      FP64 accumulator (mixed path); a warp-shuffle + shared-memory tree
+//      writes one partial per item;
+//   3. finalize: fixed-order sum of the partials of each external point, the
+//      overall normalisation, and a non-finite check into the status word.
+// The reduction order depends only on the problem shape, never on the grid
+// size or on other work in flight.
+#include <math.h>
+
+#include <algorithm>
+
+#include "ffrg_internal.cuh"
+
+namespace ffrg {
+
+// FP64 propagator with the FP64 global table: the near-pole path of the
+// mixed kernels.
+__device__ __forceinline__ double prop_fp64_global(const RhsArgs &a, const double *zrow, double s2, double om2,
+                                                   double m2, double k2, double inv_k2) {
+  s2 = fmax(s2, 0.0);
+  double Z = lerp(zrow, s2, a.x_min2, a.u_scale, a.u_off, a.n_pts);
+  return 1.0 / prop_den(a.reg, Z, om2, s2, m2, k2, inv_k2);
+}
+
+// Inverse propagator in the kernel precision.  The FP32 version switches to
+// FP64 when m^2 cancels more than half of Z (omega^2 + s^2 + k^2 r): close to
+// the convexity pole.  `pole` recomputes G from FP64 momenta and the FP64
+// table; it is only evaluated on that rare branch.
+template <typename Pole>
+__device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double s2, double om2, double m2, double k2,
+                                           double inv_k2, Pole &&) {
+  return 1.0 / prop_den(a.reg, Z, om2, s2, m2, k2, inv_k2);
+}
+
+template <typename Pole>
+__device__ __forceinline__ float inv_prop(const RhsArgs &a, float Z, float s2, float om2, float m2, float k2,
+                                          float inv_k2, Pole &&pole) {
+  float P = Z * (om2 + s2 + k2 * reg_r(a.reg, s2 * inv_k2));
+  float D = P + m2;
+  if (D < 0.5f * P) return (float)pole();
+  return __frcp_rn(D);
+}
+
+// ---------------------------------------------------------------------------
+// 1. precompute kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool skipped(const RhsArgs &a) { return a.skip && *(volatile const int *)a.skip; }
+
+__global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
+  if (skipped(a)) return;
+  const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
+  const double L = a.qmax_over_k * k;
+  const int total = (2 * a.N + 1) * a.nr;
+  const int stride = gridDim.x * blockDim.x;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    int n = idx / a.nr - a.N, r = idx % a.nr;
+    double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q;
+    if (n == -a.N) a.radq[r] = q;
+    double F;
+    if (a.model == FFRG_MODEL_FINITE_T) {
+      int row = min(abs(n), a.n_stack - 1);
+      const double *zr = a.tab + (size_t)row * a.n_pts;
+      const double *lr = a.tab + ((size_t)a.n_stack + row) * a.n_pts;
+      int i0;
+      double wl;
+      lerp_pos(q2, a.x_min2, a.u_scale, a.u_off, a.n_pts, i0, wl);
+      double Z = lerp_at(zr, i0, wl), Lq = lerp_at(lr, i0, wl);
+      double om = 2.0 * kPi * a.T * n;
+      double G = 1.0 / prop_den(a.reg, Z, om * om, q2, m2, k2, inv_k2);
+      double dR = Z * k2 * reg_rdot(a.reg, q2 * inv_k2);
+      F = w * q2 * dR * G * G * Lq;
+    } else {
+      double Z = lerp(a.tab, q2, a.x_min2, a.u_scale, a.u_off, a.n_pts);
+      double G = 1.0 / prop_den(a.reg, Z, 0.0, q2, m2, k2, inv_k2);
+      double rd = k2 * reg_rdot(a.reg, q2 * inv_k2);
+      double dR = Z * rd;
+      double meas = (a.model == FFRG_MODEL_D4_VERTEX) ? q2 * q : q2;
+      F = w * meas * dR * G * G;
+      if (a.radD) {
+        // d F / d Z(q): dR = Z k^2 rdot, G = 1/(Z P + m^2) with P = q^2 + k^2 r
+        double P = q2 + k2 * reg_r(a.reg, q2 * inv_k2);
+        a.radD[idx] = w * meas * rd * G * G * (1.0 - 2.0 * Z * G * P);
+      }
+    }
+    a.radF[idx] = F;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.tab_count; i += stride) a.tab32[i] = (float)a.tab[i];
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of the main kernels: tables, then angle rules
+// ---------------------------------------------------------------------------
+template <typename T>
+struct SmemLayout {
+  T *tab, *c1, *s1, *w1, *c2, *w2;
+  __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
+    tab = (T *)base;
+    size_t off = ((size_t)a.tab_count * sizeof(T) + 15) & ~(size_t)15;
+    c1 = (T *)(base + off);
+    s1 = c1 + a.na1;
+    w1 = s1 + a.na1;
+    c2 = w1 + a.na1;
+    w2 = c2 + a.na2;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ const T *table_src(const RhsArgs &a);
+template <>
+__device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { return a.tab; }
+template <>
+__device__ __forceinline__ const float *table_src<float>(const RhsArgs &a) { return a.tab32; }
+
+template <typename T>
+__device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
+  bool ok = stage_to_smem<T>(S.tab, table_src<T>(a), a.tab_count, bar, a.status);
+  for (int i = threadIdx.x; i < a.na1; i += blockDim.x) {
+    double c = a.a1_x[i];
+    S.c1[i] = (T)c;
+    S.s1[i] = (T)sqrt(fmax(0.0, 1.0 - c * c));
+    S.w1[i] = (T)a.a1_w[i];
+  }
+  for (int i = threadIdx.x; i < a.na2; i += blockDim.x) {
+    S.c2[i] = (T)a.a2_x[i];
+    S.w2[i] = (T)a.a2_w[i];
+  }
+  __syncthreads();
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// 2a. d=3, T=0:  row (r, angle block): sum_j v_j G(|q+p|)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) d3_main(RhsArgs a) {
+  if (skipped(a)) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ double red[kThreads / 32];
+  SmemLayout<T> S(smem, a);
+  if (!main_prologue<T>(a, S, &bar)) return;
+  const double kd = scale_k(a), m2d = mass2(a, kd);
+  const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
+  const T xmin2 = (T)a.x_min2, us = (T)a.u_scale, uo = (T)a.u_off;
+  const int np = a.n_pts, nblk = (a.na1 + a.jb - 1) / a.jb;
+  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int e = item / a.n_chunks, c = item - e * a.n_chunks;
+    const double pd = (e < a.n_ext_p) ? ext_momentum(a, e) : 0.0;
+    const T p = (T)pd;
+    const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
+    const int rows = (o1 - o0) * nblk;
+    double acc = 0.0;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+      const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
+      const double qd = a.radq[o];
+      const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
+      T rs = 0;
+      for (int j = jb0; j < jb1; ++j) {
+        T s2 = base + tqp * S.c1[j];
+        s2 = s2 > (T)0 ? s2 : (T)0;
+        T Z = lerp(S.tab, s2, xmin2, us, uo, np);
+        auto pole = [&]() {
+          return prop_fp64_global(a, a.tab, qd * qd + pd * pd + 2.0 * qd * pd * a.a1_x[j], 0.0, m2d, kd * kd,
+                                  1.0 / (kd * kd));
+        };
+        rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, m2, k2, inv_k2, pole);
+      }
+      acc = fma(a.radF[o], (double)rs, acc);
+    }
+    double t = block_sum(acc, red);
+    if (threadIdx.x == 0) a.partial[item] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2b. d=4 vertex expansion: row (r, c1 node), inner loop over c2 nodes
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) d4_main(RhsArgs a) {
+  if (skipped(a)) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ double red[kThreads / 32];
+  SmemLayout<T> S(smem, a);
+  if (!main_prologue<T>(a, S, &bar)) return;
+  const double kd = scale_k(a), m2d = mass2(a, kd);
+  const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
+  const T xmin2 = (T)a.x_min2, us = (T)a.u_scale, uo = (T)a.u_off;
+  const T third = (T)(1.0 / 3.0);
+  const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang;
+  const T *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
+  const T sum_w2 = (T)a.sum_w2;
+  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int e = item / a.n_chunks, c = item - e * a.n_chunks;
+    int block, ip, jp = 0;
+    if (e <= np_) {
+      block = 0;
+      ip = e;
+    } else if (e < np_ + 1 + np_ * npsi) {
+      block = 1;
+      ip = (e - np_ - 1) / npsi;
+      jp = (e - np_ - 1) - ip * npsi;
+    } else {
+      block = 2;
+      ip = e - np_ - 1 - np_ * npsi;
+    }
+    const double pd = (block == 0 && ip == np_) ? 0.0 : ext_momentum(a, ip);
+    const double cpsid = block == 1 ? a.psi_x[jp] : 1.0;
+    const double spsid = sqrt(fmax(0.0, 1.0 - cpsid * cpsid));
+    const T p = (T)pd, p2 = p * p, cpsi = (T)cpsid, spsi = (T)spsid;
+    const T C2 = (T)2 * p2 * ((T)1 + cpsi);
+    const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
+    const int rows = (o1 - o0) * a.na1;
+    double acc = 0.0;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+      const int r = o0 + row / a.na1, ia = row % a.na1;
+      const double qd = a.radq[r];
+      const T q = (T)qd, q2 = q * q, qp = q * p, c1 = S.c1[ia];
+      T A2 = q2 + p2 + (T)2 * qp * c1;
+      A2 = A2 > (T)0 ? A2 : (T)0;
+      const T ZA = lerp(Zt, A2, xmin2, us, uo, np);
+      auto pole_a = [&]() {
+        const double c1d = a.a1_x[ia];
+        return prop_fp64_global(a, a.tab, qd * qd + pd * pd + 2.0 * qd * pd * c1d, 0.0, m2d, kd * kd,
+                                1.0 / (kd * kd));
+      };
+      const T GA = inv_prop(a, ZA, A2, (T)0, m2, k2, inv_k2, pole_a);
+      T v;
+      if (block == 0) {
+        const T l4 = lerp(L4, (q2 + p2) * (T)0.5, xmin2, us, uo, np);
+        const T l3 = lerp(L3, (q2 + A2 + p2) * third, xmin2, us, uo, np);
+        v = sum_w2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
+      } else if (block == 2) {
+        const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * (T)0.25, xmin2, us, uo, np);
+        v = sum_w2 * GA * l4 * l4;
+      } else {
+        const T la = lerp(L3, (q2 + A2 + p2) * third, xmin2, us, uo, np);
+        const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
+        const T sab = A2 + C2;
+        T rs = 0;
+        for (int b = 0; b < a.na2; ++b) {
+          T B2 = base - t1 - t2 * S.c2[b];
+          B2 = B2 > (T)0 ? B2 : (T)0;
+          const T ZB = lerp(Zt, B2, xmin2, us, uo, np);
+          auto pole_b = [&]() {
+            const double c1d = a.a1_x[ia], s1d = sqrt(fmax(0.0, 1.0 - c1d * c1d));
+            return prop_fp64_global(a, a.tab,
+                                    qd * qd + pd * pd - 2.0 * qd * pd * (cpsid * c1d + spsid * s1d * a.a2_x[b]),
+                                    0.0, m2d, kd * kd, 1.0 / (kd * kd));
+          };
+          const T GB = inv_prop(a, ZB, B2, (T)0, m2, k2, inv_k2, pole_b);
+          const T lb = lerp(L3, (base + B2) * third, xmin2, us, uo, np);
+          const T lc = lerp(L3, (sab + B2) * third, xmin2, us, uo, np);
+          rs += S.w2[b] * GB * lb * lc;
+        }
+        v = GA * la * rs;
+      }
+      acc = fma(a.radF[r], (double)(S.w1[ia] * v), acc);
+    }
+    double t = block_sum(acc, red);
+    if (threadIdx.x == 0) a.partial[item] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2c. finite T: row (Matsubara n, r, angle block)
+//     sum_j v_j lam(n+m, s) G(n+m, s), s = |q+p|
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ft_main(RhsArgs a) {
+  if (skipped(a)) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ double red[kThreads / 32];
+  SmemLayout<T> S(smem, a);
+  if (!main_prologue<T>(a, S, &bar)) return;
+  const double kd = scale_k(a), m2d = mass2(a, kd);
+  const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
+  const T xmin2 = (T)a.x_min2, us = (T)a.u_scale, uo = (T)a.u_off;
+  const int np = a.n_pts, nm = a.n_ext_ang, nblk = (a.na1 + a.jb - 1) / a.jb;
+  const int outer_total = (2 * a.N + 1) * a.nr;
+  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
+    const int e = item / a.n_chunks, c = item - e * a.n_chunks;
+    const int ip = e / nm, m = e - ip * nm;
+    const double pd = ext_momentum(a, ip);
+    const T p = (T)pd;
+    const int o0 = c * a.cr, o1 = min(o0 + a.cr, outer_total);
+    const int rows = (o1 - o0) * nblk;
+    double acc = 0.0;
+    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+      const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
+      const int n = o / a.nr - a.N, r = o % a.nr;
+      const int srow = min(abs(n + m), a.n_stack - 1);
+      const T *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
+      const double omd = 2.0 * kPi * a.T * (double)(n + m);
+      const T om2 = (T)(omd * omd);
+      const double qd = a.radq[r];
+      const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
+      T rs = 0;
+      for (int j = jb0; j < jb1; ++j) {
+        T s2 = base + tqp * S.c1[j];
+        s2 = s2 > (T)0 ? s2 : (T)0;
+        int i0;
+        T w;
+        lerp_pos(s2, xmin2, us, uo, np, i0, w);
+        const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
+        auto pole = [&]() {
+          return prop_fp64_global(a, a.tab + (size_t)srow * np, qd * qd + pd * pd + 2.0 * qd * pd * a.a1_x[j],
+                                  omd * omd, m2d, kd * kd, 1.0 / (kd * kd));
+        };
+        rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, m2, k2, inv_k2, pole);
+      }
+      acc = fma(a.radF[o], (double)rs, acc);
+    }
+    double t = block_sum(acc, red);
+    if (threadIdx.x == 0) a.partial[item] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. finalize: fixed-order sum over chunks, normalisation, finiteness
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(RhsArgs a) {
+  if (skipped(a)) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.n_ext) return;
+  double s = 0.0;
+  const double *pp = a.partial + (size_t)e * a.n_chunks;
+  for (int c = 0; c < a.n_chunks; ++c) s += pp[c];
+  double coef = 1.0;
+  if (a.model == FFRG_MODEL_D4_VERTEX) {
+    const int np_ = a.n_ext_p;
+    if (e > np_ && e < np_ + 1 + np_ * a.n_ext_ang) coef = 3.0;
+    else if (e >= np_ + 1 + np_ * a.n_ext_ang) coef = 1.5;
+  }
+  const double v = a.norm * coef * s;
+  a.out[e] = v;
+  if (!isfinite(v)) raise_status(a.status, kStatusNonFinite);
+}
+
+// ---------------------------------------------------------------------------
+// launch
+// ---------------------------------------------------------------------------
+template <typename K>
+static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int *grid) {
+  static const size_t kMaxSmem = 227 * 1024;
+  if (smem > kMaxSmem) {
+    ctx->last_error = "dressing tables do not fit in shared memory";
+    return FFRG_EINVAL;
+  }
+  int st = ensure_smem_limit(ctx, (const void *)kernel, smem);
+  if (st) return st;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+  if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  if (per_sm < 1) {
+    ctx->last_error = "RHS kernel cannot be resident";
+    return FFRG_EINVAL;
+  }
+  *grid = std::max(1, std::min(items, per_sm * ctx->num_sms));
+  return FFRG_OK;
+}
+
+int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s) {
+  const int pre_total = std::max((2 * a.N + 1) * a.nr, a.tab_count);
+  const int pre_blocks = std::min((pre_total + kThreads - 1) / kThreads, 4 * ctx->num_sms);
+  precompute_kernel<<<pre_blocks, kThreads, 0, s>>>(a);
+  return set_cuda_error(ctx, cudaGetLastError(), "precompute launch");
+}
+
+int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision, cudaStream_t s) {
+  Plan *pl = const_cast<Plan *>(pl_c);
+  const bool mixed = precision == FFRG_MIXED;
+  int st;
+  int &grid = mixed ? pl->grid32 : pl->grid64;
+  const size_t smem = mixed ? pl->smem32 : pl->smem64;
+  void (*kern)(RhsArgs) = nullptr;
+  switch (a.model) {
+  case FFRG_MODEL_D3: kern = mixed ? d3_main<float> : d3_main<double>; break;
+  case FFRG_MODEL_D4_VERTEX: kern = mixed ? d4_main<float> : d4_main<double>; break;
+  default: kern = mixed ? ft_main<float> : ft_main<double>; break;
+  }
+  if (grid == 0) {
+    st = persistent_grid(ctx, kern, smem, a.n_items, &grid);
+    if (st) return st;
+  }
+  const int pre_total = std::max((2 * a.N + 1) * a.nr, a.tab_count);
+  const int pre_blocks = std::min((pre_total + kThreads - 1) / kThreads, 4 * ctx->num_sms);
+  precompute_kernel<<<pre_blocks, kThreads, 0, s>>>(a);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool prof = ctx->profiling && cap == cudaStreamCaptureStatusNone &&
+                    ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
+  if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
+  kern<<<grid, kThreads, smem, s>>>(a);
+  if (prof) {
+    cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
+    ctx->prof_used++;
+  }
+  finalize_kernel<<<(a.n_ext + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+  return set_cuda_error(ctx, cudaGetLastError(), "rhs launch");
+}
+
+}  // namespace ffrg

@@ -1,0 +1,189 @@
+"""GPU parity of ffrg_rhs (through the C ABI) against the FP64 CPU oracle.
+
+FP64 path: 1e-12 relative per output (Sec. 5.3.2 quadrature, computed by the
+same discrete sums; the two sides differ only in summation order and libm vs
+CUDA rounding).  Mixed path (FP32 integrand, FP64 per-radial factors and
+cross-node accumulation): the stated bound MIXED_TOL per output.
+Small cases span several work items with ragged tails; full-size cases are
+checked on sampled external points that the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ffrg_inputs as fi
+import oracle
+from gpu_common import gpu_context, rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIXED_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gpu_context()
+    yield c
+    c.close()
+
+
+def _run(ctx, wl, k, precision, out=None):
+    import paper_2412_13043_gb300 as ffrg
+    tabs = ctx.tables(wl.problem, wl.tables)
+    o = ctx.rhs(wl.problem, tabs, k, out=out, precision=precision)
+    st = ctx.status_read()
+    res = o.cpu().numpy()
+    tabs.free()
+    assert st == ffrg.OK, ffrg.strerror(st)
+    return res
+
+
+def _check(ctx, wl, k, sel=None, mixed=True):
+    import paper_2412_13043_gb300 as ffrg
+    if sel is None:
+        ref = oracle.rhs(wl.problem, wl.tables, k)
+    else:
+        ref = oracle.rhs_subset(wl.problem, wl.tables, k, sel)
+    g64 = _run(ctx, wl, k, ffrg.FP64)
+    g64 = g64 if sel is None else g64[sel]
+    e64 = rel_err(g64, ref)
+    assert np.max(e64) < FP64_TOL, (np.max(e64), int(np.argmax(e64)))
+    if mixed:
+        g32 = _run(ctx, wl, k, ffrg.MIXED)
+        g32 = g32 if sel is None else g32[sel]
+        e32 = rel_err(g32, ref)
+        print(f"model {wl.problem.model} k={k}: fp64 max rel {np.max(e64):.2e}, mixed max rel {np.max(e32):.2e}")
+        assert np.max(e32) < MIXED_TOL, (np.max(e32), int(np.argmax(e32)))
+    return e64
+
+
+# ----------------------------------------------------------------------------- d=3
+@pytest.mark.parametrize("k", [10.0, 1.3, 0.05, 0.01])
+def test_d3_small_ragged(ctx, k):
+    wl = fi.make_d3(seed=31, n_pts=23, n_ext_p=29, n_rad=37, n_ang=13)
+    wl.problem.include_p0 = 1
+    _check(ctx, wl, k)
+
+
+def test_d3_full_size(ctx):
+    wl = fi.make_d3(seed=1)       # 64 ext x (64 radial x 32 angular)
+    for k in (10.0, 0.3, 0.01):
+        _check(ctx, wl, k)
+
+
+@pytest.mark.parametrize("n_ext_p,n_rad,n_ang", [(1, 1, 1), (1, 3, 2), (2, 1, 5), (5, 600, 3), (300, 7, 1)])
+def test_d3_degenerate_shapes(ctx, n_ext_p, n_rad, n_ang):
+    wl = fi.make_d3(seed=3, n_pts=8, n_ext_p=n_ext_p, n_rad=n_rad, n_ang=n_ang)
+    _check(ctx, wl, 2.0)
+
+
+def test_d3_momenta_outside_table_clamp(ctx):
+    wl = fi.make_d3(seed=5, n_pts=16, n_ext_p=12)
+    wl.problem.p_min, wl.problem.p_max = 1e-6, 80.0   # beyond [x_min, x_max] on both sides
+    _check(ctx, wl, 3.0)
+
+
+def test_d3_litim_closed_form_on_gpu(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    pb = fi.Problem(model=fi.MODEL_D3, n_rad=16, n_ang1=4, n_ext_p=1, include_p0=1, regulator=fi.REG_LITIM,
+                    m2_over_k2=0.5, qmax_over_k=1.0)
+    wl = fi.Workload(pb, fi.constant_tables(pb, [1.0]))
+    k = 1.7
+    exact = k ** -1 / (3 * math.pi ** 2 * 1.5 ** 3)
+    g = _run(ctx, wl, k, ffrg.FP64)
+    assert abs(g[-1] - exact) / exact < 1e-13
+
+
+def test_d3_near_pole_mixed_uses_fp64_propagator(ctx):
+    """w = m^2/k^2 -> -0.999: Z s^2 + R >= k^2, so the denominator cancels to
+    ~1e-3 k^2; the mixed path must recompute those propagators in FP64."""
+    wl = fi.make_d3(seed=9, n_pts=32, n_ext_p=16, n_rad=32, n_ang=16)
+    wl.tables[:] = 1.0                     # Z = 1 makes the pole reachable at x -> 0
+    wl.problem.m2_over_k2 = -0.999
+    _check(ctx, wl, 1.0)
+
+
+# ----------------------------------------------------------------------------- d=4
+def test_d4_small_ragged(ctx):
+    wl = fi.make_d4(seed=41, n_pts=24, n_ext_ang=3, n_rad=19, n_ang1=11, n_ang2=5)
+    for k in (10.0, 0.7, 0.01):
+        _check(ctx, wl, k)
+
+
+def test_d4_full_size_sampled(ctx):
+    wl = fi.make_d4(seed=2)       # (128+1+1024+128) ext x (128 x 64 x 16)
+    np_, npsi = wl.problem.n_ext_p, wl.problem.n_ext_ang
+    sel = [0, 37, np_ - 1, np_,                                     # Z block incl. p = 0
+           np_ + 1, np_ + 1 + 50 * npsi + 3, np_ + 1 + np_ * npsi - 1,  # lambda3 block
+           np_ + 1 + np_ * npsi, np_ + 1 + np_ * npsi + 90, 2 * np_ + np_ * npsi]  # lambda4 block
+    for k in (10.0, 0.5):
+        _check(ctx, wl, k, sel=sel)
+
+
+def test_d4_litim_closed_forms_on_gpu(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    k, M2 = 2.0, 1.0
+    pb = fi.Problem(model=fi.MODEL_D4_VERTEX, n_rad=8, n_ang1=4, n_ang2=3, n_ext_p=2, n_ext_ang=3,
+                    regulator=fi.REG_LITIM, m2_over_k2=0.5, m2_shift=M2, qmax_over_k=1.0, n_tables=3, n_pts=16,
+                    p_min=1e-200, p_max=2e-200)
+    wl = fi.Workload(pb, fi.constant_tables(pb, [1.0, 0.8, 1.3]))
+    w = 0.5 + M2 / k ** 2
+    v4 = 1.0 / (32 * math.pi ** 2)
+    ex3 = 4 * v4 * k ** 0 * 0.5 / (1 + w) ** 3
+    ex4 = 4 * v4 * k ** -2 * 0.5 / (1 + w) ** 4
+    g = _run(ctx, wl, k, ffrg.FP64)
+    np_ = pb.n_ext_p
+    blk3 = g[np_ + 1: np_ + 1 + np_ * 3]
+    blk4 = g[np_ + 1 + np_ * 3:]
+    assert np.max(np.abs(blk3 - 3 * 0.8 ** 3 * ex4)) / ex4 < 1e-13
+    assert np.max(np.abs(blk4 - 1.5 * 1.3 ** 2 * ex3)) / ex3 < 1e-13
+
+
+# ----------------------------------------------------------------------------- finite T
+def test_finite_t_small_ragged(ctx):
+    wl = fi.make_finite_t(seed=51, N=3, T=0.05, n_pts=16, n_ext_p=7, n_ext_m=4, n_rad=13, n_ang=9)
+    for k in (10.0, 0.4):
+        _check(ctx, wl, k)
+
+
+@pytest.mark.parametrize("N,T_over_kend", [(16, 0.05), (32, 0.2), (64, 1.0)])
+def test_finite_t_full_size_sampled(ctx, N, T_over_kend):
+    wl = fi.make_finite_t(seed=3, N=N, T=T_over_kend * 0.01)   # 64 |p| x 9 p0, 96 x 48 x (2N+1)
+    ne = wl.problem.n_ext()
+    sel = [0, 8, 9 * 20 + 4, 9 * 40 + 1, ne - 9, ne - 1]
+    _check(ctx, wl, 1.0, sel=sel)
+
+
+# ----------------------------------------------------------------------------- errors
+def test_nonfinite_table_sets_status(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d3(seed=1, n_pts=16, n_ext_p=8, n_rad=8, n_ang=4)
+    wl.tables[0, 0, 12] = float("nan")       # node near 1.7: reached by q in [0, 4k] at k = 1
+    tabs = ctx.tables(wl.problem, wl.tables)
+    ctx.rhs(wl.problem, tabs, 1.0)
+    assert ctx.status_read() == ffrg.ENONFINITE
+    assert ctx.status_read() == ffrg.OK           # cleared after reading
+    tabs.free()
+
+
+def test_invalid_arguments_rejected(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d3(seed=1, n_pts=16, n_ext_p=8, n_rad=8, n_ang=4)
+    tabs = ctx.tables(wl.problem, wl.tables)
+    with pytest.raises(ffrg.FfrgError) as ei:
+        ctx.rhs(wl.problem, tabs, -1.0)
+    assert ei.value.code == ffrg.EINVAL
+    bad = fi.make_d4(n_pts=16).problem          # needs 3 tables, the upload has 1
+    with pytest.raises((ffrg.FfrgError, ValueError)):
+        ctx.rhs(bad, tabs, 1.0)
+    tabs.free()
+
+
+def test_repeat_is_bitwise_deterministic(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d4(seed=4, n_pts=32, n_ext_ang=4, n_rad=24, n_ang1=16, n_ang2=8)
+    a = _run(ctx, wl, 0.9, ffrg.MIXED)
+    b = _run(ctx, wl, 0.9, ffrg.MIXED)
+    assert np.array_equal(a, b)
