@@ -173,6 +173,31 @@ FFRG_API double ffrg_evals(const ffrg_problem *pb);
 FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_dev,
              int precision, void *stream);
 
+/* ffrg_rhs for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment variant.  It suits, for example, a process
+ * whose HBM is already reserved by another allocator (a framework's caching
+ * pool), and a latency-critical loop where cudaMalloc/cudaFree would stall
+ * other streams.  It computes exactly what ffrg_rhs computes with the same
+ * kernels, but needs no context and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its scratch is one fixed 4 MiB device array inside
+ * this library.  Every GPU that loads the library holds that array until the
+ * process exits.
+ *   pb, desc: problem and table layout (as for ffrg_rhs / ffrg_tables_upload);
+ *   tables_dev: caller-owned device array of n_tables x n_stack x n_pts
+ *   doubles; out_dev: caller-owned device array of ffrg_n_ext(pb) doubles;
+ *   k, precision, stream: as for ffrg_rhs.  Runs on the current CUDA device.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory limit.  Make that
+ * first call before any stream capture.  Each call copies its quadrature
+ * rules from host memory into the array, ordered on `stream`.  All calls share the one array, which keeps the last call's contents.  Calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it: serialise them.  Errors: FFRG_EINVAL for bad arguments and for problems
+ * whose scratch exceeds 4 MiB (quadrature rules + (2N+1) n_rad factors +
+ * n_ext x chunk partials + the FP32 table copy, about 460 000 doubles);
+ * FFRG_ECUDA on a CUDA error.  Non-finite results are visible only in out_dev. */
+FFRG_API int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *desc, const double *tables_dev, double k,
+                              double *out_dev, int precision, void *stream);
+
 /* Vector-Jacobian product of ffrg_rhs with respect to the table values
  * (the paper forms Jacobians by forward-mode AD, Sec. 5.2.2; this is the
  * reverse-mode counterpart): tbar_dev[j] = sum_e gbar_dev[e] d out_e / d T_j,

@@ -78,6 +78,7 @@ _SIGS = {
     "ffrg_n_ext": (_I, [ctypes.POINTER(Problem)]),
     "ffrg_evals": (_D, [ctypes.POINTER(Problem)]),
     "ffrg_rhs": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _I, _P]),
+    "ffrg_rhs_noalloc": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(TableDesc), _P, _D, _P, _I, _P]),
     "ffrg_rhs_adjoint": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P, _I, _P]),
     "ffrg_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _I, _D, _P, ctypes.POINTER(StepOpts), _I,
                        ctypes.POINTER(FlowStats), _P]),

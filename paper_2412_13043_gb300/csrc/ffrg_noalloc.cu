@@ -1,0 +1,173 @@
+// ffrg_rhs_noalloc: the RHS of ffrg_rhs for callers that cannot allocate
+// device memory.  It runs the same kernels (precompute, main, finalize) as
+// ffrg_rhs, but all of its scratch -- quadrature rules, per-radial factors,
+// partial sums, the FP32 table mirror and a status word -- lives in one
+// file-scope device array of fixed size instead of cudaMalloc'd buffers.  No
+// context, no cudaMalloc/cudaFree, no allocating library routine.
+//
+// The array belongs to every GPU that loads this library until the process
+// exits.  Host code must not hand the array's name to a kernel: on the host it
+// is only a stand-in for the symbol.  The device address is looked up once per
+// device with cudaGetSymbolAddress (on the first call made with that device
+// current) and passed to the kernels.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "ffrg_internal.cuh"
+
+namespace ffrg {
+
+constexpr size_t kNoallocScratchBytes = size_t(4) << 20;  // 4 MiB
+constexpr int kNoallocMaxDevices = 64;
+
+// Shared by every call of ffrg_rhs_noalloc on a device; keeps the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_ptr[kNoallocMaxDevices];  // device address per device
+
+static cudaError_t noalloc_scratch_for_current_device(int dev, unsigned char **out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = (unsigned char *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+// Bump allocator over the fixed array (256-byte aligned segments).
+struct ScratchCarver {
+  unsigned char *base;
+  size_t used;
+  template <typename T>
+  T *take(size_t count) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + std::max<size_t>(count * sizeof(T), 16);
+    return (T *)(base + off);
+  }
+};
+
+}  // namespace ffrg
+
+using namespace ffrg;
+
+extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *td, const double *tables_dev,
+                                double k, double *out_dev, int precision, void *stream) {
+  if (!pb || !td || !tables_dev || !out_dev) return FFRG_EINVAL;
+  if (!(k > 0.0) || !isfinite(k)) return FFRG_EINVAL;
+  if (precision != FFRG_FP64 && precision != FFRG_MIXED) return FFRG_EINVAL;
+  if (validate_problem(pb, td) != FFRG_OK) return FFRG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FFRG_ECUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return FFRG_EINVAL;
+  unsigned char *base = nullptr;
+  if (noalloc_scratch_for_current_device(dev, &base) != cudaSuccess) return FFRG_ECUDA;
+
+  // Launch geometry: the same grouping of angular rows into work items as the
+  // cached plans of ffrg_rhs use.
+  Plan pl = Plan();
+  pl.model = pb->model;
+  pl.nr = pb->n_rad;
+  pl.na1 = pb->n_ang1;
+  pl.na2 = pb->model == FFRG_MODEL_D4_VERTEX ? pb->n_ang2 : 1;
+  pl.n_ext_ang = pb->n_ext_ang;
+  pl.n_ext_p = pb->n_ext_p;
+  pl.N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
+  pl.include_p0 = pb->include_p0;
+  pl.n_ext = ffrg_n_ext(pb);
+  pl.n_tables = td->n_tables;
+  pl.n_stack = td->n_stack;
+  pl.n_pts = td->n_pts;
+  pl.tab_count = td->n_tables * td->n_stack * td->n_pts;
+  int outer_total, rows_per_outer;
+  if (pb->model == FFRG_MODEL_D4_VERTEX) {
+    pl.jb = pl.na2;
+    outer_total = pl.nr;
+    rows_per_outer = pl.na1;
+  } else {
+    pl.jb = std::min(pl.na1, 8);
+    outer_total = pl.nr * (2 * pl.N + 1);
+    rows_per_outer = (pl.na1 + pl.jb - 1) / pl.jb;
+  }
+  pl.cr = std::min(std::max(1, (2 * kThreads + rows_per_outer - 1) / rows_per_outer), outer_total);
+  pl.n_chunks = (outer_total + pl.cr - 1) / pl.cr;
+  pl.n_items = pl.n_ext * pl.n_chunks;
+
+  // quadrature rules on the host
+  std::vector<double> rx(pl.nr), rw(pl.nr), x1(pl.na1), w1(pl.na1), x2(pl.na2), w2(pl.na2);
+  int npsi = std::max(1, pl.n_ext_ang);
+  std::vector<double> xp(npsi), wp(npsi);
+  host_gauss_legendre(pl.nr, 0.0, 1.0, rx.data(), rw.data());
+  if (pb->model == FFRG_MODEL_D4_VERTEX) host_gauss_chebyshev2(pl.na1, x1.data(), w1.data());
+  else host_gauss_legendre(pl.na1, -1.0, 1.0, x1.data(), w1.data());
+  host_gauss_legendre(pl.na2, -1.0, 1.0, x2.data(), w2.data());
+  host_gauss_legendre(npsi, -1.0, 1.0, xp.data(), wp.data());
+  pl.sum_w2 = 0.0;
+  for (double v : w2) pl.sum_w2 += v;
+
+  // carve the fixed array; reject problems that do not fit
+  ScratchCarver sc{base, 0};
+  unsigned *status = sc.take<unsigned>(4);
+  pl.rad_x = sc.take<double>(pl.nr);
+  pl.rad_w = sc.take<double>(pl.nr);
+  pl.a1_x = sc.take<double>(pl.na1);
+  pl.a1_w = sc.take<double>(pl.na1);
+  pl.a2_x = sc.take<double>(pl.na2);
+  pl.a2_w = sc.take<double>(pl.na2);
+  pl.psi_x = sc.take<double>(npsi);
+  pl.psi_w = sc.take<double>(npsi);
+  pl.radF = sc.take<double>((size_t)pl.nr * (2 * pl.N + 1));
+  pl.radq = sc.take<double>(pl.nr);
+  pl.partial = sc.take<double>(pl.n_items);
+  pl.tab32 = sc.take<float>((size_t)pl.tab_count + 4);
+  if (sc.used > kNoallocScratchBytes) return FFRG_EINVAL;  // problem needs more than the 4 MiB scratch
+
+  auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  size_t ang = (size_t)pl.na1 * 3 + (size_t)pl.na2 * 2;
+  const bool mixed = precision == FFRG_MIXED;
+  const size_t smem = mixed ? al16((size_t)pl.tab_count * 4) + al16(ang * 4)
+                            : al16((size_t)pl.tab_count * 8) + al16(ang * 8);
+  if (smem > 227 * 1024) return FFRG_EINVAL;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t db = sizeof(double);
+  cudaError_t e = cudaMemsetAsync(status, 0, 4 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.rad_x, rx.data(), pl.nr * db, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.rad_w, rw.data(), pl.nr * db, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.a1_x, x1.data(), pl.na1 * db, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.a1_w, w1.data(), pl.na1 * db, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.a2_x, x2.data(), pl.na2 * db, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.a2_w, w2.data(), pl.na2 * db, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.psi_x, xp.data(), npsi * db, cudaMemcpyHostToDevice, s);
+  // copies from pageable host memory return once the source has been staged,
+  // so the host vectors may go out of scope afterwards
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pl.psi_w, wp.data(), npsi * db, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return FFRG_ECUDA;
+
+  // a context-free stand-in for the launch helpers (no device memory behind it)
+  ffrg_ctx lc;
+  lc.device = dev;
+  lc.budget = 0;
+  lc.used = 0;
+  lc.status_dev = status;
+  lc.status_host = nullptr;
+  lc.profiling = 0;
+  lc.prof_used = 0;
+  if (cudaDeviceGetAttribute(&lc.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FFRG_ECUDA;
+  pl.smem64 = al16((size_t)pl.tab_count * 8) + al16(ang * 8);
+  pl.smem32 = al16((size_t)pl.tab_count * 4) + al16(ang * 4);
+  pl.grid64 = 0;
+  pl.grid32 = 0;
+  RhsArgs a;
+  fill_args(&pl, pb, td, tables_dev, k, a);
+  a.out = out_dev;
+  a.status = status;
+  return launch_rhs(&lc, &pl, a, precision, s);
+}
