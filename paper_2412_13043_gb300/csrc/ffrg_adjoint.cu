@@ -48,7 +48,7 @@ struct LerpPos {
 
 __device__ __forceinline__ LerpPos pos_of(const RhsArgs &a, double s2) {
   LerpPos p;
-  lerp_pos(s2, a.x_min2, a.u_scale, a.u_off, a.n_pts, p.i0, p.w);
+  lerp_pos(s2, a.u_scale, a.u_off, a.n_pts, p.i0, p.w);
   return p;
 }
 __device__ __forceinline__ double val_at(const double *t, LerpPos p) { return lerp_at(t, p.i0, p.w); }

@@ -173,7 +173,7 @@ static int upload_rule(ffrg_ctx *ctx, const std::vector<double> &h, double **d) 
 static void plan_free(ffrg_ctx *ctx, Plan *pl) {
   if (!pl) return;
   double *arrs[] = {pl->rad_x, pl->rad_w, pl->a1_x, pl->a1_w, pl->a2_x, pl->a2_w, pl->psi_x, pl->psi_w,
-                    pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart};
+                    pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s};
   for (double *p : arrs) dev_free(ctx, p, 0);
   dev_free(ctx, pl->tab32, 0);
   delete pl;
@@ -248,6 +248,8 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   size_t nF = (size_t)pl->nr * (2 * pl->N + 1);
   if (!st) st = dev_alloc(ctx, (void **)&pl->radF, nF * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq, pl->nr * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->partial, (size_t)pl->n_items * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->tab32, ((size_t)pl->tab_count + 4) * sizeof(float));
   if (st) {
@@ -257,8 +259,8 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
   auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
-  pl->smem64 = al16((size_t)pl->tab_count * 8) + al16(ang * 8);
-  pl->smem32 = al16((size_t)pl->tab_count * 4) + al16(ang * 4);
+  pl->smem64 = al16(((size_t)pl->tab_count + 1) * 8) + al16(ang * 8);
+  pl->smem32 = al16(((size_t)pl->tab_count + 1) * 4) + al16(ang * 4);
   *out = pl;
   ctx->plans[key] = pl;
   return FFRG_OK;
@@ -314,6 +316,8 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.psi_x = pl->psi_x;
   a.radF = pl->radF;
   a.radq = pl->radq;
+  a.ext_pd = pl->ext_pd;
+  a.psi_s = pl->psi_s;
   a.partial = pl->partial;
 }
 
@@ -360,7 +364,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
   for (auto &kv : ctx->plans) {
     Plan *pl = kv.second;
     double *arrs[] = {pl->rad_x, pl->rad_w, pl->a1_x, pl->a1_w, pl->a2_x, pl->a2_w, pl->psi_x, pl->psi_w,
-                      pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart};
+                      pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s};
     for (double *p : arrs) cudaFree(p);
     cudaFree(pl->tab32);
     delete pl;

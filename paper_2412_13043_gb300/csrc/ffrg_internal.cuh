@@ -44,7 +44,7 @@ struct RhsArgs {
   double qmax_over_k;
   double norm;                 // overall factor applied in finalize
   double u_scale, u_off;       // u = u_scale ln(s^2) + u_off
-  double x_min2;               // lookups clamp s^2 below x_min^2
+  double x_min2;               // x_min^2 (lookups below x_min return the first node)
   double sum_w2;               // sum of the second-angle weights (D4)
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
   float *tab32;                // FP32 mirror written by the precompute kernel
@@ -58,6 +58,8 @@ struct RhsArgs {
   double *radD;                // optional: d radF / d Z(q) (adjoint)
   double *radF;                // per-(n, r) factor
   double *radq;                // per-r momentum q
+  double *ext_pd;              // per external |p| index: p_i (written by the precompute kernel)
+  double *psi_s;               // per external angle: sin(psi) (D4)
   double *partial;             // [n_ext][n_chunks]
   double *out;                 // [n_ext]
   unsigned *status;
@@ -83,20 +85,46 @@ __device__ __forceinline__ double reg_rdot(int reg, double x) {
   return 2.0 * x * x * exp(-x) / (em * em);
 }
 
+// Hardware special-function instructions (PTX ISA: lg2/ex2/rcp .approx.ftz.f32).
+__device__ __forceinline__ float hw_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float hw_ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float hw_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// FP32 regulator shape.  Exponential r(x) = x/(e^x - 1): for x < 1 the
+// Bernoulli series sum_n B_n x^n / n! through x^8 (1 - x/2 + x^2/12 - x^4/720
+// + x^6/30240 - x^8/1209600; the first omitted term x^10/47900160 is below
+// 2.1e-8); for 1 <= x <= 80, x / (2^(x log2 e) - 1) with the hardware exp2 and
+// reciprocal; above 80 the shape is below 1e-33 and is taken as 0.
 __device__ __forceinline__ float reg_r(int reg, float x) {
   if (reg == FFRG_REG_LITIM) return x < 1.f ? 1.f - x : 0.f;
-  if (x > 80.f) return 0.f;
-  if (x < 1e-30f) return 1.f;
-  return x / expm1f(x);
+  const float x2 = x * x;
+  float t = fmaf(x2, -1.0f / 1209600.0f, 1.0f / 30240.0f);
+  t = fmaf(x2, t, -1.0f / 720.0f);
+  t = fmaf(x2, t, 1.0f / 12.0f);
+  const float series = fmaf(x2, t, fmaf(x, -0.5f, 1.0f));
+  const float direct = x * hw_rcp(hw_ex2(x * 1.4426950408889634f) - 1.0f);
+  const float r = x < 1.0f ? series : direct;
+  return x > 80.f ? 0.f : r;
 }
 
 // ---------------------------------------------------------------------------
 // Log-grid lookup: u = (n-1) ln(s/x_min)/ln(x_max/x_min) = u_scale ln(s^2) + u_off,
 // clamped to [0, n-1]; linear in the value between nodes.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void lerp_pos(double s2, double x_min2, double u_scale, double u_off, int n, int &i0,
-                                         double &w) {
-  double u = u_scale * log(fmax(s2, x_min2)) + u_off;
+__device__ __forceinline__ void lerp_pos(double s2, double u_scale, double u_off, int n, int &i0, double &w) {
+  double u = u_scale * log(s2) + u_off;
   u = fmin(fmax(u, 0.0), (double)(n - 1));
   int i = (int)u;
   i = min(i, n - 2);
@@ -104,14 +132,31 @@ __device__ __forceinline__ void lerp_pos(double s2, double x_min2, double u_scal
   w = u - (double)i;
 }
 
-__device__ __forceinline__ void lerp_pos(float s2, float x_min2, float u_scale, float u_off, int n, int &i0,
-                                         float &w) {
-  float u = u_scale * __logf(fmaxf(s2, x_min2)) + u_off;
+// FP32 coordinate: u_scale here multiplies log2(s^2) (the caller folds ln 2 in,
+// see lerp_scale).  s^2 <= 0 gives log2 = -inf or NaN, both clamped to u = 0
+// (the table's first node, as for s < x_min).  floor(u) comes from adding
+// 1.5*2^23 rounded towards -inf: the sum's low mantissa bits hold floor(u); no
+// float<->int conversion instructions are needed.  At u = n-1 this gives
+// i0 = n-1, w = 0: the FP32 tables in shared memory carry one zero element
+// after the last value so that the (zero-weighted) upper neighbour is finite.
+__device__ __forceinline__ void lerp_pos(float s2, float u_scale, float u_off, int n, int &i0, float &w) {
+  float u = fmaf(u_scale, hw_lg2(s2), u_off);
   u = fminf(fmaxf(u, 0.f), (float)(n - 1));
-  int i = (int)u;
-  i = min(i, n - 2);
-  i0 = i;
-  w = u - (float)i;
+  const float magic = 12582912.0f;
+  const float t = __fadd_rd(u, magic);
+  i0 = __float_as_int(t) - 0x4B400000;
+  w = u - (t - magic);
+}
+
+// Scale of the table coordinate for each precision: ln(s^2) for FP64,
+// log2(s^2) for FP32 (factor ln 2 folded in).
+template <typename T>
+__device__ __forceinline__ T lerp_scale(double u_scale);
+template <>
+__device__ __forceinline__ double lerp_scale<double>(double u_scale) { return u_scale; }
+template <>
+__device__ __forceinline__ float lerp_scale<float>(double u_scale) {
+  return (float)(u_scale * 0.6931471805599453094);
 }
 
 template <typename T>
@@ -121,10 +166,10 @@ __device__ __forceinline__ T lerp_at(const T *tab, int i0, T w) {
 }
 
 template <typename T>
-__device__ __forceinline__ T lerp(const T *tab, T s2, T x_min2, T u_scale, T u_off, int n) {
+__device__ __forceinline__ T lerp(const T *tab, T s2, T u_scale, T u_off, int n) {
   int i0;
   T w;
-  lerp_pos(s2, x_min2, u_scale, u_off, n, i0, w);
+  lerp_pos(s2, u_scale, u_off, n, i0, w);
   return lerp_at(tab, i0, w);
 }
 
@@ -274,7 +319,7 @@ struct Plan {
   size_t smem64, smem32;    // dynamic shared memory bytes
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;
   double sum_w2;
-  double *radF, *radq, *partial;
+  double *radF, *radq, *partial, *ext_pd, *psi_s;
   float *tab32;
   double *radD, *gpart;     // adjoint scratch (allocated on first use)
   int adj_grid;

@@ -27,19 +27,63 @@
 
 namespace ffrg {
 
-// FP64 propagator with the FP64 global table: the near-pole path of the
-// mixed kernels.
+// FP64 propagator with the FP64 global table.
 __device__ __forceinline__ double prop_fp64_global(const RhsArgs &a, const double *zrow, double s2, double om2,
                                                    double m2, double k2, double inv_k2) {
   s2 = fmax(s2, 0.0);
-  double Z = lerp(zrow, s2, a.x_min2, a.u_scale, a.u_off, a.n_pts);
+  double Z = lerp(zrow, s2, a.u_scale, a.u_off, a.n_pts);
   return 1.0 / prop_den(a.reg, Z, om2, s2, m2, k2, inv_k2);
+}
+
+// Near-pole path of the mixed kernels: recompute one propagator entirely in
+// FP64 (momenta from the quadrature indices, Z from the FP64 table).  Kept out
+// of line so that none of it is evaluated on the common path.
+__device__ __noinline__ float pole_prop(const RhsArgs *a, const double *zrow, double s2, double om2) {
+  const double k = scale_k(*a), k2 = k * k;
+  return (float)prop_fp64_global(*a, zrow, s2, om2, mass2(*a, k), k2, 1.0 / k2);
+}
+
+__device__ __noinline__ float pole_d3(const RhsArgs *a, int e, int r, int j) {
+  const double p = (e < a->n_ext_p) ? ext_momentum(*a, e) : 0.0;
+  const double q = a->radq[r], c = a->a1_x[j];
+  return pole_prop(a, a->tab, q * q + p * p + 2.0 * q * p * c, 0.0);
+}
+
+// b < 0: the |q + p1| leg; b >= 0: the |q - p2| leg at second-angle node b
+__device__ __noinline__ float pole_d4(const RhsArgs *a, int e, int r, int ia, int b) {
+  const int np_ = a->n_ext_p, npsi = a->n_ext_ang;
+  int ip, jp = 0;
+  bool three = false;
+  if (e <= np_) ip = e;
+  else if (e < np_ + 1 + np_ * npsi) {
+    three = true;
+    ip = (e - np_ - 1) / npsi;
+    jp = (e - np_ - 1) - ip * npsi;
+  } else ip = e - np_ - 1 - np_ * npsi;
+  const double p = (e == np_) ? 0.0 : ext_momentum(*a, ip);
+  const double q = a->radq[r], c1 = a->a1_x[ia];
+  double s2;
+  if (b < 0) {
+    s2 = q * q + p * p + 2.0 * q * p * c1;
+  } else {
+    const double cpsi = three ? a->psi_x[jp] : 1.0, spsi = sqrt(fmax(0.0, 1.0 - cpsi * cpsi));
+    const double s1 = sqrt(fmax(0.0, 1.0 - c1 * c1));
+    s2 = q * q + p * p - 2.0 * q * p * (cpsi * c1 + spsi * s1 * a->a2_x[b]);
+  }
+  return pole_prop(a, a->tab, s2, 0.0);
+}
+
+__device__ __noinline__ float pole_ft(const RhsArgs *a, int e, int n, int r, int j) {
+  const int nm = a->n_ext_ang, ip = e / nm, m = e - ip * nm;
+  const double p = ext_momentum(*a, ip), q = a->radq[r], c = a->a1_x[j];
+  const int srow = min(abs(n + m), a->n_stack - 1);
+  const double om = 2.0 * kPi * a->T * (double)(n + m);
+  return pole_prop(a, a->tab + (size_t)srow * a->n_pts, q * q + p * p + 2.0 * q * p * c, om * om);
 }
 
 // Inverse propagator in the kernel precision.  The FP32 version switches to
 // FP64 when m^2 cancels more than half of Z (omega^2 + s^2 + k^2 r): close to
-// the convexity pole.  `pole` recomputes G from FP64 momenta and the FP64
-// table; it is only evaluated on that rare branch.
+// the convexity pole.  `pole` is only evaluated on that rare branch.
 template <typename Pole>
 __device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double s2, double om2, double m2, double k2,
                                            double inv_k2, Pole &&) {
@@ -49,11 +93,22 @@ __device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double s2
 template <typename Pole>
 __device__ __forceinline__ float inv_prop(const RhsArgs &a, float Z, float s2, float om2, float m2, float k2,
                                           float inv_k2, Pole &&pole) {
-  float P = Z * (om2 + s2 + k2 * reg_r(a.reg, s2 * inv_k2));
-  float D = P + m2;
-  if (D < 0.5f * P) return (float)pole();
-  return __frcp_rn(D);
+  const float P = Z * (om2 + s2 + k2 * reg_r(a.reg, s2 * inv_k2));
+  const float D = P + m2;
+  if (D < 0.5f * P) return pole();
+  return hw_rcp(D);
 }
+
+// resident CTAs per SM requested from the compiler: the FP32 kernels are held
+// to 64 registers so that four 256-thread CTAs fit
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = 1;
+};
+template <>
+struct MinBlocks<float> {
+  static constexpr int value = 4;
+};
 
 // ---------------------------------------------------------------------------
 // 1. precompute kernel
@@ -77,14 +132,14 @@ __global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
       const double *lr = a.tab + ((size_t)a.n_stack + row) * a.n_pts;
       int i0;
       double wl;
-      lerp_pos(q2, a.x_min2, a.u_scale, a.u_off, a.n_pts, i0, wl);
+      lerp_pos(q2, a.u_scale, a.u_off, a.n_pts, i0, wl);
       double Z = lerp_at(zr, i0, wl), Lq = lerp_at(lr, i0, wl);
       double om = 2.0 * kPi * a.T * n;
       double G = 1.0 / prop_den(a.reg, Z, om * om, q2, m2, k2, inv_k2);
       double dR = Z * k2 * reg_rdot(a.reg, q2 * inv_k2);
       F = w * q2 * dR * G * G * Lq;
     } else {
-      double Z = lerp(a.tab, q2, a.x_min2, a.u_scale, a.u_off, a.n_pts);
+      double Z = lerp(a.tab, q2, a.u_scale, a.u_off, a.n_pts);
       double G = 1.0 / prop_den(a.reg, Z, 0.0, q2, m2, k2, inv_k2);
       double rd = k2 * reg_rdot(a.reg, q2 * inv_k2);
       double dR = Z * rd;
@@ -99,17 +154,26 @@ __global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
     a.radF[idx] = F;
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.tab_count; i += stride) a.tab32[i] = (float)a.tab[i];
+  // per-external-point constants used by every work item of the main kernels
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
+  if (a.model == FFRG_MODEL_D4_VERTEX) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n_ext_ang; j += stride) {
+      const double c = a.psi_x[j];
+      a.psi_s[j] = sqrt(fmax(0.0, 1.0 - c * c));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
-// shared-memory layout of the main kernels: tables, then angle rules
+// shared-memory layout of the main kernels: tables (+ one zero element read
+// with weight 0 by lookups at the last node), then angle rules
 // ---------------------------------------------------------------------------
 template <typename T>
 struct SmemLayout {
   T *tab, *c1, *s1, *w1, *c2, *w2;
   __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
     tab = (T *)base;
-    size_t off = ((size_t)a.tab_count * sizeof(T) + 15) & ~(size_t)15;
+    size_t off = ((size_t)(a.tab_count + 1) * sizeof(T) + 15) & ~(size_t)15;
     c1 = (T *)(base + off);
     s1 = c1 + a.na1;
     w1 = s1 + a.na1;
@@ -128,6 +192,7 @@ __device__ __forceinline__ const float *table_src<float>(const RhsArgs &a) { ret
 template <typename T>
 __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
   bool ok = stage_to_smem<T>(S.tab, table_src<T>(a), a.tab_count, bar, a.status);
+  if (threadIdx.x == 0) S.tab[a.tab_count] = (T)0;
   for (int i = threadIdx.x; i < a.na1; i += blockDim.x) {
     double c = a.a1_x[i];
     S.c1[i] = (T)c;
@@ -146,20 +211,22 @@ __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar)
 // 2a. d=3, T=0:  row (r, angle block): sum_j v_j G(|q+p|)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) d3_main(RhsArgs a) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d3_main(RhsArgs a) {
   if (skipped(a)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ double red[kThreads / 32];
+  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
+  if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
   const double kd = scale_k(a), m2d = mass2(a, kd);
   const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
-  const T xmin2 = (T)a.x_min2, us = (T)a.u_scale, uo = (T)a.u_off;
+  const T us = lerp_scale<T>(a.u_scale), uo = (T)a.u_off;
   const int np = a.n_pts, nblk = (a.na1 + a.jb - 1) / a.jb;
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int e = item / a.n_chunks, c = item - e * a.n_chunks;
-    const double pd = (e < a.n_ext_p) ? ext_momentum(a, e) : 0.0;
+    const double pd = (e < a.n_ext_p) ? a.ext_pd[e] : 0.0;
     const T p = (T)pd;
     const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
     const int rows = (o1 - o0) * nblk;
@@ -170,13 +237,9 @@ __global__ void __launch_bounds__(kThreads) d3_main(RhsArgs a) {
       const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
       T rs = 0;
       for (int j = jb0; j < jb1; ++j) {
-        T s2 = base + tqp * S.c1[j];
-        s2 = s2 > (T)0 ? s2 : (T)0;
-        T Z = lerp(S.tab, s2, xmin2, us, uo, np);
-        auto pole = [&]() {
-          return prop_fp64_global(a, a.tab, qd * qd + pd * pd + 2.0 * qd * pd * a.a1_x[j], 0.0, m2d, kd * kd,
-                                  1.0 / (kd * kd));
-        };
+        const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
+        T Z = lerp(S.tab, s2, us, uo, np);
+        auto pole = [&]() { return pole_d3(&sa, e, o, j); };
         rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, m2, k2, inv_k2, pole);
       }
       acc = fma(a.radF[o], (double)rs, acc);
@@ -190,17 +253,22 @@ __global__ void __launch_bounds__(kThreads) d3_main(RhsArgs a) {
 // 2b. d=4 vertex expansion: row (r, c1 node), inner loop over c2 nodes
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) d4_main(RhsArgs a) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs a) {
   if (skipped(a)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ double red[kThreads / 32];
+  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
+  if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
   const double kd = scale_k(a), m2d = mass2(a, kd);
   const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
-  const T xmin2 = (T)a.x_min2, us = (T)a.u_scale, uo = (T)a.u_off;
-  const T third = (T)(1.0 / 3.0);
+  const T us = lerp_scale<T>(a.u_scale), uo = (T)a.u_off;
+  // S0^2 = (sum of squares)/c: the 1/c is a shift of the coordinate, -u_scale ln c
+  const T uo2 = (T)(a.u_off - a.u_scale * 0.69314718055994530942);
+  const T uo3 = (T)(a.u_off - a.u_scale * 1.09861228866810969140);
+  const T uo4 = (T)(a.u_off - a.u_scale * 1.38629436111989061883);
   const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang;
   const T *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
   const T sum_w2 = (T)a.sum_w2;
@@ -218,9 +286,9 @@ __global__ void __launch_bounds__(kThreads) d4_main(RhsArgs a) {
       block = 2;
       ip = e - np_ - 1 - np_ * npsi;
     }
-    const double pd = (block == 0 && ip == np_) ? 0.0 : ext_momentum(a, ip);
+    const double pd = (block == 0 && ip == np_) ? 0.0 : a.ext_pd[ip];
     const double cpsid = block == 1 ? a.psi_x[jp] : 1.0;
-    const double spsid = sqrt(fmax(0.0, 1.0 - cpsid * cpsid));
+    const double spsid = block == 1 ? a.psi_s[jp] : 0.0;
     const T p = (T)pd, p2 = p * p, cpsi = (T)cpsid, spsi = (T)spsid;
     const T C2 = (T)2 * p2 * ((T)1 + cpsi);
     const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
@@ -230,41 +298,30 @@ __global__ void __launch_bounds__(kThreads) d4_main(RhsArgs a) {
       const int r = o0 + row / a.na1, ia = row % a.na1;
       const double qd = a.radq[r];
       const T q = (T)qd, q2 = q * q, qp = q * p, c1 = S.c1[ia];
-      T A2 = q2 + p2 + (T)2 * qp * c1;
-      A2 = A2 > (T)0 ? A2 : (T)0;
-      const T ZA = lerp(Zt, A2, xmin2, us, uo, np);
-      auto pole_a = [&]() {
-        const double c1d = a.a1_x[ia];
-        return prop_fp64_global(a, a.tab, qd * qd + pd * pd + 2.0 * qd * pd * c1d, 0.0, m2d, kd * kd,
-                                1.0 / (kd * kd));
-      };
+      const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
+      const T ZA = lerp(Zt, A2, us, uo, np);
+      auto pole_a = [&]() { return pole_d4(&sa, e, r, ia, -1); };
       const T GA = inv_prop(a, ZA, A2, (T)0, m2, k2, inv_k2, pole_a);
       T v;
       if (block == 0) {
-        const T l4 = lerp(L4, (q2 + p2) * (T)0.5, xmin2, us, uo, np);
-        const T l3 = lerp(L3, (q2 + A2 + p2) * third, xmin2, us, uo, np);
+        const T l4 = lerp(L4, q2 + p2, us, uo2, np);
+        const T l3 = lerp(L3, q2 + A2 + p2, us, uo3, np);
         v = sum_w2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
       } else if (block == 2) {
-        const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * (T)0.25, xmin2, us, uo, np);
+        const T l4 = lerp(L4, q2 + A2 + (T)2 * p2, us, uo4, np);
         v = sum_w2 * GA * l4 * l4;
       } else {
-        const T la = lerp(L3, (q2 + A2 + p2) * third, xmin2, us, uo, np);
+        const T la = lerp(L3, q2 + A2 + p2, us, uo3, np);
         const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
         const T sab = A2 + C2;
         T rs = 0;
         for (int b = 0; b < a.na2; ++b) {
-          T B2 = base - t1 - t2 * S.c2[b];
-          B2 = B2 > (T)0 ? B2 : (T)0;
-          const T ZB = lerp(Zt, B2, xmin2, us, uo, np);
-          auto pole_b = [&]() {
-            const double c1d = a.a1_x[ia], s1d = sqrt(fmax(0.0, 1.0 - c1d * c1d));
-            return prop_fp64_global(a, a.tab,
-                                    qd * qd + pd * pd - 2.0 * qd * pd * (cpsid * c1d + spsid * s1d * a.a2_x[b]),
-                                    0.0, m2d, kd * kd, 1.0 / (kd * kd));
-          };
+          const T B2 = base - t1 - t2 * S.c2[b];
+          const T ZB = lerp(Zt, B2, us, uo, np);
+          auto pole_b = [&]() { return pole_d4(&sa, e, r, ia, b); };
           const T GB = inv_prop(a, ZB, B2, (T)0, m2, k2, inv_k2, pole_b);
-          const T lb = lerp(L3, (base + B2) * third, xmin2, us, uo, np);
-          const T lc = lerp(L3, (sab + B2) * third, xmin2, us, uo, np);
+          const T lb = lerp(L3, base + B2, us, uo3, np);
+          const T lc = lerp(L3, sab + B2, us, uo3, np);
           rs += S.w2[b] * GB * lb * lc;
         }
         v = GA * la * rs;
@@ -281,22 +338,24 @@ __global__ void __launch_bounds__(kThreads) d4_main(RhsArgs a) {
 //     sum_j v_j lam(n+m, s) G(n+m, s), s = |q+p|
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreads) ft_main(RhsArgs a) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ft_main(RhsArgs a) {
   if (skipped(a)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ double red[kThreads / 32];
+  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
+  if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
   const double kd = scale_k(a), m2d = mass2(a, kd);
   const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
-  const T xmin2 = (T)a.x_min2, us = (T)a.u_scale, uo = (T)a.u_off;
+  const T us = lerp_scale<T>(a.u_scale), uo = (T)a.u_off;
   const int np = a.n_pts, nm = a.n_ext_ang, nblk = (a.na1 + a.jb - 1) / a.jb;
   const int outer_total = (2 * a.N + 1) * a.nr;
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int e = item / a.n_chunks, c = item - e * a.n_chunks;
     const int ip = e / nm, m = e - ip * nm;
-    const double pd = ext_momentum(a, ip);
+    const double pd = a.ext_pd[ip];
     const T p = (T)pd;
     const int o0 = c * a.cr, o1 = min(o0 + a.cr, outer_total);
     const int rows = (o1 - o0) * nblk;
@@ -312,16 +371,12 @@ __global__ void __launch_bounds__(kThreads) ft_main(RhsArgs a) {
       const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
       T rs = 0;
       for (int j = jb0; j < jb1; ++j) {
-        T s2 = base + tqp * S.c1[j];
-        s2 = s2 > (T)0 ? s2 : (T)0;
+        const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
         int i0;
         T w;
-        lerp_pos(s2, xmin2, us, uo, np, i0, w);
+        lerp_pos(s2, us, uo, np, i0, w);
         const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
-        auto pole = [&]() {
-          return prop_fp64_global(a, a.tab + (size_t)srow * np, qd * qd + pd * pd + 2.0 * qd * pd * a.a1_x[j],
-                                  omd * omd, m2d, kd * kd, 1.0 / (kd * kd));
-        };
+        auto pole = [&]() { return pole_ft(&sa, e, n, r, j); };
         rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, m2, k2, inv_k2, pole);
       }
       acc = fma(a.radF[o], (double)rs, acc);
