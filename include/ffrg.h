@@ -73,7 +73,8 @@ typedef enum {
   FFRG_EPENDING = 7,        /* serving: request not finished yet */
   FFRG_EBUSY = 8,           /* serving: queue full */
   FFRG_ECUDA = 9,           /* a CUDA runtime call failed (see ffrg_last_error) */
-  FFRG_ENOTFOUND = 10       /* serving: unknown ticket */
+  FFRG_ENOTFOUND = 10,      /* serving: unknown ticket */
+  FFRG_ECANCELED = 11       /* serving: request cancelled before it finished */
 } ffrg_status;
 
 typedef enum { FFRG_FP64 = 0, FFRG_MIXED = 1 } ffrg_precision;
@@ -236,6 +237,51 @@ FFRG_API int ffrg_flow_state_size(const ffrg_problem *pb, const ffrg_table_desc 
  * clears the record.  Enabling clears it too. */
 FFRG_API int ffrg_set_profiling(ffrg_ctx *ctx, int enable);
 FFRG_API int ffrg_profile_read(ffrg_ctx *ctx, double *main_ms, long long *launches);
+
+/* ---- Serving: continuous batching of flow requests (one GPU) ----
+ * A scheduler thread keeps up to max_slots flows resident on the device
+ * (tables, DP5(4) state and RHS scratch of each), advances all of them one
+ * adaptive step per tick with batched launches (one persistent integrand
+ * launch per model over every resident flow's work items), retires finished
+ * flows and admits queued requests as soon as a slot and enough of
+ * hbm_budget_bytes are free.  Requests: frozen-background flows
+ * (feedback = 0) of FFRG_MODEL_D3 and FFRG_MODEL_FINITE_T, mixed precision
+ * (FP32 integrand, FP64 accumulation and step control).  A flow's result does
+ * not depend on which other flows share its launches. */
+typedef struct {
+  int max_slots;            /* resident flows at once, 1..256 */
+  int max_queue;            /* queued requests before submit returns FFRG_EBUSY */
+  size_t hbm_budget_bytes;  /* device memory for resident flows (0: 1 GiB) */
+} ffrg_serve_opts;
+
+typedef struct {
+  long long submitted, admitted, completed, cancelled, rejected;
+  long long ticks;          /* batched steps launched */
+  int resident, queued, peak_resident, reserved0;
+  size_t hbm_in_use;        /* bytes held by resident slots */
+} ffrg_serve_stats;
+
+/* Start the server of a context (one per context).  FFRG_EBUSY if running. */
+FFRG_API int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts);
+/* Queue one flow request; inputs are copied (host pointers): tables_host
+ * (desc layout), y0_host (ffrg_n_ext doubles), Lambda and the step options
+ * (t in t_+).  *ticket identifies it.  FFRG_EBUSY: queue full; FFRG_ENOMEM:
+ * the request alone exceeds the HBM budget; FFRG_EINVAL: unsupported request. */
+FFRG_API int ffrg_serve_submit(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *desc,
+                               const double *tables_host, const double *y0_host, double Lambda,
+                               const ffrg_step_opts *opts, unsigned long long *ticket);
+/* FFRG_EPENDING while queued or resident.  When finished: the flow's status
+ * (FFRG_OK, FFRG_ESTEP_UNDERFLOW, FFRG_EMAXSTEPS, FFRG_ENONFINITE or
+ * FFRG_ECANCELED), result_host (ffrg_n_ext doubles, may be NULL), stats and
+ * latency_s (submit to completion, may be NULL) are filled and the ticket is
+ * released.  FFRG_ENOTFOUND for unknown tickets. */
+FFRG_API int ffrg_serve_poll(ffrg_ctx *ctx, unsigned long long ticket, double *result_host, ffrg_flow_stats *stats,
+                             double *latency_s);
+/* Cancel a queued or resident request (it finishes with FFRG_ECANCELED). */
+FFRG_API int ffrg_serve_cancel(ffrg_ctx *ctx, unsigned long long ticket);
+FFRG_API int ffrg_serve_get_stats(ffrg_ctx *ctx, ffrg_serve_stats *out);
+/* Stop the scheduler: resident and queued requests finish with FFRG_ECANCELED. */
+FFRG_API int ffrg_serve_stop(ffrg_ctx *ctx);
 
 /* Wait for the stream and return (then clear) the device status word:
  * FFRG_OK, FFRG_ENONFINITE or FFRG_ETIMEOUT; FFRG_ECUDA on a CUDA error. */

@@ -17,7 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libffrg.so")
 
-OK, EINVAL, ENOMEM, ENONFINITE, ESTEP_UNDERFLOW, EMAXSTEPS, ETIMEOUT, EPENDING, EBUSY, ECUDA, ENOTFOUND = range(11)
+(OK, EINVAL, ENOMEM, ENONFINITE, ESTEP_UNDERFLOW, EMAXSTEPS, ETIMEOUT, EPENDING, EBUSY, ECUDA, ENOTFOUND,
+ ECANCELED) = range(12)
 FP64, MIXED = 0, 1
 RULE_GL, RULE_GC2 = 0, 1
 MODEL_D3, MODEL_D4_VERTEX, MODEL_FINITE_T = 1, 2, 3
@@ -61,6 +62,18 @@ class FlowStats(ctypes.Structure):
                 ("integrand_evals", ctypes.c_double), ("t_reached", ctypes.c_double)]
 
 
+class ServeOpts(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("admitted", ctypes.c_longlong),
+                ("completed", ctypes.c_longlong), ("cancelled", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("ticks", ctypes.c_longlong),
+                ("resident", ctypes.c_int), ("queued", ctypes.c_int), ("peak_resident", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("hbm_in_use", ctypes.c_size_t)]
+
+
 _lib = None
 
 # name -> (restype, argtypes)
@@ -86,6 +99,13 @@ _SIGS = {
     "ffrg_status_read": (_I, [_P, _P]),
     "ffrg_set_profiling": (_I, [_P, _I]),
     "ffrg_profile_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong)]),
+    "ffrg_serve_start": (_I, [_P, ctypes.POINTER(ServeOpts)]),
+    "ffrg_serve_submit": (_I, [_P, ctypes.POINTER(Problem), ctypes.POINTER(TableDesc), _P, _P, _D,
+                               ctypes.POINTER(StepOpts), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "ffrg_serve_poll": (_I, [_P, ctypes.c_ulonglong, _P, ctypes.POINTER(FlowStats), ctypes.POINTER(_D)]),
+    "ffrg_serve_cancel": (_I, [_P, ctypes.c_ulonglong]),
+    "ffrg_serve_get_stats": (_I, [_P, ctypes.POINTER(ServeStats)]),
+    "ffrg_serve_stop": (_I, [_P]),
     "ffrg_strerror": (ctypes.c_char_p, [_I]),
     "ffrg_last_error": (ctypes.c_char_p, [_P]),
 }
@@ -306,6 +326,48 @@ class Context:
             _check(self.handle, code, "ffrg_flow")
         return dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals,
                     integrand_evals=st.integrand_evals, t_reached=st.t_reached, status=code)
+
+    # ---- serving (continuous batching of flow requests) ----
+    def serve_start(self, max_slots: int = 64, max_queue: int = 4096, hbm_budget_bytes: int = 0):
+        o = ServeOpts(max_slots, max_queue, hbm_budget_bytes)
+        _check(self.handle, load().ffrg_serve_start(self.handle, ctypes.byref(o)), "ffrg_serve_start")
+
+    def serve_submit(self, pb, tables, y0, Lambda: float, t1: float, t0: float = 0.0, dt0: float = 1e-3,
+                     dt_min: float = 1e-10, dt_max: float = 0.5, atol: float = 1e-14, rtol: float = 1e-11,
+                     max_steps: int = 1_000_000) -> int:
+        """Queue a frozen-background flow request; returns its ticket (inputs are copied)."""
+        t = np.ascontiguousarray(np.asarray(tables, dtype=np.float64))
+        y = np.ascontiguousarray(np.asarray(y0, dtype=np.float64))
+        c, d = to_problem(pb), to_desc(pb)
+        o = StepOpts(t0, t1, dt0, dt_min, dt_max, atol, rtol, max_steps)
+        tk = ctypes.c_ulonglong()
+        code = load().ffrg_serve_submit(self.handle, ctypes.byref(c), ctypes.byref(d), t.ctypes.data, y.ctypes.data,
+                                        float(Lambda), ctypes.byref(o), ctypes.byref(tk))
+        _check(self.handle, code, "ffrg_serve_submit")
+        return tk.value
+
+    def serve_poll(self, ticket: int, n_out: int):
+        """(status, result or None, stats dict, latency_s); status EPENDING while running."""
+        out = np.empty(n_out)
+        st = FlowStats()
+        lat = _D()
+        code = load().ffrg_serve_poll(self.handle, ticket, out.ctypes.data, ctypes.byref(st), ctypes.byref(lat))
+        if code == EPENDING:
+            return code, None, None, None
+        stats = dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals,
+                     integrand_evals=st.integrand_evals, t_reached=st.t_reached)
+        return code, (out if code in (OK,) else None), stats, lat.value
+
+    def serve_cancel(self, ticket: int) -> int:
+        return load().ffrg_serve_cancel(self.handle, ticket)
+
+    def serve_stats(self) -> dict:
+        s = ServeStats()
+        _check(self.handle, load().ffrg_serve_get_stats(self.handle, ctypes.byref(s)), "ffrg_serve_get_stats")
+        return {name: getattr(s, name) for name, _ in ServeStats._fields_ if name != "reserved0"}
+
+    def serve_stop(self) -> int:
+        return load().ffrg_serve_stop(self.handle)
 
     def set_profiling(self, enable: bool) -> None:
         _check(self.handle, load().ffrg_set_profiling(self.handle, int(bool(enable))), "ffrg_set_profiling")

@@ -343,6 +343,7 @@ int ffrg_create(ffrg_ctx **out, int device, size_t hbm_budget_bytes) {
   ctx->used = 0;
   ctx->status_dev = nullptr;
   ctx->status_host = nullptr;
+  ctx->server = nullptr;
   ctx->profiling = 0;
   ctx->prof_used = 0;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -359,6 +360,7 @@ int ffrg_create(ffrg_ctx **out, int device, size_t hbm_budget_bytes) {
 
 int ffrg_destroy(ffrg_ctx *ctx) {
   if (!ctx) return FFRG_EINVAL;
+  if (ctx->server) ffrg_serve_stop(ctx);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   for (auto &kv : ctx->plans) {
@@ -534,6 +536,7 @@ const char *ffrg_strerror(int status) {
   case FFRG_EBUSY: return "busy";
   case FFRG_ECUDA: return "CUDA error";
   case FFRG_ENOTFOUND: return "unknown ticket";
+  case FFRG_ECANCELED: return "request cancelled";
   default: return "unknown status";
   }
 }

@@ -37,23 +37,6 @@ __constant__ double kDpE[7] = {35.0 / 384.0 - 5179.0 / 57600.0,
                                11.0 / 84.0 - 187.0 / 2100.0,
                                -1.0 / 40.0};
 
-struct FlowCtl {
-  double t, dt, h, t0, t1, dt_min, dt_max, atol, rtol, end_tol, Lambda;
-  double k_stage, m2_stage, err;
-  long long steps, rejects, max_steps;
-  int last_rejected, done, status, pad;
-};
-
-struct FlowArgs {
-  int ny, mode;       // mode: 0 frozen, 1 D3 feedback, 2 D4 feedback
-  int n, npsi;        // table points / external angles (feedback)
-  int tab_off, tab_len;
-  double p_min, p_step;
-  const double *psi_w;
-  double *y, *ys, *K, *raw, *tabbuf;
-  FlowCtl *ctl;
-};
-
 enum { kModeFrozen = 0, kModeD3Feedback = 1, kModeD4Feedback = 2 };
 
 __device__ __forceinline__ double ext_p(const FlowArgs &f, int i) { return f.p_min * exp((double)i * f.p_step); }
@@ -92,20 +75,20 @@ __device__ __forceinline__ void write_stage_state(const FlowArgs &f, int s, int 
   if (i == 0 && f.mode == kModeD3Feedback) f.ctl->m2_stage = v;
 }
 
-__global__ void flow_prep_kernel(FlowArgs f, int s) {
+__device__ __forceinline__ void flow_prep_body(const FlowArgs &f, int s, int i) {
   const FlowCtl *c = f.ctl;
   if (*(volatile const int *)&c->done) return;
   const double h = c->h;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) f.ctl->k_stage = c->Lambda * exp(-(c->t + kDpC[s] * h));
   if (i < f.ny) write_stage_state(f, s, i, h);
 }
 
+__global__ void flow_prep_kernel(FlowArgs f, int s) { flow_prep_body(f, s, blockIdx.x * blockDim.x + threadIdx.x); }
+
 // K_s from the RHS, then (s < 6) the state of stage s+1.
-__global__ void flow_deriv_kernel(FlowArgs f, int s) {
+__device__ __forceinline__ void flow_deriv_body(const FlowArgs &f, int s, int i) {
   const FlowCtl *c = f.ctl;
   if (*(volatile const int *)&c->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double h = c->h;
   if (i < f.ny) f.K[(size_t)s * f.ny + i] = deriv_component(f, i);
   if (s >= 1 && s < 6) {
@@ -113,6 +96,8 @@ __global__ void flow_deriv_kernel(FlowArgs f, int s) {
     if (i < f.ny) write_stage_state(f, s + 1, i, h);
   }
 }
+
+__global__ void flow_deriv_kernel(FlowArgs f, int s) { flow_deriv_body(f, s, blockIdx.x * blockDim.x + threadIdx.x); }
 
 __device__ __forceinline__ void decide_next_step(FlowCtl *c) {
   const double remaining = c->t1 - c->t;
@@ -134,7 +119,7 @@ __global__ void flow_start_kernel(FlowCtl *c) {
 
 // Error norm max_i |h sum_r E_r K_r,i| / (atol + rtol max(|y_i|, |y5_i|)),
 // accept / reject, step-size update (same controller as the CPU oracle).
-__global__ void __launch_bounds__(1024) flow_control_kernel(FlowArgs f) {
+__device__ __forceinline__ void flow_control_body(const FlowArgs &f) {
   FlowCtl *c = f.ctl;
   __shared__ double red[32];
   __shared__ int bad_s[32];
@@ -206,6 +191,60 @@ __global__ void __launch_bounds__(1024) flow_control_kernel(FlowArgs f) {
   }
   __syncthreads();
   if (threadIdx.x == 0 && !c->done) decide_next_step(c);
+}
+
+__global__ void __launch_bounds__(1024) flow_control_kernel(FlowArgs f) { flow_control_body(f); }
+
+// ---------------------------------------------------------------------------
+// Batched DP5(4) steps of many flows (serving): blockIdx.y (or blockIdx.x for
+// the control kernel) selects the flow; each flow keeps its own control block,
+// so flows at different times, step sizes and stages advance independently.
+// ---------------------------------------------------------------------------
+__global__ void batched_flow_prep_kernel(const FlowArgs *fa, int s) {
+  const FlowArgs &f = fa[blockIdx.y];
+  flow_prep_body(f, s, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void batched_flow_deriv_kernel(const FlowArgs *fa, int s) {
+  const FlowArgs &f = fa[blockIdx.y];
+  flow_deriv_body(f, s, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(1024) batched_flow_control_kernel(const FlowArgs *fa) {
+  flow_control_body(fa[blockIdx.x]);
+}
+
+__global__ void batched_flow_start_kernel(const FlowArgs *fa, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !fa[i].ctl->done) decide_next_step(fa[i].ctl);
+}
+
+// First derivative (first-same-as-last stage 0) and the first step size.
+int launch_flow_batched_init(ffrg_ctx *ctx, const FlowArgs *fa, int n, int max_ny, const BatchList &bl,
+                             cudaStream_t st) {
+  if (n == 0) return FFRG_OK;
+  const dim3 g((max_ny + 255) / 256, n);
+  batched_flow_prep_kernel<<<g, 256, 0, st>>>(fa, 0);
+  int rc = launch_rhs_batched(ctx, bl, st);
+  if (rc) return rc;
+  batched_flow_deriv_kernel<<<g, 256, 0, st>>>(fa, 0);
+  batched_flow_start_kernel<<<(n + 255) / 256, 256, 0, st>>>(fa, n);
+  return set_cuda_error(ctx, cudaGetLastError(), "batched flow init");
+}
+
+// One adaptive step of every flow in the batch (finished flows skip).
+int launch_flow_batched_step(ffrg_ctx *ctx, const FlowArgs *fa, int n, int max_ny, const BatchList &bl,
+                             cudaStream_t st) {
+  if (n == 0) return FFRG_OK;
+  const dim3 g((max_ny + 255) / 256, n);
+  batched_flow_prep_kernel<<<g, 256, 0, st>>>(fa, 1);
+  for (int s = 1; s <= 6; ++s) {
+    int rc = launch_rhs_batched(ctx, bl, st);
+    if (rc) return rc;
+    batched_flow_deriv_kernel<<<g, 256, 0, st>>>(fa, s);
+  }
+  batched_flow_control_kernel<<<n, 1024, 0, st>>>(fa);
+  return set_cuda_error(ctx, cudaGetLastError(), "batched flow step");
 }
 
 static int flow_mode(const ffrg_problem *pb, int feedback) {

@@ -300,6 +300,7 @@ struct ffrg_ctx {
   std::string last_error;
   std::map<std::vector<long long>, ffrg::Plan *> plans;
   std::vector<void *> owned;  // misc allocations freed at destroy
+  void *server;  // ffrg::Server while serving
   int profiling;
   std::vector<cudaEvent_t> prof_events;  // start/stop pairs
   int prof_used;                         // pairs recorded
@@ -330,6 +331,44 @@ struct Plan {
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
 // lowers it: plans of different sizes share the kernel).
 int ensure_smem_limit(ffrg_ctx *ctx, const void *func, size_t bytes);
+
+// Several flows' RHS in one set of launches (serving).  Descriptors live in
+// device memory; work items of the flows of one model are numbered
+// consecutively (flow f owns items start[f] .. start[f+1]-1).
+struct BatchList {
+  const RhsArgs *descs;          // [n_flows], device
+  int n_flows;
+  const int *d3_flows, *d3_start;  // device: indices into descs, cumulative items (n_d3 + 1)
+  int n_d3, d3_items;
+  const int *ft_flows, *ft_start;
+  int n_ft, ft_items;
+  int max_ext, max_pre;          // largest n_ext and precompute range among the flows
+  size_t smem_d3, smem_ft;       // largest shared-memory need per model (FP32 path)
+};
+int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s);
+
+// Device control block and argument block of one DP5(4) flow.
+struct FlowCtl {
+  double t, dt, h, t0, t1, dt_min, dt_max, atol, rtol, end_tol, Lambda;
+  double k_stage, m2_stage, err;
+  long long steps, rejects, max_steps;
+  int last_rejected, done, status, pad;
+};
+
+struct FlowArgs {
+  int ny, mode;       // mode: 0 frozen, 1 D3 feedback, 2 D4 feedback
+  int n, npsi;        // table points / external angles (feedback)
+  int tab_off, tab_len;
+  double p_min, p_step;
+  const double *psi_w;
+  double *y, *ys, *K, *raw, *tabbuf;
+  FlowCtl *ctl;
+};
+
+int launch_flow_batched_init(ffrg_ctx *ctx, const FlowArgs *fa, int n_flows, int max_ny, const BatchList &bl,
+                             cudaStream_t s);
+int launch_flow_batched_step(ffrg_ctx *ctx, const FlowArgs *fa, int n_flows, int max_ny, const BatchList &bl,
+                             cudaStream_t s);
 
 // helpers implemented in ffrg_api.cu
 int set_cuda_error(ffrg_ctx *ctx, cudaError_t e, const char *what);

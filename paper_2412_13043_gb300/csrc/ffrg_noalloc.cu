@@ -160,6 +160,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   lc.used = 0;
   lc.status_dev = status;
   lc.status_host = nullptr;
+  lc.server = nullptr;
   lc.profiling = 0;
   lc.prof_used = 0;
   if (cudaDeviceGetAttribute(&lc.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FFRG_ECUDA;

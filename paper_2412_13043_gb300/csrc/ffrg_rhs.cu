@@ -115,13 +115,11 @@ struct MinBlocks<float> {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool skipped(const RhsArgs &a) { return a.skip && *(volatile const int *)a.skip; }
 
-__global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
-  if (skipped(a)) return;
+__device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int stride) {
   const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
   const double L = a.qmax_over_k * k;
   const int total = (2 * a.N + 1) * a.nr;
-  const int stride = gridDim.x * blockDim.x;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+  for (int idx = tid0; idx < total; idx += stride) {
     int n = idx / a.nr - a.N, r = idx % a.nr;
     double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q;
     if (n == -a.N) a.radq[r] = q;
@@ -153,15 +151,20 @@ __global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
     }
     a.radF[idx] = F;
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.tab_count; i += stride) a.tab32[i] = (float)a.tab[i];
+  for (int i = tid0; i < a.tab_count; i += stride) a.tab32[i] = (float)a.tab[i];
   // per-external-point constants used by every work item of the main kernels
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
+  for (int i = tid0; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
   if (a.model == FFRG_MODEL_D4_VERTEX) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n_ext_ang; j += stride) {
+    for (int j = tid0; j < a.n_ext_ang; j += stride) {
       const double c = a.psi_x[j];
       a.psi_s[j] = sqrt(fmax(0.0, 1.0 - c * c));
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
+  if (skipped(a)) return;
+  precompute_body(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -207,9 +210,57 @@ __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar)
   return ok;
 }
 
+// Scale-dependent constants of one RHS in the kernel precision (computed once
+// per kernel, or per flow in the batched kernels).
+template <typename T>
+struct KConst {
+  T k2, inv_k2, m2, us, uo;
+};
+
+template <typename T>
+__device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
+  const double kd = scale_k(a), m2d = mass2(a, kd);
+  KConst<T> c;
+  c.k2 = (T)(kd * kd);
+  c.inv_k2 = (T)(1.0 / (kd * kd));
+  c.m2 = (T)m2d;
+  c.us = lerp_scale<T>(a.u_scale);
+  c.uo = (T)a.u_off;
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // 2a. d=3, T=0:  row (r, angle block): sum_j v_j G(|q+p|)
+// One work item: partial sum of external point e over a chunk of radial rows
+// (returned in thread 0).  `sa` is the argument block the near-pole path reads.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ double d3_item(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                          const KConst<T> &kc, int item, double *red) {
+  const T k2 = kc.k2, inv_k2 = kc.inv_k2, m2 = kc.m2, us = kc.us, uo = kc.uo;
+  const int np = a.n_pts, nblk = (a.na1 + a.jb - 1) / a.jb;
+  const int e = item / a.n_chunks, c = item - e * a.n_chunks;
+  const double pd = (e < a.n_ext_p) ? a.ext_pd[e] : 0.0;
+  const T p = (T)pd;
+  const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
+  const int rows = (o1 - o0) * nblk;
+  double acc = 0.0;
+  for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+    const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
+    const double qd = a.radq[o];
+    const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
+    T rs = 0;
+    for (int j = jb0; j < jb1; ++j) {
+      const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
+      T Z = lerp(S.tab, s2, us, uo, np);
+      auto pole = [&]() { return pole_d3(sa, e, o, j); };
+      rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, m2, k2, inv_k2, pole);
+    }
+    acc = fma(a.radF[o], (double)rs, acc);
+  }
+  return block_sum(acc, red);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d3_main(RhsArgs a) {
   if (skipped(a)) return;
@@ -220,31 +271,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d3_main(RhsArgs
   if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
-  const double kd = scale_k(a), m2d = mass2(a, kd);
-  const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
-  const T us = lerp_scale<T>(a.u_scale), uo = (T)a.u_off;
-  const int np = a.n_pts, nblk = (a.na1 + a.jb - 1) / a.jb;
+  const KConst<T> kc = make_kconst<T>(a);
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    const int e = item / a.n_chunks, c = item - e * a.n_chunks;
-    const double pd = (e < a.n_ext_p) ? a.ext_pd[e] : 0.0;
-    const T p = (T)pd;
-    const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
-    const int rows = (o1 - o0) * nblk;
-    double acc = 0.0;
-    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-      const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
-      const double qd = a.radq[o];
-      const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
-      T rs = 0;
-      for (int j = jb0; j < jb1; ++j) {
-        const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
-        T Z = lerp(S.tab, s2, us, uo, np);
-        auto pole = [&]() { return pole_d3(&sa, e, o, j); };
-        rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, m2, k2, inv_k2, pole);
-      }
-      acc = fma(a.radF[o], (double)rs, acc);
-    }
-    double t = block_sum(acc, red);
+    double t = d3_item<T>(a, &sa, S, kc, item, red);
     if (threadIdx.x == 0) a.partial[item] = t;
   }
 }
@@ -338,6 +367,43 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
 //     sum_j v_j lam(n+m, s) G(n+m, s), s = |q+p|
 // ---------------------------------------------------------------------------
 template <typename T>
+__device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                          const KConst<T> &kc, int item, double *red) {
+  const T k2 = kc.k2, inv_k2 = kc.inv_k2, m2 = kc.m2, us = kc.us, uo = kc.uo;
+  const int np = a.n_pts, nm = a.n_ext_ang, nblk = (a.na1 + a.jb - 1) / a.jb;
+  const int outer_total = (2 * a.N + 1) * a.nr;
+  const int e = item / a.n_chunks, c = item - e * a.n_chunks;
+  const int ip = e / nm, m = e - ip * nm;
+  const double pd = a.ext_pd[ip];
+  const T p = (T)pd;
+  const int o0 = c * a.cr, o1 = min(o0 + a.cr, outer_total);
+  const int rows = (o1 - o0) * nblk;
+  double acc = 0.0;
+  for (int row = threadIdx.x; row < rows; row += blockDim.x) {
+    const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
+    const int n = o / a.nr - a.N, r = o % a.nr;
+    const int srow = min(abs(n + m), a.n_stack - 1);
+    const T *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
+    const double omd = 2.0 * kPi * a.T * (double)(n + m);
+    const T om2 = (T)(omd * omd);
+    const double qd = a.radq[r];
+    const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
+    T rs = 0;
+    for (int j = jb0; j < jb1; ++j) {
+      const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
+      int i0;
+      T w;
+      lerp_pos(s2, us, uo, np, i0, w);
+      const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
+      auto pole = [&]() { return pole_ft(sa, e, n, r, j); };
+      rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, m2, k2, inv_k2, pole);
+    }
+    acc = fma(a.radF[o], (double)rs, acc);
+  }
+  return block_sum(acc, red);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ft_main(RhsArgs a) {
   if (skipped(a)) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -347,41 +413,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ft_main(RhsArgs
   if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
-  const double kd = scale_k(a), m2d = mass2(a, kd);
-  const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
-  const T us = lerp_scale<T>(a.u_scale), uo = (T)a.u_off;
-  const int np = a.n_pts, nm = a.n_ext_ang, nblk = (a.na1 + a.jb - 1) / a.jb;
-  const int outer_total = (2 * a.N + 1) * a.nr;
+  const KConst<T> kc = make_kconst<T>(a);
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    const int e = item / a.n_chunks, c = item - e * a.n_chunks;
-    const int ip = e / nm, m = e - ip * nm;
-    const double pd = a.ext_pd[ip];
-    const T p = (T)pd;
-    const int o0 = c * a.cr, o1 = min(o0 + a.cr, outer_total);
-    const int rows = (o1 - o0) * nblk;
-    double acc = 0.0;
-    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-      const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
-      const int n = o / a.nr - a.N, r = o % a.nr;
-      const int srow = min(abs(n + m), a.n_stack - 1);
-      const T *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
-      const double omd = 2.0 * kPi * a.T * (double)(n + m);
-      const T om2 = (T)(omd * omd);
-      const double qd = a.radq[r];
-      const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
-      T rs = 0;
-      for (int j = jb0; j < jb1; ++j) {
-        const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
-        int i0;
-        T w;
-        lerp_pos(s2, us, uo, np, i0, w);
-        const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
-        auto pole = [&]() { return pole_ft(&sa, e, n, r, j); };
-        rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, m2, k2, inv_k2, pole);
-      }
-      acc = fma(a.radF[o], (double)rs, acc);
-    }
-    double t = block_sum(acc, red);
+    double t = ft_item<T>(a, &sa, S, kc, item, red);
     if (threadIdx.x == 0) a.partial[item] = t;
   }
 }
@@ -389,9 +423,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ft_main(RhsArgs
 // ---------------------------------------------------------------------------
 // 3. finalize: fixed-order sum over chunks, normalisation, finiteness
 // ---------------------------------------------------------------------------
-__global__ void finalize_kernel(RhsArgs a) {
-  if (skipped(a)) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void finalize_body(const RhsArgs &a, int e) {
   if (e >= a.n_ext) return;
   double s = 0.0;
   const double *pp = a.partial + (size_t)e * a.n_chunks;
@@ -405,6 +437,11 @@ __global__ void finalize_kernel(RhsArgs a) {
   const double v = a.norm * coef * s;
   a.out[e] = v;
   if (!isfinite(v)) raise_status(a.status, kStatusNonFinite);
+}
+
+__global__ void finalize_kernel(RhsArgs a) {
+  if (skipped(a)) return;
+  finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -468,6 +505,106 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision,
   }
   finalize_kernel<<<(a.n_ext + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
   return set_cuda_error(ctx, cudaGetLastError(), "rhs launch");
+}
+
+}  // namespace ffrg
+
+// ---------------------------------------------------------------------------
+// Batched RHS of many flows (serving, mixed precision): the same item
+// functions as the single-flow kernels, driven by per-flow descriptors.
+// ---------------------------------------------------------------------------
+namespace ffrg {
+
+__global__ void __launch_bounds__(kThreads) batched_precompute_kernel(const RhsArgs *descs) {
+  const RhsArgs &a = descs[blockIdx.y];
+  if (skipped(a)) return;
+  precompute_body(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+__global__ void batched_finalize_kernel(const RhsArgs *descs) {
+  const RhsArgs &a = descs[blockIdx.y];
+  if (skipped(a)) return;
+  finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Each CTA walks a contiguous range of the combined item list; when the range
+// crosses into another flow it copies that flow's descriptor and FP32 tables
+// into shared memory (plain loads) before continuing.
+template <int MODEL>
+__global__ void __launch_bounds__(kThreads, 4)
+    batched_main_kernel(const RhsArgs *descs, const int *flows, const int *start, int n_fl, int total, int per) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double red[kThreads / 32];
+  __shared__ RhsArgs sa;
+  const int g0 = blockIdx.x * per, g1 = min(g0 + per, total);
+  int cur = -1, lo = 0, hi = 0;
+  SmemLayout<float> S(smem, descs[flows[0]]);
+  KConst<float> kc;
+  bool skip = false;
+  for (int g = g0; g < g1; ++g) {
+    if (g >= hi) {  // next flow: find f with start[f] <= g < start[f+1]
+      int f = (cur < 0) ? 0 : cur + 1;
+      while (f < n_fl && start[f + 1] <= g) ++f;
+      cur = f;
+      lo = start[f];
+      hi = start[f + 1];
+      __syncthreads();
+      if (threadIdx.x == 0) sa = descs[flows[f]];
+      __syncthreads();
+      skip = sa.skip && *(volatile const int *)sa.skip;
+      if (!skip) {
+        S = SmemLayout<float>(smem, sa);
+        for (int i = threadIdx.x; i < sa.tab_count; i += blockDim.x) S.tab[i] = sa.tab32[i];
+        if (threadIdx.x == 0) S.tab[sa.tab_count] = 0.f;
+        for (int i = threadIdx.x; i < sa.na1; i += blockDim.x) {
+          const double c = sa.a1_x[i];
+          S.c1[i] = (float)c;
+          S.s1[i] = (float)sqrt(fmax(0.0, 1.0 - c * c));
+          S.w1[i] = (float)sa.a1_w[i];
+        }
+        for (int i = threadIdx.x; i < sa.na2; i += blockDim.x) {
+          S.c2[i] = (float)sa.a2_x[i];
+          S.w2[i] = (float)sa.a2_w[i];
+        }
+        kc = make_kconst<float>(sa);
+      }
+      __syncthreads();
+    }
+    if (skip) continue;
+    const int item = g - lo;
+    double t = (MODEL == FFRG_MODEL_D3) ? d3_item<float>(sa, &sa, S, kc, item, red)
+                                        : ft_item<float>(sa, &sa, S, kc, item, red);
+    if (threadIdx.x == 0) sa.partial[item] = t;
+  }
+}
+
+template <int MODEL>
+static int launch_batched_main(ffrg_ctx *ctx, const BatchList &bl, const int *flows, const int *start, int n,
+                               int total, size_t smem, cudaStream_t s) {
+  if (n == 0 || total == 0) return FFRG_OK;
+  void (*kern)(const RhsArgs *, const int *, const int *, int, int, int) = batched_main_kernel<MODEL>;
+  int st = ensure_smem_limit(ctx, (const void *)kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
+  const int grid = std::max(1, std::min(total, per_sm * ctx->num_sms));
+  const int per = (total + grid - 1) / grid;
+  kern<<<(total + per - 1) / per, kThreads, smem, s>>>(bl.descs, flows, start, n, total, per);
+  return FFRG_OK;
+}
+
+int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s) {
+  if (bl.n_flows == 0) return FFRG_OK;
+  const int pre_blocks = std::max(1, std::min((bl.max_pre + kThreads - 1) / kThreads, 64));
+  batched_precompute_kernel<<<dim3(pre_blocks, bl.n_flows), kThreads, 0, s>>>(bl.descs);
+  int st = launch_batched_main<FFRG_MODEL_D3>(ctx, bl, bl.d3_flows, bl.d3_start, bl.n_d3, bl.d3_items,
+                                              bl.smem_d3, s);
+  if (!st) st = launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl, bl.ft_flows, bl.ft_start, bl.n_ft, bl.ft_items,
+                                                         bl.smem_ft, s);
+  if (st) return st;
+  batched_finalize_kernel<<<dim3((bl.max_ext + kThreads - 1) / kThreads, bl.n_flows), kThreads, 0, s>>>(bl.descs);
+  return set_cuda_error(ctx, cudaGetLastError(), "batched rhs launch");
 }
 
 }  // namespace ffrg

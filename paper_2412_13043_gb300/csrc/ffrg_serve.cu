@@ -1,0 +1,656 @@
+// Serving: continuous batching of RG-flow requests on one GPU.
+//
+// A scheduler thread owns up to max_slots device-resident flows ("slots").
+// Each slot holds its request's dressing tables, its DP5(4) state and its own
+// RHS scratch.  Every tick advances all resident flows by one adaptive step
+// with batched launches (one precompute, one persistent integrand launch per
+// model over the combined work list, one finalize and one derivative kernel
+// per stage, one control kernel with a CTA per flow).  Flows retire when
+// their control block says done; queued requests are admitted as soon as a
+// slot and enough of the HBM budget are free, so new flows join while others
+// are mid-flight.  Each flow's reductions and step control depend only on its
+// own data, so its result does not depend on what it is batched with.
+//
+// Requests: frozen-background flows (d_t y = -Flow, Sec. 5.2.2 Eqs. assVar /
+// flowVar) of the d=3 and finite-T models, mixed precision.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "ffrg_internal.cuh"
+
+namespace ffrg {
+
+using Clock = std::chrono::steady_clock;
+
+enum { kQueued = 0, kResident = 1, kDone = 2 };
+
+struct ServeReq {
+  unsigned long long id;
+  ffrg_problem pb;
+  ffrg_table_desc td;
+  ffrg_step_opts opts;
+  double Lambda;
+  std::vector<double> tab, y0, result;
+  int state = kQueued;
+  int status = FFRG_OK;
+  bool cancel = false;
+  ffrg_flow_stats stats{};
+  double latency = 0.0;
+  Clock::time_point t_submit;
+  size_t need = 0;   // device bytes while resident
+  int ny = 0;
+};
+
+// Geometry and device layout of one resident flow (segments of one buffer).
+struct SlotLayout {
+  Plan pl;
+  int ny, npsi;
+  size_t bytes;
+  size_t o_tab, o_tab32, o_y, o_ys, o_K, o_raw, o_radF, o_radq, o_extp, o_psis, o_part;
+  size_t o_rx, o_rw, o_a1x, o_a1w, o_a2x, o_a2w, o_psx, o_psw;
+};
+
+static size_t seg(size_t &used, size_t bytes) {
+  size_t off = (used + 255) & ~(size_t)255;
+  used = off + std::max<size_t>(bytes, 16);
+  return off;
+}
+
+static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotLayout &L) {
+  Plan &pl = L.pl;
+  pl = Plan();
+  pl.model = pb->model;
+  pl.nr = pb->n_rad;
+  pl.na1 = pb->n_ang1;
+  pl.na2 = 1;
+  pl.n_ext_ang = pb->n_ext_ang;
+  pl.n_ext_p = pb->n_ext_p;
+  pl.N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
+  pl.include_p0 = pb->include_p0;
+  pl.n_ext = ffrg_n_ext(pb);
+  pl.n_tables = td->n_tables;
+  pl.n_stack = td->n_stack;
+  pl.n_pts = td->n_pts;
+  pl.tab_count = td->n_tables * td->n_stack * td->n_pts;
+  pl.jb = std::min(pl.na1, 8);
+  const int outer_total = pl.nr * (2 * pl.N + 1);
+  const int rows_per_outer = (pl.na1 + pl.jb - 1) / pl.jb;
+  pl.cr = std::min(std::max(1, (2 * kThreads + rows_per_outer - 1) / rows_per_outer), outer_total);
+  pl.n_chunks = (outer_total + pl.cr - 1) / pl.cr;
+  pl.n_items = pl.n_ext * pl.n_chunks;
+  pl.sum_w2 = 2.0;
+  L.ny = pl.n_ext;
+  L.npsi = std::max(1, pl.n_ext_ang);
+  const size_t d = sizeof(double);
+  size_t u = 0;
+  L.o_tab = seg(u, (size_t)pl.tab_count * d);
+  L.o_tab32 = seg(u, ((size_t)pl.tab_count + 4) * sizeof(float));
+  L.o_y = seg(u, (size_t)L.ny * d);
+  L.o_ys = seg(u, (size_t)L.ny * d);
+  L.o_K = seg(u, (size_t)7 * L.ny * d);
+  L.o_raw = seg(u, (size_t)pl.n_ext * d);
+  L.o_radF = seg(u, (size_t)pl.nr * (2 * pl.N + 1) * d);
+  L.o_radq = seg(u, (size_t)pl.nr * d);
+  L.o_extp = seg(u, (size_t)pl.n_ext_p * d);
+  L.o_psis = seg(u, (size_t)L.npsi * d);
+  L.o_part = seg(u, (size_t)pl.n_items * d);
+  L.o_rx = seg(u, (size_t)pl.nr * d);
+  L.o_rw = seg(u, (size_t)pl.nr * d);
+  L.o_a1x = seg(u, (size_t)pl.na1 * d);
+  L.o_a1w = seg(u, (size_t)pl.na1 * d);
+  L.o_a2x = seg(u, d);
+  L.o_a2w = seg(u, d);
+  L.o_psx = seg(u, (size_t)L.npsi * d);
+  L.o_psw = seg(u, (size_t)L.npsi * d);
+  L.bytes = u;
+}
+
+struct Slot {
+  ServeReq *req = nullptr;
+  unsigned char *buf = nullptr;
+  size_t cap = 0;
+  SlotLayout L;
+  RhsArgs ra;
+  FlowArgs fa;
+  bool fresh = false;  // admitted, first derivative not yet taken
+};
+
+// Compact device copies of the descriptors of one launch set.
+struct LaunchSet {
+  RhsArgs *descs = nullptr;
+  FlowArgs *fa = nullptr;
+  int *lists = nullptr;  // [all | d3 flows | d3 start | ft flows | ft start]
+  BatchList bl{};
+  int n = 0, max_ny = 0;
+};
+
+struct Server {
+  ffrg_ctx lc;  // launch context of the scheduler thread (no allocations behind it)
+  ffrg_serve_opts opts{};
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<ServeReq *> queue;
+  std::unordered_map<unsigned long long, ServeReq *> reqs;
+  unsigned long long next_id = 1;
+  std::vector<Slot> slots;
+  size_t hbm_used = 0;
+  cudaStream_t st = nullptr;
+  FlowCtl *ctl_dev = nullptr, *ctl_host = nullptr;
+  unsigned *status_dev = nullptr;
+  LaunchSet step_set, init_set;
+  unsigned char *stage_host = nullptr;  // pinned staging of descriptor uploads
+  size_t stage_bytes = 0;
+  ffrg_serve_stats stats{};
+  int fatal = FFRG_OK;
+};
+
+}  // namespace ffrg
+
+namespace ffrg {
+
+// Fill a slot's device buffer from its request and build its descriptors.
+static int slot_setup(Server &S, int si) {
+  Slot &sl = S.slots[si];
+  ServeReq *r = sl.req;
+  SlotLayout &L = sl.L;
+  Plan &pl = L.pl;
+  unsigned char *b = sl.buf;
+  const size_t d = sizeof(double);
+  std::vector<double> rx(pl.nr), rw(pl.nr), x1(pl.na1), w1(pl.na1), xp(L.npsi), wp(L.npsi);
+  double x2 = 0.0, w2 = 2.0;
+  host_gauss_legendre(pl.nr, 0.0, 1.0, rx.data(), rw.data());
+  host_gauss_legendre(pl.na1, -1.0, 1.0, x1.data(), w1.data());
+  host_gauss_legendre(L.npsi, -1.0, 1.0, xp.data(), wp.data());
+  pl.rad_x = (double *)(b + L.o_rx);
+  pl.rad_w = (double *)(b + L.o_rw);
+  pl.a1_x = (double *)(b + L.o_a1x);
+  pl.a1_w = (double *)(b + L.o_a1w);
+  pl.a2_x = (double *)(b + L.o_a2x);
+  pl.a2_w = (double *)(b + L.o_a2w);
+  pl.psi_x = (double *)(b + L.o_psx);
+  pl.psi_w = (double *)(b + L.o_psw);
+  pl.radF = (double *)(b + L.o_radF);
+  pl.radq = (double *)(b + L.o_radq);
+  pl.ext_pd = (double *)(b + L.o_extp);
+  pl.psi_s = (double *)(b + L.o_psis);
+  pl.partial = (double *)(b + L.o_part);
+  pl.tab32 = (float *)(b + L.o_tab32);
+  struct Up { void *dst; const void *src; size_t n; } ups[] = {
+      {b + L.o_tab, r->tab.data(), r->tab.size() * d}, {b + L.o_y, r->y0.data(), r->y0.size() * d},
+      {pl.rad_x, rx.data(), rx.size() * d},           {pl.rad_w, rw.data(), rw.size() * d},
+      {pl.a1_x, x1.data(), x1.size() * d},            {pl.a1_w, w1.data(), w1.size() * d},
+      {pl.a2_x, &x2, d},                              {pl.a2_w, &w2, d},
+      {pl.psi_x, xp.data(), xp.size() * d},           {pl.psi_w, wp.data(), wp.size() * d}};
+  for (auto &u : ups) {
+    cudaError_t e = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, S.st);
+    if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve upload");
+  }
+  FlowCtl hc;
+  memset(&hc, 0, sizeof(hc));
+  const ffrg_step_opts &o = r->opts;
+  hc.t = o.t0;
+  hc.t0 = o.t0;
+  hc.t1 = o.t1;
+  hc.dt = fmin(fmax(o.dt0, o.dt_min), o.dt_max);
+  hc.dt_min = o.dt_min;
+  hc.dt_max = o.dt_max;
+  hc.atol = o.atol;
+  hc.rtol = o.rtol;
+  hc.end_tol = 1e-13 * fmax(fabs(o.t1 - o.t0), 1.0);
+  hc.Lambda = r->Lambda;
+  hc.max_steps = o.max_steps;
+  FlowCtl *ctl = S.ctl_dev + si;
+  cudaError_t e = cudaMemcpyAsync(ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, S.st);
+  if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve ctl upload");
+  // the host copies above come from pageable memory and the stack: wait for them
+  e = cudaStreamSynchronize(S.st);
+  if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve upload sync");
+  fill_args(&pl, &r->pb, &r->td, (const double *)(b + L.o_tab), r->Lambda, sl.ra);
+  sl.ra.out = (double *)(b + L.o_raw);
+  sl.ra.status = S.status_dev;
+  sl.ra.k_dev = &ctl->k_stage;
+  sl.ra.skip = &ctl->done;
+  FlowArgs &f = sl.fa;
+  memset(&f, 0, sizeof(f));
+  f.ny = L.ny;
+  f.mode = 0;
+  f.n = r->td.n_pts;
+  f.npsi = r->pb.n_ext_ang;
+  f.p_min = r->pb.p_min;
+  f.p_step = r->pb.n_ext_p > 1 ? log(r->pb.p_max / r->pb.p_min) / (r->pb.n_ext_p - 1) : 0.0;
+  f.psi_w = pl.psi_w;
+  f.y = (double *)(b + L.o_y);
+  f.ys = (double *)(b + L.o_ys);
+  f.K = (double *)(b + L.o_K);
+  f.raw = (double *)(b + L.o_raw);
+  f.ctl = ctl;
+  sl.fresh = true;
+  return FFRG_OK;
+}
+
+static size_t smem32_of(const Plan &pl) {
+  auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  return al16(((size_t)pl.tab_count + 1) * 4) + al16((size_t)pl.na1 * 3 * 4 + 2 * 4);
+}
+
+// Upload the descriptors of the given slots as one compact launch set.
+static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
+  const int n = (int)ids.size(), cap = (int)S.slots.size();
+  ls.n = n;
+  ls.max_ny = 0;
+  BatchList &bl = ls.bl;
+  bl = BatchList();
+  if (n == 0) return FFRG_OK;
+  // host staging: descs | fa | lists
+  RhsArgs *hd = (RhsArgs *)S.stage_host;
+  FlowArgs *hf = (FlowArgs *)(S.stage_host + sizeof(RhsArgs) * cap);
+  int *hl = (int *)(S.stage_host + (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap);
+  int *d3f = hl + cap, *d3s = d3f + cap, *ftf = d3s + cap + 1, *fts = ftf + cap;
+  int n3 = 0, nf = 0, it3 = 0, itf = 0;
+  d3s[0] = 0;
+  fts[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const Slot &sl = S.slots[ids[i]];
+    hd[i] = sl.ra;
+    hf[i] = sl.fa;
+    hl[i] = ids[i];
+    ls.max_ny = std::max(ls.max_ny, sl.L.ny);
+    bl.max_ext = std::max(bl.max_ext, sl.L.pl.n_ext);
+    bl.max_pre = std::max(bl.max_pre, std::max((2 * sl.L.pl.N + 1) * sl.L.pl.nr,
+                                               std::max(sl.L.pl.tab_count, sl.L.pl.n_ext_p)));
+    if (sl.L.pl.model == FFRG_MODEL_D3) {
+      d3f[n3++] = i;
+      it3 += sl.L.pl.n_items;
+      d3s[n3] = it3;
+      bl.smem_d3 = std::max(bl.smem_d3, smem32_of(sl.L.pl));
+    } else {
+      ftf[nf++] = i;
+      itf += sl.L.pl.n_items;
+      fts[nf] = itf;
+      bl.smem_ft = std::max(bl.smem_ft, smem32_of(sl.L.pl));
+    }
+  }
+  const size_t bytes = (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap + sizeof(int) * (5 * cap + 2);
+  cudaError_t e = cudaMemcpyAsync(ls.descs, S.stage_host, bytes, cudaMemcpyHostToDevice, S.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);  // the staging buffer is reused
+  if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve descriptor upload");
+  int *dl = ls.lists;
+  bl.descs = ls.descs;
+  bl.n_flows = n;
+  bl.d3_flows = dl + cap;
+  bl.d3_start = dl + 2 * cap;
+  bl.n_d3 = n3;
+  bl.d3_items = it3;
+  bl.ft_flows = dl + 3 * cap + 1;
+  bl.ft_start = dl + 4 * cap + 1;
+  bl.n_ft = nf;
+  bl.ft_items = itf;
+  return FFRG_OK;
+}
+
+}  // namespace ffrg
+
+namespace ffrg {
+
+static void finish_req(Server &S, ServeReq *r, int status) {
+  r->status = status;
+  r->state = kDone;
+  r->latency = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
+  if (status == FFRG_ECANCELED) S.stats.cancelled++;
+  else S.stats.completed++;
+}
+
+// Retire slot si: copy the state back (unless cancelled) and free the slot.
+static int retire(Server &S, int si, int status) {
+  Slot &sl = S.slots[si];
+  ServeReq *r = sl.req;
+  const FlowCtl &c = S.ctl_host[si];
+  if (status != FFRG_ECANCELED) {
+    r->result.resize(sl.L.ny);
+    cudaError_t e = cudaMemcpy(r->result.data(), sl.fa.y, sl.L.ny * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve result copy");
+    r->stats.steps = c.steps;
+    r->stats.rejects = c.rejects;
+    r->stats.rhs_evals = 1 + 6 * (c.steps + c.rejects);
+    r->stats.integrand_evals = (double)r->stats.rhs_evals * ffrg_evals(&r->pb);
+    r->stats.t_reached = c.t;
+  }
+  std::lock_guard<std::mutex> lock(S.mu);
+  finish_req(S, r, status);
+  sl.req = nullptr;
+  sl.fresh = false;
+  return FFRG_OK;
+}
+
+// Admit queued requests (first come, first served) while a slot is free and
+// the HBM budget holds the request's buffers.
+static int admit(Server &S) {
+  for (;;) {
+    ServeReq *r = nullptr;
+    int si = -1;
+    {
+      std::lock_guard<std::mutex> lock(S.mu);
+      while (!S.queue.empty() && S.queue.front()->cancel) {
+        ServeReq *c = S.queue.front();
+        S.queue.pop_front();
+        finish_req(S, c, FFRG_ECANCELED);
+      }
+      if (S.queue.empty()) return FFRG_OK;
+      r = S.queue.front();
+      for (int i = 0; i < (int)S.slots.size() && si < 0; ++i)
+        if (!S.slots[i].req) si = i;
+      if (si < 0) return FFRG_OK;
+      // a free slot whose buffer is large enough avoids a new allocation
+      for (int i = 0; i < (int)S.slots.size(); ++i)
+        if (!S.slots[i].req && S.slots[i].cap >= r->need) {
+          si = i;
+          break;
+        }
+      Slot &sl = S.slots[si];
+      const size_t grow = sl.cap >= r->need ? 0 : r->need - sl.cap;
+      if (S.hbm_used + grow > S.opts.hbm_budget_bytes) {
+        // release idle buffers before giving up
+        for (auto &o : S.slots)
+          if (!o.req && o.buf && &o != &sl) {
+            cudaFree(o.buf);
+            S.hbm_used -= o.cap;
+            o.buf = nullptr;
+            o.cap = 0;
+          }
+        if (S.hbm_used + grow > S.opts.hbm_budget_bytes) return FFRG_OK;
+      }
+      S.queue.pop_front();
+      r->state = kResident;
+      sl.req = r;
+    }
+    Slot &sl = S.slots[si];
+    if (sl.cap < r->need) {
+      if (sl.buf) {
+        cudaFree(sl.buf);
+        S.hbm_used -= sl.cap;
+        sl.buf = nullptr;
+        sl.cap = 0;
+      }
+      cudaError_t e = cudaMalloc((void **)&sl.buf, r->need);
+      if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve slot allocation");
+      sl.cap = r->need;
+      S.hbm_used += sl.cap;
+    }
+    slot_layout(&r->pb, &r->td, sl.L);
+    int st = slot_setup(S, si);
+    if (st) return st;
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.stats.admitted++;
+  }
+}
+
+static void scheduler(Server *Sp) {
+  Server &S = *Sp;
+  cudaSetDevice(S.lc.device);
+  bool changed = true;
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lock(S.mu);
+      if (S.stop) break;
+    }
+    int st = admit(S);
+    // new flows: first derivative and first step size
+    std::vector<int> fresh, live;
+    for (int i = 0; i < (int)S.slots.size(); ++i) {
+      if (!S.slots[i].req) continue;
+      live.push_back(i);
+      if (S.slots[i].fresh) fresh.push_back(i);
+    }
+    if (!st && !fresh.empty()) {
+      st = build_set(S, fresh, S.init_set);
+      if (!st) st = launch_flow_batched_init(&S.lc, S.init_set.fa, S.init_set.n, S.init_set.max_ny, S.init_set.bl,
+                                            S.st);
+      for (int i : fresh) S.slots[i].fresh = false;
+      changed = true;
+    }
+    if (st) {
+      S.fatal = st;
+      break;
+    }
+    if (live.empty()) {
+      std::unique_lock<std::mutex> lock(S.mu);
+      S.cv.wait_for(lock, std::chrono::milliseconds(2), [&] { return S.stop || !S.queue.empty(); });
+      continue;
+    }
+    if (changed) {
+      st = build_set(S, live, S.step_set);
+      changed = false;
+    }
+    if (!st) st = launch_flow_batched_step(&S.lc, S.step_set.fa, S.step_set.n, S.step_set.max_ny, S.step_set.bl,
+                                           S.st);
+    cudaError_t e = cudaSuccess;
+    if (!st) e = cudaMemcpyAsync(S.ctl_host, S.ctl_dev, sizeof(FlowCtl) * S.slots.size(), cudaMemcpyDeviceToHost, S.st);
+    if (!st && e == cudaSuccess) e = cudaStreamSynchronize(S.st);
+    if (!st && e != cudaSuccess) st = set_cuda_error(&S.lc, e, "serve tick");
+    if (st) {
+      S.fatal = st;
+      break;
+    }
+    {
+      std::lock_guard<std::mutex> lock(S.mu);
+      S.stats.ticks++;
+      S.stats.resident = (int)live.size();
+      S.stats.peak_resident = std::max(S.stats.peak_resident, (int)live.size());
+      S.stats.hbm_in_use = S.hbm_used;
+    }
+    for (int i : live) {
+      const FlowCtl &c = S.ctl_host[i];
+      bool cancel;
+      {
+        std::lock_guard<std::mutex> lock(S.mu);
+        cancel = S.slots[i].req->cancel;
+      }
+      if (c.done || cancel) {
+        st = retire(S, i, cancel ? FFRG_ECANCELED : c.status);
+        changed = true;
+        if (st) break;
+      }
+    }
+    if (st) {
+      S.fatal = st;
+      break;
+    }
+    S.cv.notify_all();
+  }
+  // drain: everything still queued or resident is cancelled
+  std::lock_guard<std::mutex> lock(S.mu);
+  for (auto &sl : S.slots)
+    if (sl.req) {
+      finish_req(S, sl.req, S.fatal ? S.fatal : FFRG_ECANCELED);
+      sl.req = nullptr;
+    }
+  while (!S.queue.empty()) {
+    finish_req(S, S.queue.front(), S.fatal ? S.fatal : FFRG_ECANCELED);
+    S.queue.pop_front();
+  }
+  S.stop = true;
+  S.cv.notify_all();
+}
+
+}  // namespace ffrg
+
+using namespace ffrg;
+
+static Server *server_of(ffrg_ctx *ctx) { return ctx ? (Server *)ctx->server : nullptr; }
+
+extern "C" int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts) {
+  if (!ctx || !opts) return FFRG_EINVAL;
+  if (ctx->server) return FFRG_EBUSY;
+  if (opts->max_slots < 1 || opts->max_slots > 256 || opts->max_queue < 1) return FFRG_EINVAL;
+  cudaSetDevice(ctx->device);
+  Server *S = new Server();
+  S->opts = *opts;
+  if (!S->opts.hbm_budget_bytes) S->opts.hbm_budget_bytes = size_t(1) << 30;
+  S->lc.device = ctx->device;
+  S->lc.num_sms = ctx->num_sms;
+  S->lc.budget = 0;
+  S->lc.used = 0;
+  S->lc.status_dev = nullptr;
+  S->lc.status_host = nullptr;
+  S->lc.server = nullptr;
+  S->lc.profiling = 0;
+  S->lc.prof_used = 0;
+  const int cap = opts->max_slots;
+  S->slots.resize(cap);
+  const size_t set_bytes = (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap + sizeof(int) * (5 * cap + 2);
+  S->stage_bytes = set_bytes;
+  cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&S->ctl_dev, sizeof(FlowCtl) * cap);
+  if (e == cudaSuccess) e = cudaMemset(S->ctl_dev, 0, sizeof(FlowCtl) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&S->ctl_host, sizeof(FlowCtl) * cap);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&S->status_dev, 16);
+  if (e == cudaSuccess) e = cudaMemset(S->status_dev, 0, 16);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&S->stage_host, set_bytes);
+  for (LaunchSet *ls : {&S->step_set, &S->init_set}) {
+    unsigned char *blk = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&blk, set_bytes);
+    ls->descs = (RhsArgs *)blk;
+    ls->fa = (FlowArgs *)(blk + sizeof(RhsArgs) * cap);
+    ls->lists = (int *)(blk + (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap);
+  }
+  if (e != cudaSuccess) {
+    int st = set_cuda_error(ctx, e, "ffrg_serve_start");
+    cudaFree(S->ctl_dev);
+    cudaFreeHost(S->ctl_host);
+    cudaFree(S->status_dev);
+    cudaFreeHost(S->stage_host);
+    cudaFree(S->step_set.descs);
+    cudaFree(S->init_set.descs);
+    if (S->st) cudaStreamDestroy(S->st);
+    delete S;
+    return st;
+  }
+  ctx->server = S;
+  S->th = std::thread(scheduler, S);
+  return FFRG_OK;
+}
+
+extern "C" int ffrg_serve_submit(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *desc,
+                                 const double *tables_host, const double *y0_host, double Lambda,
+                                 const ffrg_step_opts *o, unsigned long long *ticket) {
+  Server *S = server_of(ctx);
+  if (!S) return FFRG_EINVAL;
+  if (!pb || !desc || !tables_host || !y0_host || !o || !ticket) return FFRG_EINVAL;
+  if (pb->model != FFRG_MODEL_D3 && pb->model != FFRG_MODEL_FINITE_T) return FFRG_EINVAL;
+  if (validate_problem(pb, desc) != FFRG_OK) return FFRG_EINVAL;
+  if (!(Lambda > 0.0) || !isfinite(Lambda) || !(o->t1 >= o->t0) || !(o->dt0 > 0.0) || !(o->dt_min > 0.0) ||
+      !(o->dt_max >= o->dt_min) || !(o->atol >= 0.0) || !(o->rtol >= 0.0) || !(o->atol + o->rtol > 0.0) ||
+      o->max_steps < 1)
+    return FFRG_EINVAL;
+  SlotLayout L;
+  slot_layout(pb, desc, L);
+  if (smem32_of(L.pl) > 227 * 1024) return FFRG_EINVAL;
+  ServeReq *r = new ServeReq();
+  r->pb = *pb;
+  r->td = *desc;
+  r->opts = *o;
+  r->Lambda = Lambda;
+  r->tab.assign(tables_host, tables_host + (size_t)L.pl.tab_count);
+  r->y0.assign(y0_host, y0_host + L.ny);
+  r->need = L.bytes;
+  r->ny = L.ny;
+  std::lock_guard<std::mutex> lock(S->mu);
+  if (S->stop) {
+    delete r;
+    return S->fatal ? S->fatal : FFRG_EINVAL;
+  }
+  if (r->need > S->opts.hbm_budget_bytes) {
+    S->stats.rejected++;
+    delete r;
+    return FFRG_ENOMEM;
+  }
+  if ((int)S->queue.size() >= S->opts.max_queue) {
+    S->stats.rejected++;
+    delete r;
+    return FFRG_EBUSY;
+  }
+  r->id = S->next_id++;
+  r->t_submit = Clock::now();
+  S->queue.push_back(r);
+  S->reqs[r->id] = r;
+  S->stats.submitted++;
+  *ticket = r->id;
+  S->cv.notify_all();
+  return FFRG_OK;
+}
+
+extern "C" int ffrg_serve_poll(ffrg_ctx *ctx, unsigned long long ticket, double *result_host, ffrg_flow_stats *stats,
+                               double *latency_s) {
+  Server *S = server_of(ctx);
+  if (!S) return FFRG_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return FFRG_ENOTFOUND;
+  ServeReq *r = it->second;
+  if (r->state != kDone) return FFRG_EPENDING;
+  if (result_host && !r->result.empty()) memcpy(result_host, r->result.data(), r->result.size() * sizeof(double));
+  if (stats) *stats = r->stats;
+  if (latency_s) *latency_s = r->latency;
+  const int st = r->status;
+  S->reqs.erase(it);
+  delete r;
+  return st;
+}
+
+extern "C" int ffrg_serve_cancel(ffrg_ctx *ctx, unsigned long long ticket) {
+  Server *S = server_of(ctx);
+  if (!S) return FFRG_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return FFRG_ENOTFOUND;
+  it->second->cancel = true;
+  S->cv.notify_all();
+  return FFRG_OK;
+}
+
+extern "C" int ffrg_serve_get_stats(ffrg_ctx *ctx, ffrg_serve_stats *out) {
+  Server *S = server_of(ctx);
+  if (!S || !out) return FFRG_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
+  *out = S->stats;
+  out->queued = (int)S->queue.size();
+  return FFRG_OK;
+}
+
+extern "C" int ffrg_serve_stop(ffrg_ctx *ctx) {
+  Server *S = server_of(ctx);
+  if (!S) return FFRG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+    S->cv.notify_all();
+  }
+  if (S->th.joinable()) S->th.join();
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(S->st);
+  for (auto &sl : S->slots) cudaFree(sl.buf);
+  for (auto &kv : S->reqs) delete kv.second;
+  cudaFree(S->ctl_dev);
+  cudaFreeHost(S->ctl_host);
+  cudaFree(S->status_dev);
+  cudaFreeHost(S->stage_host);
+  cudaFree(S->step_set.descs);
+  cudaFree(S->init_set.descs);
+  cudaStreamDestroy(S->st);
+  const int fatal = S->fatal;
+  if (fatal) ctx->last_error = S->lc.last_error;
+  delete S;
+  ctx->server = nullptr;
+  return fatal;
+}

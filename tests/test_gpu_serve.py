@@ -1,0 +1,148 @@
+"""Serving (continuous batching of flow requests): results in the mix equal
+the results alone, match the single-flow mixed path and the oracle, and the
+scheduler admits by HBM budget, rejects, cancels and reports latency."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import ffrg_inputs as fi
+import oracle
+from gpu_common import gpu_context
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(n, seed=11):
+    return fi.serving_stream(seed=seed, n_requests=n, ext_range=(9, 27), rad_range=(8, 24), ang_range=(4, 12),
+                             pts_range=(16, 40), t_max=0.5, n_cap=6)
+
+
+def _submit(ctx, wl, rtol=1e-10, atol=1e-13):
+    t1 = math.log(wl.Lambda / wl.k_end)
+    return ctx.serve_submit(wl.problem, wl.tables, wl.y0, wl.Lambda, t1, rtol=rtol, atol=atol)
+
+
+def _wait(ctx, tickets, sizes, timeout=120.0):
+    import paper_2412_13043_gb300 as ffrg
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for tk, n in zip(tickets, sizes):
+            if tk in out:
+                continue
+            st, res, stats, lat = ctx.serve_poll(tk, n)
+            if st != ffrg.EPENDING:
+                out[tk] = (st, res, stats, lat)
+        assert time.time() - t0 < timeout, "serving did not finish"
+        time.sleep(0.002)
+    return out
+
+
+def test_mix_equals_alone_and_single_flow_path():
+    import paper_2412_13043_gb300 as ffrg
+    reqs = _stream(12)
+    # alone: one request at a time through its own server
+    alone = []
+    for rq in reqs:
+        ctx = gpu_context()
+        ctx.serve_start(max_slots=1)
+        tk = _submit(ctx, rq.workload)
+        alone.append(_wait(ctx, [tk], [rq.workload.problem.n_ext()])[tk])
+        assert ctx.serve_stop() == ffrg.OK
+        ctx.close()
+    # in the mix: all at once, fewer slots than requests so that some queue
+    ctx = gpu_context()
+    ctx.serve_start(max_slots=5)
+    tks = [_submit(ctx, rq.workload) for rq in reqs]
+    mix = _wait(ctx, tks, [rq.workload.problem.n_ext() for rq in reqs])
+    stats = ctx.serve_stats()
+    assert ctx.serve_stop() == ffrg.OK
+    assert stats["completed"] == len(reqs) and stats["peak_resident"] <= 5
+    for rq, tk, al in zip(reqs, tks, alone):
+        st, res, fst, lat = mix[tk]
+        assert st == ffrg.OK and al[0] == ffrg.OK
+        assert np.array_equal(res, al[1]), rq.rid          # bitwise, independent of batch composition
+        assert fst["steps"] == al[2]["steps"] and lat > 0
+    # single-flow mixed path (ffrg_flow) on two of them
+    for rq, tk in list(zip(reqs, tks))[:2]:
+        wl = rq.workload
+        import torch
+        tabs = ctx.tables(wl.problem, wl.tables)
+        y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+        ctx.flow(wl.problem, tabs, y, wl.Lambda, math.log(wl.Lambda / wl.k_end), precision=ffrg.MIXED,
+                 rtol=1e-10, atol=1e-13)
+        tabs.free()
+        ref = y.cpu().numpy()
+        res = mix[tk][1]
+        assert np.max(np.abs(res - ref) / np.abs(ref)) < 1e-9
+    ctx.close()
+
+
+def test_served_results_match_oracle():
+    import paper_2412_13043_gb300 as ffrg
+    reqs = _stream(4, seed=17)
+    ctx = gpu_context()
+    ctx.serve_start(max_slots=4)
+    tks = [_submit(ctx, rq.workload) for rq in reqs]
+    res = _wait(ctx, tks, [rq.workload.problem.n_ext() for rq in reqs])
+    ctx.serve_stop()
+    ctx.close()
+    for rq, tk in zip(reqs, tks):
+        wl = rq.workload
+        truth, _ = oracle.flow(wl.problem, wl.tables, wl.y0, wl.Lambda, math.log(wl.Lambda / wl.k_end),
+                               rtol=1e-13, atol=1e-16)
+        st, y, _, _ = res[tk]
+        assert st == ffrg.OK
+        assert np.max(np.abs(y - truth) / np.abs(truth)) < 1e-7, rq.rid
+
+
+def test_admission_by_hbm_budget_and_rejection():
+    import paper_2412_13043_gb300 as ffrg
+    reqs = _stream(6, seed=23)
+    ctx = gpu_context()
+    # budget for about two of these requests at a time
+    ctx.serve_start(max_slots=8, max_queue=16, hbm_budget_bytes=150_000)
+    sizes = [rq.workload.problem.n_ext() for rq in reqs]
+    tks = []
+    for rq in reqs:
+        try:
+            tks.append(_submit(ctx, rq.workload))
+        except ffrg.FfrgError as e:
+            assert e.code == ffrg.ENOMEM            # larger than the whole budget
+            tks.append(None)
+    live = [(t, n) for t, n in zip(tks, sizes) if t is not None]
+    out = _wait(ctx, [t for t, _ in live], [n for _, n in live])
+    stats = ctx.serve_stats()
+    ctx.serve_stop()
+    assert all(v[0] == ffrg.OK for v in out.values())
+    assert stats["completed"] == len(live) and stats["peak_resident"] <= 8
+    assert stats["hbm_in_use"] <= 150_000
+    # queue limit
+    ctx.serve_start(max_slots=1, max_queue=1)
+    wl = reqs[0].workload
+    first = _submit(ctx, wl)
+    with pytest.raises(ffrg.FfrgError) as ei:
+        for _ in range(50):
+            _submit(ctx, wl)
+    assert ei.value.code == ffrg.EBUSY
+    ctx.serve_stop()
+    assert ctx.serve_poll(first, 1)[0] == ffrg.EINVAL      # the server is gone
+    ctx.close()
+
+
+def test_cancel_and_unknown_ticket():
+    import paper_2412_13043_gb300 as ffrg
+    reqs = _stream(3, seed=29)
+    ctx = gpu_context()
+    ctx.serve_start(max_slots=1)
+    tks = [_submit(ctx, rq.workload, rtol=1e-12) for rq in reqs]
+    assert ctx.serve_cancel(tks[2]) == ffrg.OK            # still queued
+    out = _wait(ctx, tks, [rq.workload.problem.n_ext() for rq in reqs])
+    assert out[tks[2]][0] == ffrg.ECANCELED
+    assert out[tks[0]][0] == ffrg.OK
+    assert ctx.serve_poll(12345678, 1)[0] == ffrg.ENOTFOUND
+    assert ctx.serve_cancel(12345678) == ffrg.ENOTFOUND
+    ctx.serve_stop()
+    ctx.close()
