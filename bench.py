@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", default="ffrg", choices=["ffrg", "reference"])
     ap.add_argument("--no-flows", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -142,6 +144,91 @@ def cpu_baseline(wl, stride: int):
     return {"value": ev / dt, "unit": "integrand evals/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{len(sel)} of {pb.n_ext()} external points (every {stride}th) of the d4 RHS at k=1, "
                       f"{ev:.3g} evals, {dt:.2f} s wall"}
+
+
+def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
+    """Served mixed-precision flows (continuous batching) vs one flow at a time
+    through ffrg_flow in FP64 and mixed precision; p50/p99 latency under
+    Poisson arrivals at 0.8x the measured served capacity."""
+    import numpy as np
+    import torch
+
+    import ffrg_inputs as fi
+    import paper_2412_13043_gb300 as ffrg
+    reqs = fi.serving_stream(seed=5, n_requests=n_req)
+    rtol, atol = 1e-10, 1e-13
+
+    def t1_of(wl):
+        return math.log(wl.Lambda / wl.k_end)
+
+    # one flow at a time (the plain path), FP64 and mixed, on the first n_fp64 requests
+    single = {}
+    for name, prec in (("fp64", ffrg.FP64), ("mixed", ffrg.MIXED)):
+        outs, t_tot, ev = [], 0.0, 0.0
+        for rq in reqs[:n_fp64]:
+            wl = rq.workload
+            tabs = ctx.tables(wl.problem, wl.tables)
+            y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fs = ctx.flow(wl.problem, tabs, y, wl.Lambda, t1_of(wl), precision=prec, rtol=rtol, atol=atol)
+            torch.cuda.synchronize()
+            t_tot += time.perf_counter() - t
+            ev += fs["integrand_evals"]
+            outs.append(y.cpu().numpy())
+            tabs.free()
+        single[name] = {"flows_per_s": len(outs) / t_tot, "evals_per_s": ev / t_tot, "outs": outs}
+
+    def run(arrivals):
+        ctx.serve_start(max_slots=64, max_queue=len(reqs) + 8, hbm_budget_bytes=8 << 30)
+        tick, lat, res, ev = {}, {}, {}, [0.0]
+        t0 = time.perf_counter()
+        i = 0
+        while len(lat) < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
+                wl = reqs[i].workload
+                tick[ctx.serve_submit(wl.problem, wl.tables, wl.y0, wl.Lambda, t1_of(wl), rtol=rtol,
+                                      atol=atol)] = i
+                i += 1
+            for tk, j in list(tick.items()):
+                st, out, fst, l = ctx.serve_poll(tk, reqs[j].workload.problem.n_ext())
+                if st != ffrg.EPENDING:
+                    assert st == ffrg.OK, ffrg.strerror(st)
+                    ev[0] += fst["integrand_evals"]
+                    lat[j] = l
+                    res[j] = out
+                    del tick[tk]
+            if now > seconds_cap:
+                raise RuntimeError("serving benchmark exceeded its time cap")
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        stats = ctx.serve_stats()
+        ctx.serve_stop()
+        return wall, lat, res, stats, ev[0]
+
+    wall, lat_sat, res, stats, ev_sat = run([0.0] * len(reqs))
+    capacity = len(reqs) / wall
+    err = max(float(np.max(np.abs(res[j] - single["fp64"]["outs"][j]) / np.abs(single["fp64"]["outs"][j])))
+              for j in range(n_fp64))
+    rate = 0.8 * capacity
+    arrivals = [rq.arrival_s * (200.0 / rate) for rq in reqs]   # the stream was drawn at 200 Hz
+    wall_p, lat, _, stats_p, _ = run(arrivals)
+    lv = sorted(lat.values())
+    return {"requests": len(reqs), "families": "T=0 d3 frozen flows and finite-T frozen flows, "
+                                              "ext 32-256, radial 32-128, angular 16-64, tables 64-256 pts",
+            "served_flows_per_s": capacity, "served_integrand_evals_per_s": ev_sat / wall,
+            "fp64_one_at_a_time_evals_per_s": single["fp64"]["evals_per_s"],
+            "mixed_one_at_a_time_evals_per_s": single["mixed"]["evals_per_s"],
+            "peak_resident": stats["peak_resident"], "ticks": stats["ticks"],
+            "fp64_one_at_a_time_flows_per_s": single["fp64"]["flows_per_s"],
+            "mixed_one_at_a_time_flows_per_s": single["mixed"]["flows_per_s"],
+            "speedup_served_over_fp64": capacity / single["fp64"]["flows_per_s"],
+            "sample_for_one_at_a_time": n_fp64,
+            "served_vs_fp64_endpoint_max_rel_diff": err, "rtol": rtol,
+            "poisson_rate_hz": rate, "poisson_flows_per_s": len(reqs) / wall_p,
+            "latency_p50_s": lv[len(lv) // 2], "latency_p99_s": lv[min(len(lv) - 1, int(0.99 * len(lv)))],
+            "saturation_latency_p50_s": sorted(lat_sat.values())[len(lat_sat) // 2]}
 
 
 def run_reference(args):
@@ -330,6 +417,10 @@ def main():
                  **res}
         tf.free()
 
+    serving = None
+    if not args.no_serve:
+        serving = serving_bench(ctx, args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, stride=4)
@@ -351,6 +442,7 @@ def main():
             "roofline": roofline,
             "clocks": clocks,
             "flows": flows,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
