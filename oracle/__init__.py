@@ -101,6 +101,8 @@ def _load():
         lib.orc_flow.argtypes = [pp, dp, I, D, dp, P(_StepOpts), P(_Stats)]
         lib.orc_flow_deriv.argtypes = [pp, dp, I, D, D, dp, dp]
         lib.orc_dp45_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
+        lib.orc_ros2_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
+        lib.orc_ros2_flow.argtypes = [pp, D, dp, P(_StepOpts), P(_Stats)]
         lib.orc_flow_state_size.argtypes = [pp, I]
         lib.orc_d3_summand.argtypes = [pp, dp, D, D, D]
         lib.orc_d3_summand.restype = D
@@ -258,6 +260,27 @@ def dp45_textbook(which: int, y0, t1: float, dt0: float = 0.1, dt_min: float = 1
     st = _Stats()
     code = _load().orc_dp45_textbook(int(which), _ptr(y), ctypes.byref(o), ctypes.byref(st))
     return y, dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals, status=code)
+
+
+def ros2_textbook(which: int, y0, t1: float, dt0: float = 0.1, dt_min: float = 1e-12, dt_max: float = 1.0,
+                  atol: float = 1e-12, rtol: float = 1e-9, max_steps: int = 1_000_000, t0: float = 0.0):
+    """The oracle's ROS2 driver on a textbook ODE (see orc_ros2_textbook)."""
+    y = _f64(y0).copy()
+    o = _StepOpts(t0, t1, dt0, dt_min, dt_max, atol, rtol, max_steps)
+    st = _Stats()
+    code = _load().orc_ros2_textbook(int(which), _ptr(y), ctypes.byref(o), ctypes.byref(st))
+    return y, dict(steps=st.steps, rejects=st.rejects, jacobians=st.rhs_evals, status=code)
+
+
+def ros2_flow(pb, y0, Lambda: float, t1: float, dt0: float = 1e-2, dt_min: float = 1e-10, dt_max: float = 0.5,
+              atol: float = 1e-12, rtol: float = 1e-8, max_steps: int = 1_000_000, t0: float = 0.0):
+    """ROS2 flow of the d=4 feedback state (the tables) with the exact state Jacobian."""
+    y = _f64(y0).copy()
+    o = _StepOpts(t0, t1, dt0, dt_min, dt_max, atol, rtol, max_steps)
+    st = _Stats()
+    code = _load().orc_ros2_flow(ctypes.byref(_problem(pb)), Lambda, _ptr(y), ctypes.byref(o), ctypes.byref(st))
+    _check(code, "ros2_flow")
+    return y, dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals)
 
 
 def d3_summand(pb, tables, k, q2, s2) -> float:

@@ -909,3 +909,210 @@ void orc_d4_summand_batch(int block, const orc_problem *pb, const double *tab, d
     else out[i] = orc_d4_summand_4(pb, tab, k, q2[i], p2, A2[i]);
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* Linearly implicit (Rosenbrock) stepping.  ROS2 of Verwer, Spee, Blom  */
+/* and Hundsdorfer (SIAM J. Sci. Comput. 20, 1999), written from its      */
+/* published definition, gamma = 1 + 1/sqrt(2):                          */
+/*   (I - gamma h J) k1 = f(t, y)                                          */
+/*   (I - gamma h J) k2 = f(t + h, y + h k1) - 2 k1                        */
+/*   y_new = y + h (3/2 k1 + 1/2 k2);  estimate y_new - (y + h k1).        */
+/* Second order for any matrix J (W-method); L-stable with the exact J.    */
+/* Step control as for DP5(4) with the exponent 1/2.                       */
+/* ------------------------------------------------------------------ */
+typedef int (*jac_fn)(void *ctx, double t, const double *y, double *J, int ny);
+
+/* Solve A x = b in place (b -> x) by Gaussian elimination with partial
+ * pivoting; A (row-major n x n) is overwritten. */
+static int dense_solve(double *A, double *b, int n) {
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(A[(size_t)i * n + k]) > fabs(A[(size_t)piv * n + k])) piv = i;
+    if (A[(size_t)piv * n + k] == 0.0) return ORC_ENONFINITE;
+    if (piv != k) {
+      for (int j = 0; j < n; ++j) {
+        double t = A[(size_t)k * n + j];
+        A[(size_t)k * n + j] = A[(size_t)piv * n + j];
+        A[(size_t)piv * n + j] = t;
+      }
+      double t = b[k];
+      b[k] = b[piv];
+      b[piv] = t;
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      for (int j = k; j < n; ++j) A[(size_t)i * n + j] -= l * A[(size_t)k * n + j];
+      b[i] -= l * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= A[(size_t)i * n + j] * b[j];
+    b[i] = s / A[(size_t)i * n + i];
+  }
+  return ORC_OK;
+}
+
+static int ros2_run(deriv_fn f, jac_fn jf, void *ctx, int ny, double *y, const orc_step_opts *o, long *n_steps,
+                    long *n_rejects, long *n_jac) {
+  const double g = 1.0 + 1.0 / sqrt(2.0);
+  size_t nn = (size_t)ny * ny;
+  double *J = malloc(sizeof(double) * nn), *W = malloc(sizeof(double) * nn);
+  double *f0 = malloc(sizeof(double) * ny), *k1 = malloc(sizeof(double) * ny), *k2 = malloc(sizeof(double) * ny);
+  double *y1 = malloc(sizeof(double) * ny), *yn = malloc(sizeof(double) * ny);
+  int st = (J && W && f0 && k1 && k2 && y1 && yn) ? ORC_OK : ORC_ENOMEM;
+  double t = o->t0, dt = fmin(fmax(o->dt0, o->dt_min), o->dt_max);
+  long steps = 0, rejects = 0, jacs = 0;
+  int last_rejected = 0, have_jac = 0;
+  double span = fabs(o->t1 - o->t0);
+  if (!st) st = f(ctx, t, y, f0, ny);
+  while (!st && o->t1 - t > 1e-13 * (span > 1.0 ? span : 1.0)) {
+    if (steps + rejects >= o->max_steps) { st = ORC_EMAXSTEPS; break; }
+    double h = dt < o->t1 - t ? dt : o->t1 - t;
+    if (!have_jac) {
+      st = jf(ctx, t, y, J, ny);
+      if (st) break;
+      ++jacs;
+      have_jac = 1;
+    }
+    for (size_t q = 0; q < nn; ++q) W[q] = -g * h * J[q];
+    for (int i = 0; i < ny; ++i) W[(size_t)i * ny + i] += 1.0;
+    memcpy(k1, f0, sizeof(double) * ny);
+    st = dense_solve(W, k1, ny);
+    if (st) break;
+    for (int i = 0; i < ny; ++i) y1[i] = y[i] + h * k1[i];
+    st = f(ctx, t + h, y1, k2, ny);
+    if (st) break;
+    for (int i = 0; i < ny; ++i) k2[i] -= 2.0 * k1[i];
+    for (size_t q = 0; q < nn; ++q) W[q] = -g * h * J[q];
+    for (int i = 0; i < ny; ++i) W[(size_t)i * ny + i] += 1.0;
+    st = dense_solve(W, k2, ny);
+    if (st) break;
+    double err = 0.0;
+    int finite = 1;
+    for (int i = 0; i < ny; ++i) {
+      yn[i] = y[i] + h * (1.5 * k1[i] + 0.5 * k2[i]);
+      double e = fabs(yn[i] - y1[i]) / (o->atol + o->rtol * fmax(fabs(y[i]), fabs(yn[i])));
+      if (!isfinite(e)) finite = 0;
+      if (e > err) err = e;
+    }
+    if (!finite) { st = ORC_ENONFINITE; break; }
+    if (err <= 1.0) {
+      t += h;
+      memcpy(y, yn, sizeof(double) * ny);
+      ++steps;
+      st = f(ctx, t, y, f0, ny);
+      have_jac = 0;
+      double fac = (err == 0.0) ? 5.0 : 0.9 * pow(err, -0.5);
+      if (fac > 5.0) fac = 5.0;
+      if (fac < 0.2) fac = 0.2;
+      if (last_rejected && fac > 1.0) fac = 1.0;
+      last_rejected = 0;
+      dt = h * fac;
+    } else {
+      ++rejects;
+      if (h <= o->dt_min) { st = ORC_ESTEP_UNDERFLOW; break; }
+      double fac = 0.9 * pow(err, -0.5);
+      if (fac < 0.2) fac = 0.2;
+      dt = h * fac;
+      last_rejected = 1;
+    }
+    if (dt > o->dt_max) dt = o->dt_max;
+    if (dt < o->dt_min) dt = o->dt_min;
+  }
+  *n_steps = steps;
+  *n_rejects = rejects;
+  *n_jac = jacs;
+  free(J); free(W); free(f0); free(k1); free(k2); free(y1); free(yn);
+  return st;
+}
+
+/* Textbook problems for the ROS2 driver (closed-form solutions):
+ *   0: y' = y cos t, J = cos t                  -> y0 exp(sin t)
+ *   1: y' = -2 t y^2, J = -4 t y                -> 1/(1/y0 + t^2)
+ *   2: y0' = y1, y1' = -y0 (exact J)            -> rotation
+ *   3: y' = -1e4 (y - cos t) - sin t, J = -1e4  -> cos t (stiff, y0 = 1)
+ *   4: problem 2 with J := 0 (W-method: still second order) */
+static int tb_f(void *ctx, double t, const double *y, double *dy, int ny) {
+  int w = *(int *)ctx;
+  (void)ny;
+  if (w == 0) dy[0] = y[0] * cos(t);
+  else if (w == 1) dy[0] = -2.0 * t * y[0] * y[0];
+  else if (w == 3) dy[0] = -1e4 * (y[0] - cos(t)) - sin(t);
+  else { dy[0] = y[1]; dy[1] = -y[0]; }
+  return ORC_OK;
+}
+
+static int tb_j(void *ctx, double t, const double *y, double *J, int ny) {
+  int w = *(int *)ctx;
+  (void)ny;
+  if (w == 0) J[0] = cos(t);
+  else if (w == 1) J[0] = -4.0 * t * y[0];
+  else if (w == 3) J[0] = -1e4;
+  else if (w == 2) { J[0] = 0.0; J[1] = 1.0; J[2] = -1.0; J[3] = 0.0; }
+  else { J[0] = J[1] = J[2] = J[3] = 0.0; }
+  return ORC_OK;
+}
+
+int orc_ros2_textbook(int which, double *y, const orc_step_opts *o, orc_flow_stats *stats) {
+  if (which < 0 || which > 4 || !y || !o) return ORC_EINVAL;
+  long s = 0, r = 0, jn = 0;
+  int ny = (which == 2 || which == 4) ? 2 : 1;
+  int st = ros2_run(tb_f, tb_j, &which, ny, y, o, &s, &r, &jn);
+  if (stats) {
+    stats->steps = s;
+    stats->rejects = r;
+    stats->rhs_evals = jn;  /* Jacobian evaluations */
+  }
+  return st;
+}
+
+/* State Jacobian of the d=4 feedback flow: column j = map(d raw / d T_j),
+ * with the map of flow_deriv (d_t Z_i = -(D2(p_i)-D2(0))/p_i^2, d_t lambda3_i =
+ * -sum_psi (w/2) Flow3, d_t lambda4_i = -Flow4) applied to a raw derivative. */
+static int d4_state_jac(void *ctxp, double t, const double *y, double *J, int ny) {
+  flow_ctx *fc = (flow_ctx *)ctxp;
+  const orc_problem *pb = fc->pb;
+  int n = pb->n_pts, npsi = pb->n_ext_ang, ne = orc_n_ext(pb);
+  double k = fc->Lambda * exp(-t);
+  double *dt = calloc(ny, sizeof(double)), *o = malloc(sizeof(double) * ne), *d = malloc(sizeof(double) * ne);
+  if (!dt || !o || !d) { free(dt); free(o); free(d); return ORC_ENOMEM; }
+  int st = ORC_OK;
+  for (int j = 0; j < ny && !st; ++j) {
+    dt[j] = 1.0;
+    st = orc_rhs_jvp(pb, y, dt, k, o, d);
+    dt[j] = 0.0;
+    for (int i = 0; i < n && !st; ++i) {
+      double p = ext_p(pb, i);
+      J[(size_t)i * ny + j] = -(d[i] - d[n]) / (p * p);
+      acc_t a = {0, 0};
+      for (int q = 0; q < npsi; ++q) acc_add(&a, 0.5 * fc->psi_w[q] * d[n + 1 + i * npsi + q]);
+      J[(size_t)(n + i) * ny + j] = -acc_get(&a);
+      J[(size_t)(2 * n + i) * ny + j] = -d[n + 1 + n * npsi + i];
+    }
+  }
+  free(dt); free(o); free(d);
+  return st;
+}
+
+/* ROS2 flow of the d=4 feedback state (the tables) with the exact state
+ * Jacobian recomputed at every accepted step. */
+int orc_ros2_flow(const orc_problem *pb, double Lambda, double *y, const orc_step_opts *o, orc_flow_stats *stats) {
+  int st = check_problem(pb);
+  if (st) return st;
+  if (pb->model != ORC_D4_VERTEX || !o || !y || !(Lambda > 0.0)) return ORC_EINVAL;
+  if (pb->n_ext_p != pb->n_pts || pb->p_min != pb->x_min || pb->p_max != pb->x_max) return ORC_EINVAL;
+  int ny = orc_flow_state_size(pb, 1);
+  flow_ctx fc;
+  st = flow_ctx_init(&fc, pb, NULL, 1, Lambda);
+  long s = 0, r = 0, jn = 0;
+  if (!st) st = ros2_run(flow_deriv_cb, d4_state_jac, &fc, ny, y, o, &s, &r, &jn);
+  if (stats) {
+    stats->steps = s;
+    stats->rejects = r;
+    stats->rhs_evals = fc.rhs_evals;
+  }
+  flow_ctx_free(&fc);
+  return st;
+}

@@ -553,3 +553,46 @@ def test_jacobian_columns_are_jvps():
     # linear in the table: integrand is rational in Z -> no, but the lambda-free
     # d=3 RHS depends on Z only through lerps: columns far from all lookups vanish
     assert J.shape == (pb.n_ext(), wl.tables.size)
+
+
+# --------------------------------------------------------------------------
+# linearly implicit ROS2 (Rosenbrock) driver and the d=4 feedback flow
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("which", [0, 2, 4])
+def test_ros2_second_order(which):
+    """ROS2 (Verwer, Spee, Blom, Hundsdorfer 1999) is second order, also with a
+    zero matrix in place of the Jacobian (which 4: W-method property)."""
+    t1 = 2.0
+    y0 = [1.0, 0.0] if which in (2, 4) else [1.0]
+    exact = [math.exp(math.sin(t1))] if which == 0 else [math.cos(t1), -math.sin(t1)]
+    errs = []
+    for h in (0.1, 0.05, 0.025, 0.0125):
+        y, st = oracle.ros2_textbook(which, y0, t1, dt0=h, dt_min=h, dt_max=h, rtol=1e6, atol=1e6)
+        assert st["status"] == 0
+        errs.append(np.max(np.abs(y - exact)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(1.8 < o < 2.3 for o in orders[1:]), orders
+
+
+def test_ros2_stiff_problem_is_stable_at_large_steps():
+    """Prothero-Robinson, lambda = 1e4: fixed steps with lambda h = 1000 stay
+    bounded and first-order accurate (the known stiff order reduction of
+    Rosenbrock methods on non-autonomous problems without a time-derivative
+    term); an explicit method would be unstable at these steps."""
+    errs = []
+    for h in (0.2, 0.1, 0.05):
+        y, st = oracle.ros2_textbook(3, [1.0], 2.0, dt0=h, dt_min=h, dt_max=h, rtol=1e6, atol=1e6)
+        errs.append(abs(y[0] - math.cos(2.0)))
+        assert errs[-1] < h
+    assert 0.8 < math.log2(errs[1] / errs[2]) < 1.3
+
+
+def test_ros2_d4_feedback_flow_matches_dp45():
+    wl = fi.make_d4(seed=6, n_pts=8, n_ext_ang=2, n_rad=8, n_ang1=4, n_ang2=3)
+    pb = wl.problem
+    pb.p_min = pb.x_min = 0.05
+    t1 = 2.0
+    ref, _ = oracle.flow(pb, wl.tables, wl.y0, wl.Lambda, t1, feedback=1, rtol=1e-12, atol=1e-14)
+    y, st = oracle.ros2_flow(pb, wl.y0, wl.Lambda, t1, rtol=1e-8, atol=1e-12)
+    assert np.max(np.abs(y - ref) / np.abs(ref)) < 2e-6, np.max(np.abs(y - ref) / np.abs(ref))
+    assert st["steps"] > 3
