@@ -131,6 +131,7 @@ typedef struct {
   long long steps, rejects, rhs_evals;
   double integrand_evals; /* rhs_evals x (external points x quadrature nodes) */
   double t_reached;
+  long long jac_evals;    /* Jacobian evaluations (Rosenbrock flows) */
 } ffrg_flow_stats;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
@@ -227,6 +228,24 @@ FFRG_API int ffrg_rhs_adjoint(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_
 FFRG_API int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, int feedback, double Lambda,
               double *state_dev, const ffrg_step_opts *opts, int precision, ffrg_flow_stats *stats,
               void *stream);
+/* Full Jacobian of ffrg_rhs with respect to the table values (one pass of the
+ * reverse-mode kernels with a gradient row per external point; Sec. 5.2.2
+ * "jacobian_variables" counterpart): J_dev[e * T + j] = d out_e / d T_j,
+ * T = n_tables x n_stack x n_pts, device, row-major, overwritten.  Models D3
+ * and D4_VERTEX, FP64, tables up to ~2400 values.  Asynchronous. */
+FFRG_API int ffrg_rhs_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
+                               double *J_dev, void *stream);
+
+/* Linearly implicit flow of the d=4 feedback state (the three tables, as for
+ * ffrg_flow with feedback = 1) with ROS2 (Verwer, Spee, Blom, Hundsdorfer
+ * 1999; the paper's implicit steppers use Jacobians, Sec. 5.2.1 / 5.2.2):
+ * W = I - gamma h J, gamma = 1 + 1/sqrt(2), J = d(d_t y)/dy from
+ * ffrg_rhs_jacobian; error estimate from the embedded first-order solution,
+ * step-size exponent 1/2; FP64 throughout.  Synchronous; state_dev as for
+ * ffrg_flow; stats->jac_evals counts Jacobians.  3 n_pts <= 4096. */
+FFRG_API int ffrg_rosenbrock_flow(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double Lambda,
+                                  double *state_dev, const ffrg_step_opts *opts, ffrg_flow_stats *stats, void *stream);
+
 /* Length of the flow state for (pb, feedback); -1 on a bad combination. */
 FFRG_API int ffrg_flow_state_size(const ffrg_problem *pb, const ffrg_table_desc *desc, int feedback);
 

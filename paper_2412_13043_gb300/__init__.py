@@ -59,7 +59,8 @@ class StepOpts(ctypes.Structure):
 
 class FlowStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("rejects", ctypes.c_longlong), ("rhs_evals", ctypes.c_longlong),
-                ("integrand_evals", ctypes.c_double), ("t_reached", ctypes.c_double)]
+                ("integrand_evals", ctypes.c_double), ("t_reached", ctypes.c_double),
+                ("jac_evals", ctypes.c_longlong)]
 
 
 class ServeOpts(ctypes.Structure):
@@ -95,6 +96,9 @@ _SIGS = {
     "ffrg_rhs_adjoint": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P, _I, _P]),
     "ffrg_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _I, _D, _P, ctypes.POINTER(StepOpts), _I,
                        ctypes.POINTER(FlowStats), _P]),
+    "ffrg_rhs_jacobian": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P]),
+    "ffrg_rosenbrock_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, ctypes.POINTER(StepOpts),
+                                  ctypes.POINTER(FlowStats), _P]),
     "ffrg_flow_state_size": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(TableDesc), _I]),
     "ffrg_status_read": (_I, [_P, _P]),
     "ffrg_set_profiling": (_I, [_P, _I]),
@@ -379,6 +383,33 @@ class Context:
         _check(self.handle, load().ffrg_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n)),
                "ffrg_profile_read")
         return ms.value, n.value
+
+    def rhs_jacobian(self, pb, tables: Tables, k: float, J=None, stream=None):
+        """d out_e / d T_j as a CUDA float64 tensor [n_ext, table values]."""
+        import torch
+        c = to_problem(pb)
+        n = tables.desc.n_tables * tables.desc.n_stack * tables.desc.n_pts
+        if J is None:
+            J = torch.empty(load().ffrg_n_ext(ctypes.byref(c)), n, dtype=torch.float64, device=f"cuda:{self.device}")
+        code = load().ffrg_rhs_jacobian(self.handle, ctypes.byref(c), tables.handle, float(k), _dev_ptr(J, "J"),
+                                        _stream_handle(stream))
+        _check(self.handle, code, "ffrg_rhs_jacobian")
+        return J
+
+    def rosenbrock_flow(self, pb, tables: Tables, state, Lambda: float, t1: float, t0: float = 0.0,
+                        dt0: float = 1e-2, dt_min: float = 1e-10, dt_max: float = 0.5, atol: float = 1e-12,
+                        rtol: float = 1e-8, max_steps: int = 1_000_000, stream=None, raise_on_error: bool = True):
+        """ROS2 flow of the d=4 feedback state (CUDA float64 tensor, overwritten)."""
+        c = to_problem(pb)
+        o = StepOpts(t0, t1, dt0, dt_min, dt_max, atol, rtol, max_steps)
+        st = FlowStats()
+        code = load().ffrg_rosenbrock_flow(self.handle, ctypes.byref(c), tables.handle, float(Lambda),
+                                           _dev_ptr(state, "state"), ctypes.byref(o), ctypes.byref(st),
+                                           _stream_handle(stream))
+        if raise_on_error:
+            _check(self.handle, code, "ffrg_rosenbrock_flow")
+        return dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals, jac_evals=st.jac_evals,
+                    integrand_evals=st.integrand_evals, t_reached=st.t_reached, status=code)
 
     def status_read(self, stream=None) -> int:
         return load().ffrg_status_read(self.handle, _stream_handle(stream))

@@ -28,7 +28,29 @@ struct AdjArgs {
   RhsArgs a;
   const double *gbar;  // [n_ext]
   double *gpart;       // [grid][tab_count]
+  double *jrows;       // Jacobian mode: one gradient row per work item [n_items][tab_count]
 };
+
+// Jacobian mode: clear the warp-private gradients before a work item ...
+__device__ __forceinline__ void jac_item_begin(const AdjArgs &A, double *grad) {
+  if (!A.jrows) return;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < nw * A.a.tab_count; i += blockDim.x) grad[i] = 0.0;
+  __syncthreads();
+}
+
+// ... and sum them (warps in order) into the item's row after it.
+__device__ __forceinline__ void jac_item_end(const AdjArgs &A, const double *grad, int item) {
+  if (!A.jrows) return;
+  __syncthreads();
+  const int nw = blockDim.x >> 5, T = A.a.tab_count;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += grad[(size_t)w * T + i];
+    A.jrows[(size_t)item * T + i] = s;
+  }
+}
 
 // lanes add in turn: lane 0 first, lane 31 last
 __device__ __forceinline__ void warp_scatter2(double *g, int i0, double v0, double v1, int lane) {
@@ -88,6 +110,7 @@ __device__ bool adj_prologue(const RhsArgs &a, AdjSmem &S, uint64_t *bar) {
 }
 
 __device__ void adj_epilogue(const AdjArgs &A, AdjSmem &S) {
+  if (A.jrows) return;
   __syncthreads();
   const RhsArgs &a = A.a;
   const int nw = blockDim.x >> 5;
@@ -119,7 +142,8 @@ __global__ void __launch_bounds__(kAdjThreads) d3_adjoint(AdjArgs A) {
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int e = item / a.n_chunks, c = item - e * a.n_chunks;
     const double p = (e < a.n_ext_p) ? ext_momentum(a, e) : 0.0;
-    const double gn = A.gbar[e] * a.norm;
+    const double gn = (A.jrows ? 1.0 : A.gbar[e]) * a.norm;
+    jac_item_begin(A, S.grad);
     const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
     const int rows = (o1 - o0) * nblk;
     for (int base = warp * 32; base < rows; base += blockDim.x) {
@@ -157,6 +181,7 @@ __global__ void __launch_bounds__(kAdjThreads) d3_adjoint(AdjArgs A) {
       }
       warp_scatter2(g, iq, q0, q1, lane);
     }
+    jac_item_end(A, S.grad, item);
   }
   adj_epilogue(A, S);
 }
@@ -195,7 +220,8 @@ __global__ void __launch_bounds__(kAdjThreads) d4_adjoint(AdjArgs A) {
     const double cpsi = block == 1 ? a.psi_x[jp] : 1.0, spsi = sqrt(fmax(0.0, 1.0 - cpsi * cpsi));
     const double p2 = p * p, C2 = 2.0 * p2 * (1.0 + cpsi);
     const double coef = block == 1 ? 3.0 : (block == 2 ? 1.5 : 1.0);
-    const double gn = A.gbar[e] * a.norm * coef;
+    const double gn = (A.jrows ? 1.0 : A.gbar[e]) * a.norm * coef;
+    jac_item_begin(A, S.grad);
     const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
     const int rows = (o1 - o0) * a.na1;
     for (int base = warp * 32; base < rows; base += blockDim.x) {
@@ -256,6 +282,7 @@ __global__ void __launch_bounds__(kAdjThreads) d4_adjoint(AdjArgs A) {
       const double cq = valid ? gn * dF * w1 * v : 0.0;
       warp_scatter2(g, oZ + pq.i0, (1.0 - pq.w) * cq, pq.w * cq, lane);
     }
+    jac_item_end(A, S.grad, item);
   }
   adj_epilogue(A, S);
 }
@@ -273,6 +300,83 @@ __global__ void adj_reduce_kernel(const double *gpart, int grid, int count, doub
 
 using namespace ffrg;
 
+namespace ffrg {
+
+// fixed-order sum of the chunk rows of each external point: J[e][j]
+__global__ void jac_reduce_kernel(const double *jrows, int n_ext, int n_chunks, int T, double *J) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n_ext * T) return;
+  const int e = (int)(idx / T), j = (int)(idx % T);
+  double s = 0.0;
+  for (int c = 0; c < n_chunks; ++c) s += jrows[((size_t)e * n_chunks + c) * T + j];
+  J[idx] = s;
+}
+
+// Launch geometry, shared memory and scratch of the adjoint kernels of a plan.
+static int adjoint_setup(ffrg_ctx *ctx, Plan *pl, int model, void (**kern_out)(AdjArgs)) {
+  void (*kern)(AdjArgs) = model == FFRG_MODEL_D3 ? d3_adjoint : d4_adjoint;
+  *kern_out = kern;
+  if (pl->adj_grid) return FFRG_OK;
+  const int nw = kAdjThreads / 32;
+  size_t smem = (((size_t)pl->tab_count * 8 + 15) & ~(size_t)15) +
+                ((((size_t)(3 * pl->na1 + 2 * pl->na2)) * 8 + 15) & ~(size_t)15) + (size_t)nw * pl->tab_count * 8;
+  if (smem > 200 * 1024) {
+    ctx->last_error = "adjoint: tables too large for per-warp shared-memory gradients";
+    return FFRG_EINVAL;
+  }
+  int st = ensure_smem_limit(ctx, (const void *)kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, smem);
+  if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
+  int grid = std::max(1, std::min(pl->n_items, per_sm * ctx->num_sms));
+  st = dev_alloc(ctx, (void **)&pl->radD, (size_t)pl->nr * (2 * pl->N + 1) * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->gpart, (size_t)grid * pl->tab_count * sizeof(double));
+  if (st) return st;
+  pl->adj_smem = smem;
+  pl->adj_grid = grid;
+  return FFRG_OK;
+}
+
+// Full Jacobian d out_e / d T_j (row-major n_ext x table values) at scale k.
+int launch_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, const double *tab, double k,
+                    double *J, cudaStream_t s) {
+  if (pb->model != FFRG_MODEL_D3 && pb->model != FFRG_MODEL_D4_VERTEX) return FFRG_EINVAL;
+  int st = validate_problem(pb, td);
+  if (st) return st;
+  Plan *pl = nullptr;
+  st = get_plan(ctx, pb, td, &pl);
+  if (st) return st;
+  void (*kern)(AdjArgs) = nullptr;
+  st = adjoint_setup(ctx, pl, pb->model, &kern);
+  if (st) return st;
+  if (!pl->jrows) {
+    st = dev_alloc(ctx, (void **)&pl->jrows, (size_t)pl->n_items * pl->tab_count * sizeof(double));
+    if (st) return st;
+  }
+  AdjArgs A;
+  memset(&A, 0, sizeof(A));
+  fill_args(pl, pb, td, tab, k, A.a);
+  A.a.status = ctx->status_dev;
+  A.a.radD = pl->radD;
+  A.jrows = pl->jrows;
+  st = launch_precompute(ctx, A.a, s);
+  if (st) return st;
+  kern<<<pl->adj_grid, kAdjThreads, pl->adj_smem, s>>>(A);
+  const size_t tot = (size_t)pl->n_ext * pl->tab_count;
+  jac_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(pl->jrows, pl->n_ext, pl->n_chunks, pl->tab_count, J);
+  return set_cuda_error(ctx, cudaGetLastError(), "jacobian launch");
+}
+
+}  // namespace ffrg
+
+extern "C" int ffrg_rhs_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
+                                 double *J_dev, void *stream) {
+  if (!ctx || !pb || !tables || !J_dev || !(k > 0.0) || !isfinite(k)) return FFRG_EINVAL;
+  cudaSetDevice(ctx->device);
+  return launch_jacobian(ctx, pb, &tables->desc, tables->dev, k, J_dev, (cudaStream_t)stream);
+}
+
 extern "C" int ffrg_rhs_adjoint(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
                                 const double *gbar_dev, double *tbar_dev, int precision, void *stream) {
   if (!ctx || !pb || !tables || !gbar_dev || !tbar_dev) return FFRG_EINVAL;
@@ -286,28 +390,11 @@ extern "C" int ffrg_rhs_adjoint(ffrg_ctx *ctx, const ffrg_problem *pb, const ffr
   st = get_plan(ctx, pb, &tables->desc, &pl);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  void (*kern)(AdjArgs) = pb->model == FFRG_MODEL_D3 ? d3_adjoint : d4_adjoint;
-  if (!pl->adj_grid) {
-    const int nw = kAdjThreads / 32;
-    size_t smem = (((size_t)pl->tab_count * 8 + 15) & ~(size_t)15) +
-                  ((((size_t)(3 * pl->na1 + 2 * pl->na2)) * 8 + 15) & ~(size_t)15) + (size_t)nw * pl->tab_count * 8;
-    if (smem > 200 * 1024) {
-      ctx->last_error = "adjoint: tables too large for per-warp shared-memory gradients";
-      return FFRG_EINVAL;
-    }
-    st = ensure_smem_limit(ctx, (const void *)kern, smem);
-    if (st) return st;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, smem);
-    if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
-    int grid = std::max(1, std::min(pl->n_items, per_sm * ctx->num_sms));
-    st = dev_alloc(ctx, (void **)&pl->radD, (size_t)pl->nr * (2 * pl->N + 1) * sizeof(double));
-    if (!st) st = dev_alloc(ctx, (void **)&pl->gpart, (size_t)grid * pl->tab_count * sizeof(double));
-    if (st) return st;
-    pl->adj_smem = smem;
-    pl->adj_grid = grid;
-  }
+  void (*kern)(AdjArgs) = nullptr;
+  st = adjoint_setup(ctx, pl, pb->model, &kern);
+  if (st) return st;
   AdjArgs A;
+  memset(&A, 0, sizeof(A));
   fill_args(pl, pb, &tables->desc, tables->dev, k, A.a);
   A.a.status = ctx->status_dev;
   A.a.radD = pl->radD;

@@ -173,7 +173,7 @@ static int upload_rule(ffrg_ctx *ctx, const std::vector<double> &h, double **d) 
 static void plan_free(ffrg_ctx *ctx, Plan *pl) {
   if (!pl) return;
   double *arrs[] = {pl->rad_x, pl->rad_w, pl->a1_x, pl->a1_w, pl->a2_x, pl->a2_w, pl->psi_x, pl->psi_w,
-                    pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s};
+                    pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s, pl->jrows};
   for (double *p : arrs) dev_free(ctx, p, 0);
   dev_free(ctx, pl->tab32, 0);
   delete pl;
@@ -366,7 +366,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
   for (auto &kv : ctx->plans) {
     Plan *pl = kv.second;
     double *arrs[] = {pl->rad_x, pl->rad_w, pl->a1_x, pl->a1_w, pl->a2_x, pl->a2_w, pl->psi_x, pl->psi_w,
-                      pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s};
+                      pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s, pl->jrows};
     for (double *p : arrs) cudaFree(p);
     cudaFree(pl->tab32);
     delete pl;

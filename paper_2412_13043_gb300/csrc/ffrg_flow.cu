@@ -247,6 +247,194 @@ int launch_flow_batched_step(ffrg_ctx *ctx, const FlowArgs *fa, int n, int max_n
   return set_cuda_error(ctx, cudaGetLastError(), "batched flow step");
 }
 
+// ---------------------------------------------------------------------------
+// Linearly implicit ROS2 flow (Verwer, Spee, Blom, Hundsdorfer 1999) of the
+// d=4 feedback state, gamma = 1 + 1/sqrt(2):
+//   W = I - gamma h J,  W k1 = f(t, y),  W k2 = f(t + h, y + h k1) - 2 k1,
+//   y_new = y + h (3/2 k1 + 1/2 k2),  error estimate y_new - (y + h k1).
+// J = d(d_t y)/dy from the table Jacobian of the RHS (reverse-mode kernels)
+// mapped like the derivative; dense LU with partial pivoting in one CTA.
+// ---------------------------------------------------------------------------
+constexpr double kRosGamma = 1.7071067811865475244;
+
+// W[i][j] = delta_ij - gh (M Jraw)[i][j], M = the map raw -> d_t y (d=4 feedback)
+__global__ void ros_build_w_kernel(FlowArgs f, const double *Jraw, double gh, double *W) {
+  const int ny = f.ny, n = f.n, npsi = f.npsi;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)ny * ny) return;
+  const int i = (int)(idx / ny), j = (int)(idx % ny);
+  double m;
+  if (i < n) {
+    const double p = ext_p(f, i);
+    m = -(Jraw[(size_t)i * ny + j] - Jraw[(size_t)n * ny + j]) / (p * p);
+  } else if (i < 2 * n) {
+    double s = 0.0;
+    for (int q = 0; q < npsi; ++q) s += 0.5 * f.psi_w[q] * Jraw[(size_t)(n + 1 + (i - n) * npsi + q) * ny + j];
+    m = -s;
+  } else {
+    m = -Jraw[(size_t)(n + 1 + n * npsi + (i - 2 * n)) * ny + j];
+  }
+  W[idx] = (i == j ? 1.0 : 0.0) - gh * m;
+}
+
+// In-place LU with partial pivoting (one CTA); a zero pivot stops the flow.
+__global__ void __launch_bounds__(1024) lu_kernel(double *W, int n, int *piv, FlowCtl *ctl) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ int p_s;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bidx = n;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = fabs(W[(size_t)i * n + k]);
+      if (v > best || (v == best && i < bidx)) { best = v; bidx = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bidx, o);
+      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int p = n;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+      p_s = (b > 0.0 && isfinite(b)) ? p : -1;
+      piv[k] = p;
+      if (p_s < 0) { ctl->status = FFRG_ENONFINITE; ctl->done = 1; }
+    }
+    __syncthreads();
+    const int p = p_s;
+    if (p < 0) return;
+    if (p != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double t = W[(size_t)k * n + j];
+        W[(size_t)k * n + j] = W[(size_t)p * n + j];
+        W[(size_t)p * n + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / W[(size_t)k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) W[(size_t)i * n + k] *= inv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
+      const int i = k + 1 + q / m, j = k + 1 + q % m;
+      W[(size_t)i * n + j] -= W[(size_t)i * n + k] * W[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+}
+
+// x = W^{-1} b with the factors of lu_kernel (one CTA); x may alias b.
+__global__ void __launch_bounds__(1024) lu_solve_kernel(const double *W, const int *piv, int n, const double *b,
+                                                        double *x, const FlowCtl *ctl) {
+  if (*(volatile const int *)&ctl->done) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = b[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < n; ++k)
+      if (piv[k] != k) {
+        const double t = x[k];
+        x[k] = x[piv[k]];
+        x[piv[k]] = t;
+      }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {  // unit lower triangle
+    const double xj = x[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) x[i] -= W[(size_t)i * n + j] * xj;
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {  // upper triangle
+    if (threadIdx.x == 0) x[j] /= W[(size_t)j * n + j];
+    __syncthreads();
+    const double xj = x[j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) x[i] -= W[(size_t)i * n + j] * xj;
+    __syncthreads();
+  }
+}
+
+// f = d_t y from the raw RHS (out), optionally minus 2 k1
+__global__ void ros_map_kernel(FlowArgs f, double *out, const double *k1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= f.ny) return;
+  double v = deriv_component(f, i);
+  if (k1) v -= 2.0 * k1[i];
+  out[i] = v;
+}
+
+// y1 = y + h k1 (also the tables of the second stage)
+__global__ void ros_stage_kernel(FlowArgs f, const double *k1) {
+  const FlowCtl *c = f.ctl;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= f.ny) return;
+  const double v = f.y[i] + c->h * k1[i];
+  f.ys[i] = v;
+  f.tabbuf[i] = v;
+}
+
+// combine, error estimate, accept / reject, step size (exponent 1/2), next h
+__global__ void __launch_bounds__(1024) ros_control_kernel(FlowArgs f, const double *k1, const double *k2) {
+  FlowCtl *c = f.ctl;
+  __shared__ double red[32];
+  __shared__ int bad_s[32];
+  __shared__ int acc_s;
+  if (*(volatile const int *)&c->done) return;
+  const double h = c->h;
+  double emax = 0.0;
+  int bad = 0;
+  for (int i = threadIdx.x; i < f.ny; i += blockDim.x) {
+    const double yn = f.y[i] + h * (1.5 * k1[i] + 0.5 * k2[i]);
+    const double e = fabs(yn - f.ys[i]) / (c->atol + c->rtol * fmax(fabs(f.y[i]), fabs(yn)));
+    if (!isfinite(e)) bad = 1;
+    else emax = fmax(emax, e);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
+    bad |= __shfl_down_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = emax; bad_s[threadIdx.x >> 5] = bad; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double err = 0.0;
+    int anybad = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { err = fmax(err, red[w]); anybad |= bad_s[w]; }
+    c->err = err;
+    int acc = 0;
+    if (anybad) {
+      c->status = FFRG_ENONFINITE;
+      c->done = 1;
+    } else if (err <= 1.0) {
+      acc = 1;
+      c->t += h;
+      c->steps += 1;
+      double fac = (err == 0.0) ? 5.0 : 0.9 * pow(err, -0.5);
+      fac = fmin(fmax(fac, 0.2), 5.0);
+      if (c->last_rejected) fac = fmin(fac, 1.0);
+      c->last_rejected = 0;
+      c->dt = h * fac;
+    } else {
+      c->rejects += 1;
+      if (h <= c->dt_min) {
+        c->status = FFRG_ESTEP_UNDERFLOW;
+        c->done = 1;
+      } else {
+        c->dt = h * fmax(0.9 * pow(err, -0.5), 0.2);
+        c->last_rejected = 1;
+      }
+    }
+    c->dt = fmin(fmax(c->dt, c->dt_min), c->dt_max);
+    c->accepted = acc;
+    acc_s = acc;
+  }
+  __syncthreads();
+  if (acc_s)
+    for (int i = threadIdx.x; i < f.ny; i += blockDim.x) f.y[i] = f.y[i] + h * (1.5 * k1[i] + 0.5 * k2[i]);
+  __syncthreads();
+  if (threadIdx.x == 0 && !c->done) decide_next_step(c);
+}
+
 static int flow_mode(const ffrg_problem *pb, int feedback) {
   if (!feedback) return kModeFrozen;
   if (pb->model == FFRG_MODEL_D3) return kModeD3Feedback;
@@ -415,6 +603,7 @@ extern "C" int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_ta
       stats->rhs_evals = 1 + 6 * attempts_done;
       stats->integrand_evals = (double)stats->rhs_evals * ffrg_evals(&pb);
       stats->t_reached = ctl_host->t;
+      stats->jac_evals = 0;
     }
     st = ctl_host->status;
     // order the caller's stream after the flow
@@ -431,5 +620,152 @@ extern "C" int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_ta
   dev_free(ctx, K, (size_t)7 * ny * sizeof(double));
   dev_free(ctx, raw, (size_t)n_ext * sizeof(double));
   dev_free(ctx, tabbuf, tab_bytes);
+  return st;
+}
+
+extern "C" int ffrg_rosenbrock_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_tables *tables,
+                                    double Lambda, double *state_dev, const ffrg_step_opts *o, ffrg_flow_stats *stats,
+                                    void *stream) {
+  if (!ctx || !pb_in || !tables || !state_dev || !o) return FFRG_EINVAL;
+  if (!(Lambda > 0.0) || !isfinite(Lambda)) return FFRG_EINVAL;
+  if (!(o->t1 >= o->t0) || !(o->dt0 > 0.0) || !(o->dt_min > 0.0) || !(o->dt_max >= o->dt_min) || !(o->atol >= 0.0) ||
+      !(o->rtol >= 0.0) || !(o->atol + o->rtol > 0.0) || o->max_steps < 1)
+    return FFRG_EINVAL;
+  ffrg_problem pb = *pb_in;
+  const ffrg_table_desc *td = &tables->desc;
+  if (pb.model != FFRG_MODEL_D4_VERTEX) return FFRG_EINVAL;
+  int st = validate_problem(&pb, td);
+  if (st) return st;
+  if (pb.n_ext_p != td->n_pts || pb.p_min != td->x_min || pb.p_max != td->x_max) return FFRG_EINVAL;
+  const int ny = 3 * td->n_pts;
+  if (ny > 4096) return FFRG_EINVAL;
+  cudaSetDevice(ctx->device);
+  Plan *pl = nullptr;
+  st = get_plan(ctx, &pb, td, &pl);
+  if (st) return st;
+  const int ne = pl->n_ext;
+  cudaStream_t user = (cudaStream_t)stream;
+  FlowCtl *ctl = nullptr, *hc_pin = nullptr;
+  double *f0 = nullptr, *k1 = nullptr, *k2 = nullptr, *ys = nullptr, *raw = nullptr, *tab = nullptr, *Jraw = nullptr,
+         *W = nullptr;
+  int *piv = nullptr;
+  const size_t d = sizeof(double);
+  st = dev_alloc(ctx, (void **)&ctl, sizeof(FlowCtl));
+  if (!st) st = dev_alloc(ctx, (void **)&f0, ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&k1, ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&k2, ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&ys, ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&raw, ne * d);
+  if (!st) st = dev_alloc(ctx, (void **)&tab, (ny * d + 255) & ~(size_t)255);
+  if (!st) st = dev_alloc(ctx, (void **)&Jraw, (size_t)ne * ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&W, (size_t)ny * ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&piv, ny * sizeof(int));
+  if (!st) st = set_cuda_error(ctx, cudaMallocHost((void **)&hc_pin, sizeof(FlowCtl)), "cudaMallocHost");
+  FlowCtl hc;
+  memset(&hc, 0, sizeof(hc));
+  hc.t = o->t0;
+  hc.t0 = o->t0;
+  hc.t1 = o->t1;
+  hc.dt = fmin(fmax(o->dt0, o->dt_min), o->dt_max);
+  hc.dt_min = o->dt_min;
+  hc.dt_max = o->dt_max;
+  hc.atol = o->atol;
+  hc.rtol = o->rtol;
+  hc.end_tol = 1e-13 * fmax(fabs(o->t1 - o->t0), 1.0);
+  hc.Lambda = Lambda;
+  hc.max_steps = o->max_steps;
+  FlowArgs f;
+  memset(&f, 0, sizeof(f));
+  f.ny = ny;
+  f.mode = kModeD4Feedback;
+  f.n = td->n_pts;
+  f.npsi = pb.n_ext_ang;
+  f.tab_len = ny;
+  f.p_min = pb.p_min;
+  f.p_step = pb.n_ext_p > 1 ? log(pb.p_max / pb.p_min) / (pb.n_ext_p - 1) : 0.0;
+  f.psi_w = pl->psi_w;
+  f.y = state_dev;
+  f.ys = ys;
+  f.raw = raw;
+  f.tabbuf = tab;
+  f.ctl = ctl;
+  const int eb = 256, eg = (ny + eb - 1) / eb;
+  long long rhs_calls = 0, jacs = 0;
+  // RHS (FP64) of the tables in `tab` at scale k into raw
+  auto rhs_at = [&](double k) {
+    RhsArgs a;
+    fill_args(pl, &pb, td, tab, k, a);
+    a.out = raw;
+    a.status = ctx->status_dev;
+    ++rhs_calls;
+    return launch_rhs(ctx, pl, a, FFRG_FP64, user);
+  };
+  auto read_ctl = [&]() {
+    cudaError_t e = cudaMemcpyAsync(hc_pin, ctl, sizeof(FlowCtl), cudaMemcpyDeviceToHost, user);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(user);
+    return set_cuda_error(ctx, e, "rosenbrock sync");
+  };
+  if (!st) st = set_cuda_error(ctx, cudaMemcpyAsync(ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, user), "ctl");
+  if (!st) st = set_cuda_error(ctx, cudaMemcpyAsync(tab, state_dev, ny * d, cudaMemcpyDeviceToDevice, user), "tab");
+  if (!st) st = rhs_at(Lambda * exp(-o->t0));
+  if (!st) {
+    ros_map_kernel<<<eg, eb, 0, user>>>(f, f0, nullptr);
+    flow_start_kernel<<<1, 32, 0, user>>>(ctl);
+    st = read_ctl();
+  }
+  bool need_jac = true;
+  while (!st && !hc_pin->done) {
+    const double t = hc_pin->t, h = hc_pin->h;
+    if (need_jac) {
+      st = launch_jacobian(ctx, &pb, td, tab, Lambda * exp(-t), Jraw, user);
+      ++jacs;
+      need_jac = false;
+      if (st) break;
+    }
+    const size_t nn = (size_t)ny * ny;
+    ros_build_w_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, user>>>(f, Jraw, kRosGamma * h, W);
+    lu_kernel<<<1, 1024, 0, user>>>(W, ny, piv, ctl);
+    lu_solve_kernel<<<1, 1024, 0, user>>>(W, piv, ny, f0, k1, ctl);
+    ros_stage_kernel<<<eg, eb, 0, user>>>(f, k1);
+    st = rhs_at(Lambda * exp(-(t + h)));
+    if (st) break;
+    ros_map_kernel<<<eg, eb, 0, user>>>(f, k2, k1);
+    lu_solve_kernel<<<1, 1024, 0, user>>>(W, piv, ny, k2, k2, ctl);
+    ros_control_kernel<<<1, 1024, 0, user>>>(f, k1, k2);
+    st = read_ctl();
+    if (st) break;
+    if (hc_pin->accepted && !hc_pin->done) {
+      st = set_cuda_error(ctx, cudaMemcpyAsync(tab, state_dev, ny * d, cudaMemcpyDeviceToDevice, user), "tab");
+      if (!st) st = rhs_at(Lambda * exp(-hc_pin->t));
+      if (!st) ros_map_kernel<<<eg, eb, 0, user>>>(f, f0, nullptr);
+      need_jac = true;
+    } else if (!hc_pin->done) {
+      // rejected: same Jacobian, stage tables back to the current state
+      st = set_cuda_error(ctx, cudaMemcpyAsync(tab, state_dev, ny * d, cudaMemcpyDeviceToDevice, user), "tab");
+    }
+  }
+  if (!st) {
+    if (stats) {
+      stats->steps = hc_pin->steps;
+      stats->rejects = hc_pin->rejects;
+      stats->rhs_evals = rhs_calls;
+      stats->integrand_evals = (double)rhs_calls * ffrg_evals(&pb);
+      stats->t_reached = hc_pin->t;
+      stats->jac_evals = jacs;
+    }
+    st = hc_pin->status;
+  }
+  cudaStreamSynchronize(user);
+  if (hc_pin) cudaFreeHost(hc_pin);
+  dev_free(ctx, ctl, sizeof(FlowCtl));
+  dev_free(ctx, f0, ny * d);
+  dev_free(ctx, k1, ny * d);
+  dev_free(ctx, k2, ny * d);
+  dev_free(ctx, ys, ny * d);
+  dev_free(ctx, raw, ne * d);
+  dev_free(ctx, tab, (ny * d + 255) & ~(size_t)255);
+  dev_free(ctx, Jraw, (size_t)ne * ny * d);
+  dev_free(ctx, W, (size_t)ny * ny * d);
+  dev_free(ctx, piv, ny * sizeof(int));
   return st;
 }

@@ -323,6 +323,7 @@ struct Plan {
   double *radF, *radq, *partial, *ext_pd, *psi_s;
   float *tab32;
   double *radD, *gpart;     // adjoint scratch (allocated on first use)
+  double *jrows;            // Jacobian rows per work item (allocated on first use)
   int adj_grid;
   size_t adj_smem;
   std::vector<double> psi_w_host;
@@ -352,7 +353,7 @@ struct FlowCtl {
   double t, dt, h, t0, t1, dt_min, dt_max, atol, rtol, end_tol, Lambda;
   double k_stage, m2_stage, err;
   long long steps, rejects, max_steps;
-  int last_rejected, done, status, pad;
+  int last_rejected, done, status, accepted;
 };
 
 struct FlowArgs {
@@ -384,5 +385,7 @@ int host_gauss_chebyshev2(int n, double *x, double *w);
 // kernels launched from several translation units (ffrg_rhs.cu)
 int launch_rhs(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s);
 int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s);
+int launch_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, const double *tab, double k,
+                    double *J, cudaStream_t s);
 
 }  // namespace ffrg

@@ -115,3 +115,41 @@ def test_adjoint_rejects_unsupported(ctx):
         ctx.rhs_adjoint(wl1.problem, t1, 1.0, g1, precision=ffrg.MIXED)
     tabs.free()
     t1.free()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_jacobian_matches_oracle(ctx, name):
+    wl = CASES[name]()
+    k = 0.9
+    tabs = ctx.tables(wl.problem, wl.tables)
+    J = ctx.rhs_jacobian(wl.problem, tabs, k).cpu().numpy()
+    tabs.free()
+    ref = oracle.rhs_jacobian(wl.problem, wl.tables, k)
+    assert np.max(np.abs(J - ref)) / np.max(np.abs(ref)) < 1e-12
+
+
+def test_rosenbrock_flow_matches_oracle_ros2_and_dp45():
+    """ROS2 on the device (Jacobian from the reverse-mode kernels, LU on the
+    device) against the oracle's ROS2 and a tight DP5(4) reference."""
+    import math
+
+    import torch
+
+    import paper_2412_13043_gb300 as ffrg
+    c = gpu_context()
+    wl = fi.make_d4(seed=6, n_pts=8, n_ext_ang=2, n_rad=8, n_ang1=4, n_ang2=3)
+    pb = wl.problem
+    pb.p_min = pb.x_min = 0.05
+    t1 = 2.0
+    ref, _ = oracle.flow(pb, wl.tables, wl.y0, wl.Lambda, t1, feedback=1, rtol=1e-12, atol=1e-14)
+    yo, so = oracle.ros2_flow(pb, wl.y0, wl.Lambda, t1, rtol=1e-8, atol=1e-12)
+    tabs = c.tables(pb, wl.tables)
+    y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+    st = c.rosenbrock_flow(pb, tabs, y, wl.Lambda, t1, rtol=1e-8, atol=1e-12)
+    tabs.free()
+    c.close()
+    yg = y.cpu().numpy()
+    assert st["status"] == ffrg.OK and st["jac_evals"] >= st["steps"]
+    assert abs(st["steps"] - so["steps"]) <= 2
+    assert np.max(np.abs(yg - yo) / np.abs(yo)) < 1e-9      # same method, same decisions
+    assert np.max(np.abs(yg - ref) / np.abs(ref)) < 2e-6     # second-order accuracy at rtol 1e-8
