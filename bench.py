@@ -231,6 +231,44 @@ def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
             "saturation_latency_p50_s": sorted(lat_sat.values())[len(lat_sat) // 2]}
 
 
+def implicit_bench(ctx):
+    """Linearly implicit ROS2 (Jacobian from the adjoint kernels) vs
+    explicit DP5(4), both FP64, on the d=4 feedback flow, at matched endpoint
+    error against a tight DP5(4) reference."""
+    import numpy as np
+    import torch
+
+    import ffrg_inputs as fi
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d4(seed=6, n_pts=32, n_ext_ang=4, n_rad=32, n_ang1=16, n_ang2=8)
+    pb = wl.problem
+    pb.p_min = pb.x_min = 0.01
+    t1 = math.log(wl.Lambda / wl.k_end)
+    tabs = ctx.tables(pb, wl.tables)
+
+    def run(kind, rtol):
+        y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        if kind == "dp45":
+            st = ctx.flow(pb, tabs, y, wl.Lambda, t1, feedback=1, precision=ffrg.FP64, rtol=rtol, atol=1e-14)
+        else:
+            st = ctx.rosenbrock_flow(pb, tabs, y, wl.Lambda, t1, rtol=rtol, atol=1e-14)
+        torch.cuda.synchronize()
+        return y.cpu().numpy(), time.perf_counter() - t, st
+
+    ref, _, _ = run("dp45", 1e-12)
+    rows = []
+    for kind, rtol in (("dp45", 1e-6), ("dp45", 1e-8), ("ros2", 1e-5), ("ros2", 1e-6), ("ros2", 1e-7)):
+        y, dt, st = run(kind, rtol)
+        rows.append({"method": kind, "rtol": rtol, "endpoint_rel_err": float(np.max(np.abs(y - ref) / np.abs(ref))),
+                     "steps": st["steps"], "rejects": st["rejects"], "rhs_evals": st["rhs_evals"],
+                     "jacobians": st["jac_evals"], "seconds": dt})
+    tabs.free()
+    return {"workload": "d4 feedback flow, 32-pt tables, 4 ext angles, 32 x 16 x 8 nodes, k: 10 -> 0.01, FP64",
+            "runs": rows}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -421,6 +459,10 @@ def main():
     if not args.no_serve:
         serving = serving_bench(ctx, args.serve_requests)
 
+    implicit = None
+    if not args.no_flows:
+        implicit = implicit_bench(ctx)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, stride=4)
@@ -443,6 +485,7 @@ def main():
             "clocks": clocks,
             "flows": flows,
             "serving": serving,
+            "implicit_vs_explicit": implicit,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

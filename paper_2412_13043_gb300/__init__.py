@@ -328,7 +328,7 @@ class Context:
                                 _stream_handle(stream))
         if raise_on_error:
             _check(self.handle, code, "ffrg_flow")
-        return dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals,
+        return dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals, jac_evals=st.jac_evals,
                     integrand_evals=st.integrand_evals, t_reached=st.t_reached, status=code)
 
     # ---- serving (continuous batching of flow requests) ----

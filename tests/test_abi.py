@@ -89,7 +89,7 @@ def test_flow_state_size():
 
 
 def test_strerror_covers_codes():
-    for c in range(11):
+    for c in range(12):
         assert ffrg.strerror(c)
     assert "unknown" in ffrg.strerror(99)
 
