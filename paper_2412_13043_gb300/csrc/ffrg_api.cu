@@ -251,16 +251,17 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->partial, (size_t)pl->n_items * sizeof(double));
-  if (!st) st = dev_alloc(ctx, (void **)&pl->tab32, ((size_t)pl->tab_count + 4) * sizeof(float));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->tab32, (size_t)pl->tab_count * sizeof(float2));
   if (st) {
     plan_free(ctx, pl);
     return st;
   }
-  // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
+  // shared memory: tables (FP64 values or FP32 node pairs, 8 bytes a node) +
+  // angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
   auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
-  pl->smem64 = al16(((size_t)pl->tab_count + 1) * 8) + al16(ang * 8);
-  pl->smem32 = al16(((size_t)pl->tab_count + 1) * 4) + al16(ang * 4);
+  pl->smem64 = al16((size_t)pl->tab_count * 8) + al16(ang * 8);
+  pl->smem32 = al16((size_t)pl->tab_count * 8) + al16(ang * 4);
   *out = pl;
   ctx->plans[key] = pl;
   return FFRG_OK;

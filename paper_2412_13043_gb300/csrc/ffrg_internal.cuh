@@ -47,7 +47,7 @@ struct RhsArgs {
   double x_min2;               // x_min^2 (lookups below x_min return the first node)
   double sum_w2;               // sum of the second-angle weights (D4)
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
-  float *tab32;                // FP32 mirror written by the precompute kernel
+  float2 *tab32;               // FP32 node pairs (T[i], T[i+1] - T[i]; 0 at a row end), precompute kernel
   const double *rad_x, *rad_w; // unit-interval GL rule on [0, 1]
   const double *a1_x, *a1_w;   // first angle rule
   const double *a2_x, *a2_w;   // second angle rule (D4)
@@ -102,23 +102,6 @@ __device__ __forceinline__ float hw_rcp(float x) {
   return y;
 }
 
-// FP32 regulator shape.  Exponential r(x) = x/(e^x - 1): for x < 1 the
-// Bernoulli series sum_n B_n x^n / n! through x^8 (1 - x/2 + x^2/12 - x^4/720
-// + x^6/30240 - x^8/1209600; the first omitted term x^10/47900160 is below
-// 2.1e-8); for 1 <= x <= 80, x / (2^(x log2 e) - 1) with the hardware exp2 and
-// reciprocal; above 80 the shape is below 1e-33 and is taken as 0.
-__device__ __forceinline__ float reg_r(int reg, float x) {
-  if (reg == FFRG_REG_LITIM) return x < 1.f ? 1.f - x : 0.f;
-  const float x2 = x * x;
-  float t = fmaf(x2, -1.0f / 1209600.0f, 1.0f / 30240.0f);
-  t = fmaf(x2, t, -1.0f / 720.0f);
-  t = fmaf(x2, t, 1.0f / 12.0f);
-  const float series = fmaf(x2, t, fmaf(x, -0.5f, 1.0f));
-  const float direct = x * hw_rcp(hw_ex2(x * 1.4426950408889634f) - 1.0f);
-  const float r = x < 1.0f ? series : direct;
-  return x > 80.f ? 0.f : r;
-}
-
 // ---------------------------------------------------------------------------
 // Log-grid lookup: u = (n-1) ln(s/x_min)/ln(x_max/x_min) = u_scale ln(s^2) + u_off,
 // clamped to [0, n-1]; linear in the value between nodes.
@@ -132,31 +115,53 @@ __device__ __forceinline__ void lerp_pos(double s2, double u_scale, double u_off
   w = u - (double)i;
 }
 
-// FP32 coordinate: u_scale here multiplies log2(s^2) (the caller folds ln 2 in,
-// see lerp_scale).  s^2 <= 0 gives log2 = -inf or NaN, both clamped to u = 0
-// (the table's first node, as for s < x_min).  floor(u) comes from adding
-// 1.5*2^23 rounded towards -inf: the sum's low mantissa bits hold floor(u); no
-// float<->int conversion instructions are needed.  At u = n-1 this gives
-// i0 = n-1, w = 0: the FP32 tables in shared memory carry one zero element
-// after the last value so that the (zero-weighted) upper neighbour is finite.
-__device__ __forceinline__ void lerp_pos(float s2, float u_scale, float u_off, int n, int &i0, float &w) {
-  float u = fmaf(u_scale, hw_lg2(s2), u_off);
-  u = fminf(fmaxf(u, 0.f), (float)(n - 1));
+// FP32 coordinate, normalised: u1 = u / (n-1) = sat(u_scale1 log2(s^2) + u_off1)
+// in one saturating FMA (the caller passes u_scale ln 2 / (n-1) and
+// u_off / (n-1), see lerp_scale / lerp_off).  s^2 <= 0 gives log2 = -inf or
+// NaN, both saturated to 0 (the first node, as for s < x_min).  floor(u) comes
+// from u1 (n-1) + 1.5*2^23 rounded towards -inf: the low mantissa bits of the
+// sum hold floor(u), so no float<->int conversion is needed.  At u = n-1 this
+// gives i0 = n-1, w = 0; the FP32 node pairs carry a zero difference there.
+__device__ __forceinline__ void lerp_pos(float s2, float u_scale1, float u_off1, int n, int &i0, float &w) {
+  const float nm1 = (float)(n - 1);
+  float u1;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u1) : "f"(u_scale1), "f"(hw_lg2(s2)), "f"(u_off1));
   const float magic = 12582912.0f;
-  const float t = __fadd_rd(u, magic);
+  const float t = __fmaf_rd(u1, nm1, magic);
   i0 = __float_as_int(t) - 0x4B400000;
-  w = u - (t - magic);
+  w = fmaf(u1, nm1, magic - t);
 }
 
-// Scale of the table coordinate for each precision: ln(s^2) for FP64,
-// log2(s^2) for FP32 (factor ln 2 folded in).
+// Scale and offset of the table coordinate for each precision: ln(s^2) and
+// u_off for FP64; log2(s^2) (factor ln 2 folded in) divided by n-1 for FP32.
 template <typename T>
-__device__ __forceinline__ T lerp_scale(double u_scale);
+__device__ __forceinline__ T lerp_scale(double u_scale, int n);
 template <>
-__device__ __forceinline__ double lerp_scale<double>(double u_scale) { return u_scale; }
+__device__ __forceinline__ double lerp_scale<double>(double u_scale, int) { return u_scale; }
 template <>
-__device__ __forceinline__ float lerp_scale<float>(double u_scale) {
-  return (float)(u_scale * 0.6931471805599453094);
+__device__ __forceinline__ float lerp_scale<float>(double u_scale, int n) {
+  return (float)(u_scale * 0.6931471805599453094 / (double)(n - 1));
+}
+template <typename T>
+__device__ __forceinline__ T lerp_off(double u_off, int n);
+template <>
+__device__ __forceinline__ double lerp_off<double>(double u_off, int) { return u_off; }
+template <>
+__device__ __forceinline__ float lerp_off<float>(double u_off, int n) {
+  return (float)(u_off / (double)(n - 1));
+}
+
+// FP32 lookup on node pairs: one 8-byte shared load and one FMA
+__device__ __forceinline__ float lerp_at(const float2 *tab, int i0, float w) {
+  const float2 v = tab[i0];
+  return fmaf(w, v.y, v.x);
+}
+
+__device__ __forceinline__ float lerp(const float2 *tab, float s2, float u_scale1, float u_off1, int n) {
+  int i0;
+  float w;
+  lerp_pos(s2, u_scale1, u_off1, n, i0, w);
+  return lerp_at(tab, i0, w);
 }
 
 template <typename T>
@@ -321,7 +326,7 @@ struct Plan {
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;
   double sum_w2;
   double *radF, *radq, *partial, *ext_pd, *psi_s;
-  float *tab32;
+  float2 *tab32;
   double *radD, *gpart;     // adjoint scratch (allocated on first use)
   double *jrows;            // Jacobian rows per work item (allocated on first use)
   int adj_grid;

@@ -128,14 +128,14 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.ext_pd = sc.take<double>(pl.n_ext_p);
   pl.psi_s = sc.take<double>(npsi);
   pl.partial = sc.take<double>(pl.n_items);
-  pl.tab32 = sc.take<float>((size_t)pl.tab_count + 4);
+  pl.tab32 = sc.take<float2>((size_t)pl.tab_count);
   if (sc.used > kNoallocScratchBytes) return FFRG_EINVAL;  // problem needs more than the 4 MiB scratch
 
   auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   size_t ang = (size_t)pl.na1 * 3 + (size_t)pl.na2 * 2;
   const bool mixed = precision == FFRG_MIXED;
-  const size_t smem = mixed ? al16(((size_t)pl.tab_count + 1) * 4) + al16(ang * 4)
-                            : al16(((size_t)pl.tab_count + 1) * 8) + al16(ang * 8);
+  const size_t smem = mixed ? al16((size_t)pl.tab_count * 8) + al16(ang * 4)
+                            : al16((size_t)pl.tab_count * 8) + al16(ang * 8);
   if (smem > 227 * 1024) return FFRG_EINVAL;
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -164,8 +164,8 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   lc.profiling = 0;
   lc.prof_used = 0;
   if (cudaDeviceGetAttribute(&lc.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FFRG_ECUDA;
-  pl.smem64 = al16(((size_t)pl.tab_count + 1) * 8) + al16(ang * 8);
-  pl.smem32 = al16(((size_t)pl.tab_count + 1) * 4) + al16(ang * 4);
+  pl.smem64 = al16((size_t)pl.tab_count * 8) + al16(ang * 8);
+  pl.smem32 = al16((size_t)pl.tab_count * 8) + al16(ang * 4);
   pl.grid64 = 0;
   pl.grid32 = 0;
   RhsArgs a;

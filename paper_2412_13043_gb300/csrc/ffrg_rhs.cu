@@ -81,22 +81,67 @@ __device__ __noinline__ float pole_ft(const RhsArgs *a, int e, int n, int r, int
   return pole_prop(a, a->tab + (size_t)srow * a->n_pts, q * q + p * p + 2.0 * q * p * c, om * om);
 }
 
+// Scale-dependent constants of one RHS in the kernel precision (computed once
+// per kernel, or per flow in the batched kernels).  us/uo: table coordinate
+// (divided by n-1 in FP32); plim = -2 m^2 (near-pole test); yk = log2(e)/k^2
+// and kh = k^2 ln 2 (FP32 regulator form).
+template <typename T>
+struct KConst {
+  T k2, inv_k2, m2, us, uo, plim, yk, kh;
+};
+
+template <typename T>
+__device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
+  const double kd = scale_k(a), m2d = mass2(a, kd);
+  KConst<T> c;
+  c.k2 = (T)(kd * kd);
+  c.inv_k2 = (T)(1.0 / (kd * kd));
+  c.m2 = (T)m2d;
+  c.us = lerp_scale<T>(a.u_scale, a.n_pts);
+  c.uo = lerp_off<T>(a.u_off, a.n_pts);
+  c.plim = (T)(-2.0 * m2d);
+  c.yk = (T)(1.4426950408889634074 / (kd * kd));
+  c.kh = (T)(kd * kd * 0.6931471805599453094);
+  return c;
+}
+
+// FP32 regulator in propagator form.  With x = s^2/k^2 the kinetic part of the
+// inverse propagator is Z (omega^2 + s^2 + k^2 r(x)) = Z (omega^2 + k^2 h(x)),
+// h(x) = x + r(x); for the exponential shape r = x/(e^x - 1) this is
+// h(x) = x/(1 - e^{-x}), for the flat shape h = max(1, x).  Evaluated as
+// g(y) = h(x)/ln 2 at y = x log2(e) (so that the hardware exp2 takes y):
+//   x >= 1: g = y / (1 - 2^{-y})  (no cancellation, 1 - e^{-x} >= 0.63; for
+//           large x, 2^{-y} underflows to 0 and g = y exactly);
+//   x < 1:  the Bernoulli series h = 1 + x/2 + x^2/12 - x^4/720 + x^6/30240
+//           - x^8/1209600, rewritten in y (first omitted term x^10/47900160
+//           < 2.1e-8 relative).
+__device__ __forceinline__ float reg_g(int reg, float y) {
+  if (reg == FFRG_REG_LITIM) return fmaxf(y, 1.4426950408889634f);
+  const float y2 = y * y;
+  float t = fmaf(y2, -6.3553057516916001e-8f, 5.2910945025509696e-6f);
+  t = fmaf(y2, t, -4.6253423887351317e-4f);
+  t = fmaf(y2, t, 5.7762265046662109e-2f);
+  const float series = fmaf(y2, t, fmaf(y, 0.5f, 1.4426950408889634f));
+  const float direct = y * hw_rcp(1.0f - hw_ex2(-y));
+  return y < 1.4426950408889634f ? series : direct;
+}
+
 // Inverse propagator in the kernel precision.  The FP32 version switches to
-// FP64 when m^2 cancels more than half of Z (omega^2 + s^2 + k^2 r): close to
-// the convexity pole.  `pole` is only evaluated on that rare branch.
+// FP64 when m^2 cancels more than half of Z (omega^2 + s^2 + k^2 r), i.e.
+// P < -2 m^2: close to the convexity pole.  `pole` is only evaluated on that
+// rare branch.
 template <typename Pole>
-__device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double s2, double om2, double m2, double k2,
-                                           double inv_k2, Pole &&) {
-  return 1.0 / prop_den(a.reg, Z, om2, s2, m2, k2, inv_k2);
+__device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double s2, double om2,
+                                           const KConst<double> &kc, Pole &&) {
+  return 1.0 / prop_den(a.reg, Z, om2, s2, kc.m2, kc.k2, kc.inv_k2);
 }
 
 template <typename Pole>
-__device__ __forceinline__ float inv_prop(const RhsArgs &a, float Z, float s2, float om2, float m2, float k2,
-                                          float inv_k2, Pole &&pole) {
-  const float P = Z * (om2 + s2 + k2 * reg_r(a.reg, s2 * inv_k2));
-  const float D = P + m2;
-  if (D < 0.5f * P) return pole();
-  return hw_rcp(D);
+__device__ __forceinline__ float inv_prop(const RhsArgs &a, float Z, float s2, float om2, const KConst<float> &kc,
+                                          Pole &&pole) {
+  const float P = Z * fmaf(kc.kh, reg_g(a.reg, s2 * kc.yk), om2);
+  if (P < kc.plim) return pole();
+  return hw_rcp(P + kc.m2);
 }
 
 // resident CTAs per SM requested from the compiler: the FP32 kernels are held
@@ -151,7 +196,11 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int 
     }
     a.radF[idx] = F;
   }
-  for (int i = tid0; i < a.tab_count; i += stride) a.tab32[i] = (float)a.tab[i];
+  for (int i = tid0; i < a.tab_count; i += stride) {
+    const float v = (float)a.tab[i];
+    const float d = (i % a.n_pts == a.n_pts - 1) ? 0.0f : (float)a.tab[i + 1] - v;
+    a.tab32[i] = make_float2(v, d);
+  }
   // per-external-point constants used by every work item of the main kernels
   for (int i = tid0; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
   if (a.model == FFRG_MODEL_D4_VERTEX) {
@@ -168,34 +217,54 @@ __global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// shared-memory layout of the main kernels: tables (+ one zero element read
-// with weight 0 by lookups at the last node), then angle rules
+// shared-memory layout of the main kernels: tables (FP64 values, or FP32 node
+// pairs), then the second-angle (node, weight) pairs and the first-angle
+// nodes, sines and weights
 // ---------------------------------------------------------------------------
 template <typename T>
+struct TabOf {
+  using type = double;
+};
+template <>
+struct TabOf<float> {
+  using type = float2;
+};
+template <typename T>
+struct Pair2 {
+  using type = double2;
+};
+template <>
+struct Pair2<float> {
+  using type = float2;
+};
+
+template <typename T>
 struct SmemLayout {
-  T *tab, *c1, *s1, *w1, *c2, *w2;
+  using Tab = typename TabOf<T>::type;
+  using P2 = typename Pair2<T>::type;
+  Tab *tab;
+  P2 *cw2;
+  T *c1, *s1, *w1;
   __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
-    tab = (T *)base;
-    size_t off = ((size_t)(a.tab_count + 1) * sizeof(T) + 15) & ~(size_t)15;
-    c1 = (T *)(base + off);
+    tab = (Tab *)base;
+    size_t off = ((size_t)a.tab_count * sizeof(Tab) + 15) & ~(size_t)15;
+    cw2 = (P2 *)(base + off);
+    c1 = (T *)(cw2 + a.na2);
     s1 = c1 + a.na1;
     w1 = s1 + a.na1;
-    c2 = w1 + a.na1;
-    w2 = c2 + a.na2;
   }
 };
 
 template <typename T>
-__device__ __forceinline__ const T *table_src(const RhsArgs &a);
+__device__ __forceinline__ const typename TabOf<T>::type *table_src(const RhsArgs &a);
 template <>
 __device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { return a.tab; }
 template <>
-__device__ __forceinline__ const float *table_src<float>(const RhsArgs &a) { return a.tab32; }
+__device__ __forceinline__ const float2 *table_src<float>(const RhsArgs &a) { return a.tab32; }
 
+// angle rules into shared memory in the kernel precision
 template <typename T>
-__device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
-  bool ok = stage_to_smem<T>(S.tab, table_src<T>(a), a.tab_count, bar, a.status);
-  if (threadIdx.x == 0) S.tab[a.tab_count] = (T)0;
+__device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S) {
   for (int i = threadIdx.x; i < a.na1; i += blockDim.x) {
     double c = a.a1_x[i];
     S.c1[i] = (T)c;
@@ -203,30 +272,17 @@ __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar)
     S.w1[i] = (T)a.a1_w[i];
   }
   for (int i = threadIdx.x; i < a.na2; i += blockDim.x) {
-    S.c2[i] = (T)a.a2_x[i];
-    S.w2[i] = (T)a.a2_w[i];
+    S.cw2[i].x = (T)a.a2_x[i];
+    S.cw2[i].y = (T)a.a2_w[i];
   }
-  __syncthreads();
-  return ok;
 }
 
-// Scale-dependent constants of one RHS in the kernel precision (computed once
-// per kernel, or per flow in the batched kernels).
 template <typename T>
-struct KConst {
-  T k2, inv_k2, m2, us, uo;
-};
-
-template <typename T>
-__device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
-  const double kd = scale_k(a), m2d = mass2(a, kd);
-  KConst<T> c;
-  c.k2 = (T)(kd * kd);
-  c.inv_k2 = (T)(1.0 / (kd * kd));
-  c.m2 = (T)m2d;
-  c.us = lerp_scale<T>(a.u_scale);
-  c.uo = (T)a.u_off;
-  return c;
+__device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
+  bool ok = stage_to_smem<typename TabOf<T>::type>(S.tab, table_src<T>(a), a.tab_count, bar, a.status);
+  stage_angles<T>(a, S);
+  __syncthreads();
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -237,7 +293,7 @@ __device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
 template <typename T>
 __device__ __forceinline__ double d3_item(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
                                           const KConst<T> &kc, int item, double *red) {
-  const T k2 = kc.k2, inv_k2 = kc.inv_k2, m2 = kc.m2, us = kc.us, uo = kc.uo;
+  const T us = kc.us, uo = kc.uo;
   const int np = a.n_pts, nblk = (a.na1 + a.jb - 1) / a.jb;
   const int e = item / a.n_chunks, c = item - e * a.n_chunks;
   const double pd = (e < a.n_ext_p) ? a.ext_pd[e] : 0.0;
@@ -254,7 +310,7 @@ __device__ __forceinline__ double d3_item(const RhsArgs &a, const RhsArgs *sa, c
       const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
       T Z = lerp(S.tab, s2, us, uo, np);
       auto pole = [&]() { return pole_d3(sa, e, o, j); };
-      rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, m2, k2, inv_k2, pole);
+      rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, kc, pole);
     }
     acc = fma(a.radF[o], (double)rs, acc);
   }
@@ -291,15 +347,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
   if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
-  const double kd = scale_k(a), m2d = mass2(a, kd);
-  const T k2 = (T)(kd * kd), inv_k2 = (T)(1.0 / (kd * kd)), m2 = (T)m2d;
-  const T us = lerp_scale<T>(a.u_scale), uo = (T)a.u_off;
+  const KConst<T> kc = make_kconst<T>(a);
+  const T us = kc.us, uo = kc.uo;
   // S0^2 = (sum of squares)/c: the 1/c is a shift of the coordinate, -u_scale ln c
-  const T uo2 = (T)(a.u_off - a.u_scale * 0.69314718055994530942);
-  const T uo3 = (T)(a.u_off - a.u_scale * 1.09861228866810969140);
-  const T uo4 = (T)(a.u_off - a.u_scale * 1.38629436111989061883);
+  const T uo2 = lerp_off<T>(a.u_off - a.u_scale * 0.69314718055994530942, a.n_pts);
+  const T uo3 = lerp_off<T>(a.u_off - a.u_scale * 1.09861228866810969140, a.n_pts);
+  const T uo4 = lerp_off<T>(a.u_off - a.u_scale * 1.38629436111989061883, a.n_pts);
   const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang;
-  const T *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
+  const auto *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
   const T sum_w2 = (T)a.sum_w2;
   for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
     const int e = item / a.n_chunks, c = item - e * a.n_chunks;
@@ -330,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
       const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
       const T ZA = lerp(Zt, A2, us, uo, np);
       auto pole_a = [&]() { return pole_d4(&sa, e, r, ia, -1); };
-      const T GA = inv_prop(a, ZA, A2, (T)0, m2, k2, inv_k2, pole_a);
+      const T GA = inv_prop(a, ZA, A2, (T)0, kc, pole_a);
       T v;
       if (block == 0) {
         const T l4 = lerp(L4, q2 + p2, us, uo2, np);
@@ -345,13 +400,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
         const T sab = A2 + C2;
         T rs = 0;
         for (int b = 0; b < a.na2; ++b) {
-          const T B2 = base - t1 - t2 * S.c2[b];
+          const auto cw = S.cw2[b];
+          const T B2 = base - t1 - t2 * cw.x;
           const T ZB = lerp(Zt, B2, us, uo, np);
           auto pole_b = [&]() { return pole_d4(&sa, e, r, ia, b); };
-          const T GB = inv_prop(a, ZB, B2, (T)0, m2, k2, inv_k2, pole_b);
+          const T GB = inv_prop(a, ZB, B2, (T)0, kc, pole_b);
           const T lb = lerp(L3, base + B2, us, uo3, np);
           const T lc = lerp(L3, sab + B2, us, uo3, np);
-          rs += S.w2[b] * GB * lb * lc;
+          rs += cw.y * GB * lb * lc;
         }
         v = GA * la * rs;
       }
@@ -369,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
 template <typename T>
 __device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
                                           const KConst<T> &kc, int item, double *red) {
-  const T k2 = kc.k2, inv_k2 = kc.inv_k2, m2 = kc.m2, us = kc.us, uo = kc.uo;
+  const T us = kc.us, uo = kc.uo;
   const int np = a.n_pts, nm = a.n_ext_ang, nblk = (a.na1 + a.jb - 1) / a.jb;
   const int outer_total = (2 * a.N + 1) * a.nr;
   const int e = item / a.n_chunks, c = item - e * a.n_chunks;
@@ -383,7 +439,7 @@ __device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, c
     const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
     const int n = o / a.nr - a.N, r = o % a.nr;
     const int srow = min(abs(n + m), a.n_stack - 1);
-    const T *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
+    const auto *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
     const double omd = 2.0 * kPi * a.T * (double)(n + m);
     const T om2 = (T)(omd * omd);
     const double qd = a.radq[r];
@@ -396,7 +452,7 @@ __device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, c
       lerp_pos(s2, us, uo, np, i0, w);
       const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
       auto pole = [&]() { return pole_ft(sa, e, n, r, j); };
-      rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, m2, k2, inv_k2, pole);
+      rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, kc, pole);
     }
     acc = fma(a.radF[o], (double)rs, acc);
   }
@@ -555,17 +611,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       if (!skip) {
         S = SmemLayout<float>(smem, sa);
         for (int i = threadIdx.x; i < sa.tab_count; i += blockDim.x) S.tab[i] = sa.tab32[i];
-        if (threadIdx.x == 0) S.tab[sa.tab_count] = 0.f;
-        for (int i = threadIdx.x; i < sa.na1; i += blockDim.x) {
-          const double c = sa.a1_x[i];
-          S.c1[i] = (float)c;
-          S.s1[i] = (float)sqrt(fmax(0.0, 1.0 - c * c));
-          S.w1[i] = (float)sa.a1_w[i];
-        }
-        for (int i = threadIdx.x; i < sa.na2; i += blockDim.x) {
-          S.c2[i] = (float)sa.a2_x[i];
-          S.w2[i] = (float)sa.a2_w[i];
-        }
+        stage_angles<float>(sa, S);
         kc = make_kconst<float>(sa);
       }
       __syncthreads();

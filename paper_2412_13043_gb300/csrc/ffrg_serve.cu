@@ -93,7 +93,7 @@ static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotL
   const size_t d = sizeof(double);
   size_t u = 0;
   L.o_tab = seg(u, (size_t)pl.tab_count * d);
-  L.o_tab32 = seg(u, ((size_t)pl.tab_count + 4) * sizeof(float));
+  L.o_tab32 = seg(u, (size_t)pl.tab_count * sizeof(float2));
   L.o_y = seg(u, (size_t)L.ny * d);
   L.o_ys = seg(u, (size_t)L.ny * d);
   L.o_K = seg(u, (size_t)7 * L.ny * d);
@@ -185,7 +185,7 @@ static int slot_setup(Server &S, int si) {
   pl.ext_pd = (double *)(b + L.o_extp);
   pl.psi_s = (double *)(b + L.o_psis);
   pl.partial = (double *)(b + L.o_part);
-  pl.tab32 = (float *)(b + L.o_tab32);
+  pl.tab32 = (float2 *)(b + L.o_tab32);
   struct Up { void *dst; const void *src; size_t n; } ups[] = {
       {b + L.o_tab, r->tab.data(), r->tab.size() * d}, {b + L.o_y, r->y0.data(), r->y0.size() * d},
       {pl.rad_x, rx.data(), rx.size() * d},           {pl.rad_w, rw.data(), rw.size() * d},
@@ -241,7 +241,7 @@ static int slot_setup(Server &S, int si) {
 
 static size_t smem32_of(const Plan &pl) {
   auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  return al16(((size_t)pl.tab_count + 1) * 4) + al16((size_t)pl.na1 * 3 * 4 + 2 * 4);
+  return al16((size_t)pl.tab_count * 8) + al16((size_t)pl.na1 * 3 * 4 + 2 * 4);
 }
 
 // Upload the descriptors of the given slots as one compact launch set.
