@@ -358,6 +358,9 @@ int launch_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc
   memset(&A, 0, sizeof(A));
   fill_args(pl, pb, td, tab, k, A.a);
   A.a.status = ctx->status_dev;
+  A.a.cr = pl->cr;  // block-sized work items
+  A.a.n_chunks = pl->n_chunks;
+  A.a.n_items = pl->n_items;
   A.a.radD = pl->radD;
   A.jrows = pl->jrows;
   st = launch_precompute(ctx, A.a, s);
@@ -397,6 +400,9 @@ extern "C" int ffrg_rhs_adjoint(ffrg_ctx *ctx, const ffrg_problem *pb, const ffr
   memset(&A, 0, sizeof(A));
   fill_args(pl, pb, &tables->desc, tables->dev, k, A.a);
   A.a.status = ctx->status_dev;
+  A.a.cr = pl->cr;  // block-sized work items
+  A.a.n_chunks = pl->n_chunks;
+  A.a.n_items = pl->n_items;
   A.a.radD = pl->radD;
   A.gbar = gbar_dev;
   A.gpart = pl->gpart;

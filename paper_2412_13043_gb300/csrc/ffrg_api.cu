@@ -176,22 +176,18 @@ static void plan_free(ffrg_ctx *ctx, Plan *pl) {
                     pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s, pl->jrows};
   for (double *p : arrs) dev_free(ctx, p, 0);
   dev_free(ctx, pl->tab32, 0);
+  dev_free(ctx, pl->radq32, 0);
+  dev_free(ctx, pl->work_ctr, 0);
   delete pl;
 }
 
 // Launch geometry: rows of angle work are grouped into work items (external
-// point x chunk of outer rows) so that each item keeps a 256-thread CTA busy
-// and there are many items per SM for load balance.
-int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {
-  std::vector<long long> key = {pb->model, pb->n_rad, pb->n_ang1, pb->n_ang2, pb->n_ext_p, pb->n_ext_ang,
-                                pb->n_matsubara, pb->include_p0, td->n_tables, td->n_stack, td->n_pts};
-  auto it = ctx->plans.find(key);
-  if (it != ctx->plans.end()) {
-    *out = it->second;
-    return FFRG_OK;
-  }
-  Plan *pl = new Plan();  // value-initialised: pointers null, counts zero
-  pl->key = key;
+// point x chunk of outer rows).  The block-sized items (about two rows per
+// thread of a 256-thread CTA) serve the adjoint kernels and the d=3 and
+// finite-T forward kernels.  The d=4 forward kernel gives each item to one
+// warp (about eight rows per lane): its partial sum needs only shuffles, no
+// block barrier, and a quarter of the FP64 reduction work.
+void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) {
   pl->model = pb->model;
   pl->nr = pb->n_rad;
   pl->na1 = pb->n_ang1;
@@ -205,8 +201,6 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   pl->n_stack = td->n_stack;
   pl->n_pts = td->n_pts;
   pl->tab_count = td->n_tables * td->n_stack * td->n_pts;
-
-  // rows per outer index and outer indices per item
   int outer_total, rows_per_outer;
   if (pb->model == FFRG_MODEL_D4_VERTEX) {
     pl->jb = pl->na2;
@@ -217,11 +211,28 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
     outer_total = pl->nr * (2 * pl->N + 1);
     rows_per_outer = (pl->na1 + pl->jb - 1) / pl->jb;
   }
-  int target_rows = 2 * kThreads;
-  pl->cr = std::max(1, (target_rows + rows_per_outer - 1) / rows_per_outer);
-  pl->cr = std::min(pl->cr, outer_total);
+  auto chunk = [&](int target_rows) {
+    return std::min(std::max(1, (target_rows + rows_per_outer - 1) / rows_per_outer), outer_total);
+  };
+  pl->cr = chunk(2 * kThreads);
   pl->n_chunks = (outer_total + pl->cr - 1) / pl->cr;
   pl->n_items = pl->n_ext * pl->n_chunks;
+  pl->fcr = pb->model == FFRG_MODEL_D4_VERTEX ? chunk(8 * 32) : pl->cr;
+  pl->fn_chunks = (outer_total + pl->fcr - 1) / pl->fcr;
+  pl->fn_items = pl->n_ext * pl->fn_chunks;
+}
+
+int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {
+  std::vector<long long> key = {pb->model, pb->n_rad, pb->n_ang1, pb->n_ang2, pb->n_ext_p, pb->n_ext_ang,
+                                pb->n_matsubara, pb->include_p0, td->n_tables, td->n_stack, td->n_pts};
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) {
+    *out = it->second;
+    return FFRG_OK;
+  }
+  Plan *pl = new Plan();  // value-initialised: pointers null, counts zero
+  pl->key = key;
+  plan_geometry(pl, pb, td);
 
   int st = FFRG_OK;
   std::vector<double> x(pl->nr), w(pl->nr);
@@ -248,9 +259,11 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   size_t nF = (size_t)pl->nr * (2 * pl->N + 1);
   if (!st) st = dev_alloc(ctx, (void **)&pl->radF, nF * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq, pl->nr * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->radq32, pl->nr * sizeof(float));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->work_ctr, sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
-  if (!st) st = dev_alloc(ctx, (void **)&pl->partial, (size_t)pl->n_items * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->partial, (size_t)pl->fn_items * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->tab32, (size_t)pl->tab_count * sizeof(float2));
   if (st) {
     plan_free(ctx, pl);
@@ -284,9 +297,9 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.n_stack = td->n_stack;
   a.n_pts = td->n_pts;
   a.tab_count = pl->tab_count;
-  a.cr = pl->cr;
-  a.n_chunks = pl->n_chunks;
-  a.n_items = pl->n_items;
+  a.cr = pl->fcr;
+  a.n_chunks = pl->fn_chunks;
+  a.n_items = pl->fn_items;
   a.jb = pl->jb;
   a.k = k;
   a.m2_over_k2 = pb->m2_over_k2;
@@ -317,6 +330,8 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.psi_x = pl->psi_x;
   a.radF = pl->radF;
   a.radq = pl->radq;
+  a.radq32 = pl->radq32;
+  a.work_ctr = pl->work_ctr;
   a.ext_pd = pl->ext_pd;
   a.psi_s = pl->psi_s;
   a.partial = pl->partial;
@@ -370,6 +385,8 @@ int ffrg_destroy(ffrg_ctx *ctx) {
                       pl->radF, pl->radq, pl->partial, pl->radD, pl->gpart, pl->ext_pd, pl->psi_s, pl->jrows};
     for (double *p : arrs) cudaFree(p);
     cudaFree(pl->tab32);
+    cudaFree(pl->radq32);
+    cudaFree(pl->work_ctr);
     delete pl;
   }
   ctx->plans.clear();

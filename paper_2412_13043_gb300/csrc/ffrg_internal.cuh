@@ -58,6 +58,8 @@ struct RhsArgs {
   double *radD;                // optional: d radF / d Z(q) (adjoint)
   double *radF;                // per-(n, r) factor
   double *radq;                // per-r momentum q
+  float *radq32;               // per-r momentum q in FP32 (optional, D4)
+  unsigned *work_ctr;          // optional: dynamic work-item counter, reset by the precompute kernel
   double *ext_pd;              // per external |p| index: p_i (written by the precompute kernel)
   double *psi_s;               // per external angle: sin(psi) (D4)
   double *partial;             // [n_ext][n_chunks]
@@ -320,12 +322,15 @@ struct Plan {
   int model;
   int nr, na1, na2, n_ext_ang, n_ext_p, N, include_p0, n_ext;
   int n_tables, n_stack, n_pts, tab_count;
-  int cr, n_chunks, n_items, jb;
+  int cr, n_chunks, n_items, jb;  // block-sized work items (adjoint kernels)
+  int fcr, fn_chunks, fn_items;   // work items of the forward RHS kernels (warp-sized for D4)
   int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
   size_t smem64, smem32;    // dynamic shared memory bytes
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;
   double sum_w2;
   double *radF, *radq, *partial, *ext_pd, *psi_s;
+  float *radq32;
+  unsigned *work_ctr;
   float2 *tab32;
   double *radD, *gpart;     // adjoint scratch (allocated on first use)
   double *jrows;            // Jacobian rows per work item (allocated on first use)
@@ -333,6 +338,10 @@ struct Plan {
   size_t adj_smem;
   std::vector<double> psi_w_host;
 };
+
+// Shape and launch geometry of a plan (no allocation): sizes from the problem
+// and the table descriptor, and the grouping of angular rows into work items.
+void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td);
 
 // Raise a kernel's dynamic shared-memory limit to at least `bytes` (never
 // lowers it: plans of different sizes share the kernel).

@@ -73,32 +73,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   // Launch geometry: the same grouping of angular rows into work items as the
   // cached plans of ffrg_rhs use.
   Plan pl = Plan();
-  pl.model = pb->model;
-  pl.nr = pb->n_rad;
-  pl.na1 = pb->n_ang1;
-  pl.na2 = pb->model == FFRG_MODEL_D4_VERTEX ? pb->n_ang2 : 1;
-  pl.n_ext_ang = pb->n_ext_ang;
-  pl.n_ext_p = pb->n_ext_p;
-  pl.N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
-  pl.include_p0 = pb->include_p0;
-  pl.n_ext = ffrg_n_ext(pb);
-  pl.n_tables = td->n_tables;
-  pl.n_stack = td->n_stack;
-  pl.n_pts = td->n_pts;
-  pl.tab_count = td->n_tables * td->n_stack * td->n_pts;
-  int outer_total, rows_per_outer;
-  if (pb->model == FFRG_MODEL_D4_VERTEX) {
-    pl.jb = pl.na2;
-    outer_total = pl.nr;
-    rows_per_outer = pl.na1;
-  } else {
-    pl.jb = std::min(pl.na1, 8);
-    outer_total = pl.nr * (2 * pl.N + 1);
-    rows_per_outer = (pl.na1 + pl.jb - 1) / pl.jb;
-  }
-  pl.cr = std::min(std::max(1, (2 * kThreads + rows_per_outer - 1) / rows_per_outer), outer_total);
-  pl.n_chunks = (outer_total + pl.cr - 1) / pl.cr;
-  pl.n_items = pl.n_ext * pl.n_chunks;
+  plan_geometry(&pl, pb, td);
 
   // quadrature rules on the host
   std::vector<double> rx(pl.nr), rw(pl.nr), x1(pl.na1), w1(pl.na1), x2(pl.na2), w2(pl.na2);
@@ -125,9 +100,11 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.psi_w = sc.take<double>(npsi);
   pl.radF = sc.take<double>((size_t)pl.nr * (2 * pl.N + 1));
   pl.radq = sc.take<double>(pl.nr);
+  pl.radq32 = sc.take<float>(pl.nr);
+  pl.work_ctr = sc.take<unsigned>(4);
   pl.ext_pd = sc.take<double>(pl.n_ext_p);
   pl.psi_s = sc.take<double>(npsi);
-  pl.partial = sc.take<double>(pl.n_items);
+  pl.partial = sc.take<double>(pl.fn_items);
   pl.tab32 = sc.take<float2>((size_t)pl.tab_count);
   if (sc.used > kNoallocScratchBytes) return FFRG_EINVAL;  // problem needs more than the 4 MiB scratch
 

@@ -161,13 +161,17 @@ struct MinBlocks<float> {
 __device__ __forceinline__ bool skipped(const RhsArgs &a) { return a.skip && *(volatile const int *)a.skip; }
 
 __device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int stride) {
+  if (a.work_ctr && tid0 == 0) *a.work_ctr = 0u;  // the main kernel runs after this one (stream order)
   const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
   const double L = a.qmax_over_k * k;
   const int total = (2 * a.N + 1) * a.nr;
   for (int idx = tid0; idx < total; idx += stride) {
     int n = idx / a.nr - a.N, r = idx % a.nr;
     double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q;
-    if (n == -a.N) a.radq[r] = q;
+    if (n == -a.N) {
+      a.radq[r] = q;
+      if (a.radq32) a.radq32[r] = (float)q;
+    }
     double F;
     if (a.model == FFRG_MODEL_FINITE_T) {
       int row = min(abs(n), a.n_stack - 1);
@@ -335,14 +339,24 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d3_main(RhsArgs
 }
 
 // ---------------------------------------------------------------------------
-// 2b. d=4 vertex expansion: row (r, c1 node), inner loop over c2 nodes
+// 2b. d=4 vertex expansion: row (r, c1 node), inner loop over c2 nodes.
+// Work items are warp-sized (about eight rows per lane) and are handed out by
+// a device counter, the three-point items (the 16x more expensive ones) first.
+// Each item is summed by one warp in a fixed order (rows by lane, then a
+// shuffle tree), so the result does not depend on which warp took it.
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T radial_q(const RhsArgs &a, int r);
+template <>
+__device__ __forceinline__ double radial_q<double>(const RhsArgs &a, int r) { return a.radq[r]; }
+template <>
+__device__ __forceinline__ float radial_q<float>(const RhsArgs &a, int r) { return a.radq32[r]; }
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs a) {
   if (skipped(a)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
-  __shared__ double red[kThreads / 32];
   __shared__ RhsArgs sa;  // for the out-of-line near-pole path
   if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
@@ -353,11 +367,20 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
   const T uo2 = lerp_off<T>(a.u_off - a.u_scale * 0.69314718055994530942, a.n_pts);
   const T uo3 = lerp_off<T>(a.u_off - a.u_scale * 1.09861228866810969140, a.n_pts);
   const T uo4 = lerp_off<T>(a.u_off - a.u_scale * 1.38629436111989061883, a.n_pts);
-  const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang;
+  const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang, na1 = a.na1;
   const auto *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
   const T sum_w2 = (T)a.sum_w2;
-  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    const int e = item / a.n_chunks, c = item - e * a.n_chunks;
+  const int lane = threadIdx.x & 31;
+  const int dr = 32 / na1, dia = 32 % na1;  // row step of one lane in (r, ia)
+  for (;;) {
+    int d = 0;
+    if (lane == 0) d = (int)atomicAdd(a.work_ctr, 1u);
+    d = __shfl_sync(0xffffffffu, d, 0);
+    if (d >= a.n_items) break;
+    // rank d -> external point: rotate so that the three-point block comes first
+    const int c = d % a.n_chunks;
+    const int e = (d / a.n_chunks + np_ + 1) % a.n_ext;
+    const int item = e * a.n_chunks + c;
     int block, ip, jp = 0;
     if (e <= np_) {
       block = 0;
@@ -376,12 +399,11 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
     const T p = (T)pd, p2 = p * p, cpsi = (T)cpsid, spsi = (T)spsid;
     const T C2 = (T)2 * p2 * ((T)1 + cpsi);
     const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
-    const int rows = (o1 - o0) * a.na1;
+    const int rows = (o1 - o0) * na1;
     double acc = 0.0;
-    for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-      const int r = o0 + row / a.na1, ia = row % a.na1;
-      const double qd = a.radq[r];
-      const T q = (T)qd, q2 = q * q, qp = q * p, c1 = S.c1[ia];
+    int r = o0 + lane / na1, ia = lane % na1;
+    for (int row = lane; row < rows; row += 32) {
+      const T q = radial_q<T>(a, r), q2 = q * q, qp = q * p, c1 = S.c1[ia];
       const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
       const T ZA = lerp(Zt, A2, us, uo, np);
       auto pole_a = [&]() { return pole_d4(&sa, e, r, ia, -1); };
@@ -412,9 +434,16 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
         v = GA * la * rs;
       }
       acc = fma(a.radF[r], (double)(S.w1[ia] * v), acc);
+      r += dr;
+      ia += dia;
+      if (ia >= na1) {
+        ia -= na1;
+        ++r;
+      }
     }
-    double t = block_sum(acc, red);
-    if (threadIdx.x == 0) a.partial[item] = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) a.partial[item] = acc;
   }
 }
 
@@ -541,6 +570,10 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision,
   case FFRG_MODEL_D3: kern = mixed ? d3_main<float> : d3_main<double>; break;
   case FFRG_MODEL_D4_VERTEX: kern = mixed ? d4_main<float> : d4_main<double>; break;
   default: kern = mixed ? ft_main<float> : ft_main<double>; break;
+  }
+  if (a.model == FFRG_MODEL_D4_VERTEX && (!a.work_ctr || !a.radq32)) {
+    ctx->last_error = "d=4 plan without work counter or FP32 radial nodes";
+    return FFRG_EINVAL;
   }
   if (grid == 0) {
     st = persistent_grid(ctx, kern, smem, a.n_items, &grid);

@@ -68,25 +68,7 @@ static size_t seg(size_t &used, size_t bytes) {
 static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotLayout &L) {
   Plan &pl = L.pl;
   pl = Plan();
-  pl.model = pb->model;
-  pl.nr = pb->n_rad;
-  pl.na1 = pb->n_ang1;
-  pl.na2 = 1;
-  pl.n_ext_ang = pb->n_ext_ang;
-  pl.n_ext_p = pb->n_ext_p;
-  pl.N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
-  pl.include_p0 = pb->include_p0;
-  pl.n_ext = ffrg_n_ext(pb);
-  pl.n_tables = td->n_tables;
-  pl.n_stack = td->n_stack;
-  pl.n_pts = td->n_pts;
-  pl.tab_count = td->n_tables * td->n_stack * td->n_pts;
-  pl.jb = std::min(pl.na1, 8);
-  const int outer_total = pl.nr * (2 * pl.N + 1);
-  const int rows_per_outer = (pl.na1 + pl.jb - 1) / pl.jb;
-  pl.cr = std::min(std::max(1, (2 * kThreads + rows_per_outer - 1) / rows_per_outer), outer_total);
-  pl.n_chunks = (outer_total + pl.cr - 1) / pl.cr;
-  pl.n_items = pl.n_ext * pl.n_chunks;
+  plan_geometry(&pl, pb, td);
   pl.sum_w2 = 2.0;
   L.ny = pl.n_ext;
   L.npsi = std::max(1, pl.n_ext_ang);
