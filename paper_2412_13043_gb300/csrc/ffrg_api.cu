@@ -178,6 +178,7 @@ static void plan_free(ffrg_ctx *ctx, Plan *pl) {
   dev_free(ctx, pl->tab32, 0);
   dev_free(ctx, pl->radq32, 0);
   dev_free(ctx, pl->work_ctr, 0);
+  dev_free(ctx, pl->ext_done, 0);
   delete pl;
 }
 
@@ -261,6 +262,7 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq, pl->nr * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq32, pl->nr * sizeof(float));
   if (!st) st = dev_alloc(ctx, (void **)&pl->work_ctr, sizeof(unsigned));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->ext_done, (size_t)pl->n_ext * sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->partial, (size_t)pl->fn_items * sizeof(double));
@@ -332,6 +334,7 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.radq = pl->radq;
   a.radq32 = pl->radq32;
   a.work_ctr = pl->work_ctr;
+  a.ext_done = pl->ext_done;
   a.ext_pd = pl->ext_pd;
   a.psi_s = pl->psi_s;
   a.partial = pl->partial;
@@ -387,6 +390,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
     cudaFree(pl->tab32);
     cudaFree(pl->radq32);
     cudaFree(pl->work_ctr);
+    cudaFree(pl->ext_done);
     delete pl;
   }
   ctx->plans.clear();

@@ -60,6 +60,7 @@ struct RhsArgs {
   double *radq;                // per-r momentum q
   float *radq32;               // per-r momentum q in FP32 (optional, D4)
   unsigned *work_ctr;          // optional: dynamic work-item counter, reset by the precompute kernel
+  unsigned *ext_done;          // optional: finished items per external point (D4), reset likewise
   double *ext_pd;              // per external |p| index: p_i (written by the precompute kernel)
   double *psi_s;               // per external angle: sin(psi) (D4)
   double *partial;             // [n_ext][n_chunks]
@@ -330,7 +331,7 @@ struct Plan {
   double sum_w2;
   double *radF, *radq, *partial, *ext_pd, *psi_s;
   float *radq32;
-  unsigned *work_ctr;
+  unsigned *work_ctr, *ext_done;
   float2 *tab32;
   double *radD, *gpart;     // adjoint scratch (allocated on first use)
   double *jrows;            // Jacobian rows per work item (allocated on first use)

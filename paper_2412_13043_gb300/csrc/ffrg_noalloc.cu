@@ -102,6 +102,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.radq = sc.take<double>(pl.nr);
   pl.radq32 = sc.take<float>(pl.nr);
   pl.work_ctr = sc.take<unsigned>(4);
+  pl.ext_done = sc.take<unsigned>(pl.n_ext);
   pl.ext_pd = sc.take<double>(pl.n_ext_p);
   pl.psi_s = sc.take<double>(npsi);
   pl.partial = sc.take<double>(pl.fn_items);

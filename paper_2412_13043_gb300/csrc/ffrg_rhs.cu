@@ -83,11 +83,15 @@ __device__ __noinline__ float pole_ft(const RhsArgs *a, int e, int n, int r, int
 
 // Scale-dependent constants of one RHS in the kernel precision (computed once
 // per kernel, or per flow in the batched kernels).  us/uo: table coordinate
-// (divided by n-1 in FP32); plim = -2 m^2 (near-pole test); yk = log2(e)/k^2
-// and kh = k^2 ln 2 (FP32 regulator form).
+// (divided by n-1 in FP32); plim = -2 m^2 (near-pole test).  The kernels pass
+// squared momenta to the propagator as y = sy s^2 and omega^2 as som omega^2:
+// FP64 sy = som = 1; FP32 sy = log2(e)/k^2 (the regulator's exp2 argument)
+// and som = 1/(k^2 ln 2), with the FP32 Z table pre-scaled by k^2 ln 2
+// (see reg_g).  lnsy = ln(sy) shifts table coordinates taken in y.
 template <typename T>
 struct KConst {
-  T k2, inv_k2, m2, us, uo, plim, yk, kh;
+  T k2, inv_k2, m2, us, uo, plim, sy, som;
+  double lnsy;
 };
 
 template <typename T>
@@ -100,13 +104,16 @@ __device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
   c.us = lerp_scale<T>(a.u_scale, a.n_pts);
   c.uo = lerp_off<T>(a.u_off, a.n_pts);
   c.plim = (T)(-2.0 * m2d);
-  c.yk = (T)(1.4426950408889634074 / (kd * kd));
-  c.kh = (T)(kd * kd * 0.6931471805599453094);
+  const bool f32 = sizeof(T) == 4;
+  c.sy = (T)(f32 ? 1.4426950408889634074 / (kd * kd) : 1.0);
+  c.som = (T)(f32 ? 1.0 / (kd * kd * 0.6931471805599453094) : 1.0);
+  c.lnsy = f32 ? log(1.4426950408889634074 / (kd * kd)) : 0.0;
   return c;
 }
 
 // FP32 regulator in propagator form.  With x = s^2/k^2 the kinetic part of the
 // inverse propagator is Z (omega^2 + s^2 + k^2 r(x)) = Z (omega^2 + k^2 h(x)),
+// = (k^2 ln 2 Z) (g(y) + omega^2/(k^2 ln 2)),
 // h(x) = x + r(x); for the exponential shape r = x/(e^x - 1) this is
 // h(x) = x/(1 - e^{-x}), for the flat shape h = max(1, x).  Evaluated as
 // g(y) = h(x)/ln 2 at y = x log2(e) (so that the hardware exp2 takes y):
@@ -126,21 +133,23 @@ __device__ __forceinline__ float reg_g(int reg, float y) {
   return y < 1.4426950408889634f ? series : direct;
 }
 
-// Inverse propagator in the kernel precision.  The FP32 version switches to
-// FP64 when m^2 cancels more than half of Z (omega^2 + s^2 + k^2 r), i.e.
-// P < -2 m^2: close to the convexity pole.  `pole` is only evaluated on that
-// rare branch.
-template <typename Pole>
-__device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double s2, double om2,
+// Inverse propagator in the kernel precision from the table value Zs, the
+// scaled momentum y = sy s^2 and om2s = som omega^2 (FP64: Z, s^2, omega^2).
+// The FP32 version switches to FP64 when m^2 cancels more than half of
+// Z (omega^2 + s^2 + k^2 r), i.e. P < -2 m^2: close to the convexity pole.
+// `pole` is only evaluated on that rare branch.  POLE = false drops the test;
+// callers use it only when m^2 >= 0 and no Z < 0, where P >= 0 >= -2 m^2.
+template <bool POLE = true, typename Pole>
+__device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double y, double om2s,
                                            const KConst<double> &kc, Pole &&) {
-  return 1.0 / prop_den(a.reg, Z, om2, s2, kc.m2, kc.k2, kc.inv_k2);
+  return 1.0 / prop_den(a.reg, Z, om2s, y, kc.m2, kc.k2, kc.inv_k2);
 }
 
-template <typename Pole>
-__device__ __forceinline__ float inv_prop(const RhsArgs &a, float Z, float s2, float om2, const KConst<float> &kc,
+template <bool POLE = true, typename Pole>
+__device__ __forceinline__ float inv_prop(const RhsArgs &a, float Zs, float y, float om2s, const KConst<float> &kc,
                                           Pole &&pole) {
-  const float P = Z * fmaf(kc.kh, reg_g(a.reg, s2 * kc.yk), om2);
-  if (P < kc.plim) return pole();
+  const float P = Zs * (reg_g(a.reg, y) + om2s);
+  if (POLE && P < kc.plim) return pole();
   return hw_rcp(P + kc.m2);
 }
 
@@ -200,11 +209,18 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int 
     }
     a.radF[idx] = F;
   }
+  // FP32 node pairs; the Z table (table 0, every stack row) carries the factor
+  // k^2 ln 2 of the FP32 propagator form
+  const double kh = k2 * 0.6931471805599453094;
+  const int z_count = a.n_stack * a.n_pts;
   for (int i = tid0; i < a.tab_count; i += stride) {
-    const float v = (float)a.tab[i];
-    const float d = (i % a.n_pts == a.n_pts - 1) ? 0.0f : (float)a.tab[i + 1] - v;
+    const double f = i < z_count ? kh : 1.0;
+    const float v = (float)(f * a.tab[i]);
+    const float d = (i % a.n_pts == a.n_pts - 1) ? 0.0f : (float)(f * a.tab[i + 1]) - v;
     a.tab32[i] = make_float2(v, d);
   }
+  if (a.ext_done)
+    for (int i = tid0; i < a.n_ext; i += stride) a.ext_done[i] = 0u;
   // per-external-point constants used by every work item of the main kernels
   for (int i = tid0; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
   if (a.model == FFRG_MODEL_D4_VERTEX) {
@@ -266,6 +282,9 @@ __device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { r
 template <>
 __device__ __forceinline__ const float2 *table_src<float>(const RhsArgs &a) { return a.tab32; }
 
+__device__ __forceinline__ double table_value(double v) { return v; }
+__device__ __forceinline__ float table_value(float2 v) { return v.x; }
+
 // angle rules into shared memory in the kernel precision
 template <typename T>
 __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S) {
@@ -314,7 +333,7 @@ __device__ __forceinline__ double d3_item(const RhsArgs &a, const RhsArgs *sa, c
       const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
       T Z = lerp(S.tab, s2, us, uo, np);
       auto pole = [&]() { return pole_d3(sa, e, o, j); };
-      rs += S.w1[j] * inv_prop(a, Z, s2, (T)0, kc, pole);
+      rs += S.w1[j] * inv_prop(a, Z, s2 * kc.sy, (T)0, kc, pole);
     }
     acc = fma(a.radF[o], (double)rs, acc);
   }
@@ -352,21 +371,32 @@ __device__ __forceinline__ double radial_q<double>(const RhsArgs &a, int r) { re
 template <>
 __device__ __forceinline__ float radial_q<float>(const RhsArgs &a, int r) { return a.radq32[r]; }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs a) {
-  if (skipped(a)) return;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar;
-  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
-  if (threadIdx.x == 0) sa = a;
-  SmemLayout<T> S(smem, a);
-  if (!main_prologue<T>(a, S, &bar)) return;
-  const KConst<T> kc = make_kconst<T>(a);
-  const T us = kc.us, uo = kc.uo;
+// Output of external point e from the sum s of its partials: diagram
+// coefficient (d=4: 1, 3, 3/2 for the Z, lambda3, lambda4 blocks), overall
+// normalisation, and the non-finite check into the status word.
+__device__ __forceinline__ void write_output(const RhsArgs &a, int e, double s) {
+  double coef = 1.0;
+  if (a.model == FFRG_MODEL_D4_VERTEX) {
+    const int np_ = a.n_ext_p;
+    if (e > np_ && e < np_ + 1 + np_ * a.n_ext_ang) coef = 3.0;
+    else if (e >= np_ + 1 + np_ * a.n_ext_ang) coef = 1.5;
+  }
+  const double v = a.norm * coef * s;
+  a.out[e] = v;
+  if (!isfinite(v)) raise_status(a.status, kStatusNonFinite);
+}
+
+// Work loop of the d=4 kernel.  All squared momenta are taken as y = sy s^2;
+// table coordinates in y use offsets shifted by -u_scale ln(sy).
+template <typename T, bool POLE>
+__device__ __forceinline__ void d4_items(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                         const KConst<T> &kc) {
+  const T us = kc.us, sy = kc.sy;
   // S0^2 = (sum of squares)/c: the 1/c is a shift of the coordinate, -u_scale ln c
-  const T uo2 = lerp_off<T>(a.u_off - a.u_scale * 0.69314718055994530942, a.n_pts);
-  const T uo3 = lerp_off<T>(a.u_off - a.u_scale * 1.09861228866810969140, a.n_pts);
-  const T uo4 = lerp_off<T>(a.u_off - a.u_scale * 1.38629436111989061883, a.n_pts);
+  const T uo1 = lerp_off<T>(a.u_off - a.u_scale * kc.lnsy, a.n_pts);
+  const T uo2 = lerp_off<T>(a.u_off - a.u_scale * (0.69314718055994530942 + kc.lnsy), a.n_pts);
+  const T uo3 = lerp_off<T>(a.u_off - a.u_scale * (1.09861228866810969140 + kc.lnsy), a.n_pts);
+  const T uo4 = lerp_off<T>(a.u_off - a.u_scale * (1.38629436111989061883 + kc.lnsy), a.n_pts);
   const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang, na1 = a.na1;
   const auto *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
   const T sum_w2 = (T)a.sum_w2;
@@ -405,30 +435,31 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
     for (int row = lane; row < rows; row += 32) {
       const T q = radial_q<T>(a, r), q2 = q * q, qp = q * p, c1 = S.c1[ia];
       const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
-      const T ZA = lerp(Zt, A2, us, uo, np);
-      auto pole_a = [&]() { return pole_d4(&sa, e, r, ia, -1); };
-      const T GA = inv_prop(a, ZA, A2, (T)0, kc, pole_a);
+      const T Ay = A2 * sy;
+      const T ZA = lerp(Zt, Ay, us, uo1, np);
+      auto pole_a = [&]() { return pole_d4(sa, e, r, ia, -1); };
+      const T GA = inv_prop<POLE>(a, ZA, Ay, (T)0, kc, pole_a);
       T v;
       if (block == 0) {
-        const T l4 = lerp(L4, q2 + p2, us, uo2, np);
-        const T l3 = lerp(L3, q2 + A2 + p2, us, uo3, np);
+        const T l4 = lerp(L4, (q2 + p2) * sy, us, uo2, np);
+        const T l3 = lerp(L3, (q2 + A2 + p2) * sy, us, uo3, np);
         v = sum_w2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
       } else if (block == 2) {
-        const T l4 = lerp(L4, q2 + A2 + (T)2 * p2, us, uo4, np);
+        const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * sy, us, uo4, np);
         v = sum_w2 * GA * l4 * l4;
       } else {
-        const T la = lerp(L3, q2 + A2 + p2, us, uo3, np);
+        const T la = lerp(L3, (q2 + A2 + p2) * sy, us, uo3, np);
         const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
-        const T sab = A2 + C2;
+        const T by = base * sy, b0 = (base - t1) * sy, t2y = t2 * sy, sy_ab = (A2 + C2) * sy;
         T rs = 0;
         for (int b = 0; b < a.na2; ++b) {
           const auto cw = S.cw2[b];
-          const T B2 = base - t1 - t2 * cw.x;
-          const T ZB = lerp(Zt, B2, us, uo, np);
-          auto pole_b = [&]() { return pole_d4(&sa, e, r, ia, b); };
-          const T GB = inv_prop(a, ZB, B2, (T)0, kc, pole_b);
-          const T lb = lerp(L3, base + B2, us, uo3, np);
-          const T lc = lerp(L3, sab + B2, us, uo3, np);
+          const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
+          const T ZB = lerp(Zt, By, us, uo1, np);
+          auto pole_b = [&]() { return pole_d4(sa, e, r, ia, b); };
+          const T GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
+          const T lb = lerp(L3, by + By, us, uo3, np);
+          const T lc = lerp(L3, sy_ab + By, us, uo3, np);
           rs += cw.y * GB * lb * lc;
         }
         v = GA * la * rs;
@@ -443,8 +474,42 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) a.partial[item] = acc;
+    // the warp that completes external point e sums its partials (fixed order)
+    unsigned done = 0;
+    if (lane == 0) {
+      a.partial[item] = acc;
+      __threadfence();
+      done = atomicAdd(a.ext_done + e, 1u);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    if (done == (unsigned)a.n_chunks - 1u) {
+      __threadfence();
+      const double *pp = a.partial + (size_t)e * a.n_chunks;
+      double t = 0.0;
+      for (int j = lane; j < a.n_chunks; j += 32) t += __ldcg(pp + j);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) write_output(a, e, t);
+    }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs a) {
+  if (skipped(a)) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
+  if (threadIdx.x == 0) sa = a;
+  SmemLayout<T> S(smem, a);
+  if (!main_prologue<T>(a, S, &bar)) return;
+  const KConst<T> kc = make_kconst<T>(a);
+  // the near-pole test can only fire with m^2 < 0 or a negative Z node
+  int neg = 0;
+  for (int i = threadIdx.x; i < a.n_pts; i += blockDim.x) neg |= table_value(S.tab[i]) < (T)0;
+  const bool may_pole = __syncthreads_or(neg) || kc.m2 < (T)0;
+  if (may_pole) d4_items<T, true>(a, &sa, S, kc);
+  else d4_items<T, false>(a, &sa, S, kc);
 }
 
 // ---------------------------------------------------------------------------
@@ -470,7 +535,7 @@ __device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, c
     const int srow = min(abs(n + m), a.n_stack - 1);
     const auto *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
     const double omd = 2.0 * kPi * a.T * (double)(n + m);
-    const T om2 = (T)(omd * omd);
+    const T om2s = (T)(omd * omd) * kc.som;
     const double qd = a.radq[r];
     const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
     T rs = 0;
@@ -481,7 +546,7 @@ __device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, c
       lerp_pos(s2, us, uo, np, i0, w);
       const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
       auto pole = [&]() { return pole_ft(sa, e, n, r, j); };
-      rs += S.w1[j] * Lv * inv_prop(a, Z, s2, om2, kc, pole);
+      rs += S.w1[j] * Lv * inv_prop(a, Z, s2 * kc.sy, om2s, kc, pole);
     }
     acc = fma(a.radF[o], (double)rs, acc);
   }
@@ -513,15 +578,7 @@ __device__ __forceinline__ void finalize_body(const RhsArgs &a, int e) {
   double s = 0.0;
   const double *pp = a.partial + (size_t)e * a.n_chunks;
   for (int c = 0; c < a.n_chunks; ++c) s += pp[c];
-  double coef = 1.0;
-  if (a.model == FFRG_MODEL_D4_VERTEX) {
-    const int np_ = a.n_ext_p;
-    if (e > np_ && e < np_ + 1 + np_ * a.n_ext_ang) coef = 3.0;
-    else if (e >= np_ + 1 + np_ * a.n_ext_ang) coef = 1.5;
-  }
-  const double v = a.norm * coef * s;
-  a.out[e] = v;
-  if (!isfinite(v)) raise_status(a.status, kStatusNonFinite);
+  write_output(a, e, s);
 }
 
 __global__ void finalize_kernel(RhsArgs a) {
@@ -571,7 +628,7 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision,
   case FFRG_MODEL_D4_VERTEX: kern = mixed ? d4_main<float> : d4_main<double>; break;
   default: kern = mixed ? ft_main<float> : ft_main<double>; break;
   }
-  if (a.model == FFRG_MODEL_D4_VERTEX && (!a.work_ctr || !a.radq32)) {
+  if (a.model == FFRG_MODEL_D4_VERTEX && (!a.work_ctr || !a.radq32 || !a.ext_done)) {
     ctx->last_error = "d=4 plan without work counter or FP32 radial nodes";
     return FFRG_EINVAL;
   }
@@ -592,7 +649,9 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision,
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;
   }
-  finalize_kernel<<<(a.n_ext + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+  // the d=4 kernel writes its outputs itself (last warp per external point)
+  if (a.model != FFRG_MODEL_D4_VERTEX)
+    finalize_kernel<<<(a.n_ext + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
   return set_cuda_error(ctx, cudaGetLastError(), "rhs launch");
 }
 
