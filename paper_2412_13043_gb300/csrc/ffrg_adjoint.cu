@@ -359,6 +359,7 @@ int launch_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc
   fill_args(pl, pb, td, tab, k, A.a);
   A.a.status = ctx->status_dev;
   A.a.cr = pl->cr;  // block-sized work items
+  A.a.jb = pl->jb;
   A.a.n_chunks = pl->n_chunks;
   A.a.n_items = pl->n_items;
   A.a.radD = pl->radD;
@@ -401,6 +402,7 @@ extern "C" int ffrg_rhs_adjoint(ffrg_ctx *ctx, const ffrg_problem *pb, const ffr
   fill_args(pl, pb, &tables->desc, tables->dev, k, A.a);
   A.a.status = ctx->status_dev;
   A.a.cr = pl->cr;  // block-sized work items
+  A.a.jb = pl->jb;
   A.a.n_chunks = pl->n_chunks;
   A.a.n_items = pl->n_items;
   A.a.radD = pl->radD;

@@ -179,15 +179,16 @@ static void plan_free(ffrg_ctx *ctx, Plan *pl) {
   dev_free(ctx, pl->radq32, 0);
   dev_free(ctx, pl->work_ctr, 0);
   dev_free(ctx, pl->ext_done, 0);
+  dev_free(ctx, pl->kconst, 0);
+  dev_free(ctx, pl->radF32, 0);
   delete pl;
 }
 
 // Launch geometry: rows of angle work are grouped into work items (external
-// point x chunk of outer rows).  The block-sized items (about two rows per
-// thread of a 256-thread CTA) serve the adjoint kernels and the d=3 and
-// finite-T forward kernels.  The d=4 forward kernel gives each item to one
-// warp (about eight rows per lane): its partial sum needs only shuffles, no
-// block barrier, and a quarter of the FP64 reduction work.
+// point x chunk of outer rows).  The block-sized items (about two rows of at
+// most 8 angle nodes per thread of a 256-thread CTA) serve the adjoint
+// kernels.  The forward kernels give each item to one warp: the partial sum
+// needs only shuffles, no block barrier, and little FP64 reduction work.
 void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) {
   pl->model = pb->model;
   pl->nr = pb->n_rad;
@@ -202,6 +203,9 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   pl->n_stack = td->n_stack;
   pl->n_pts = td->n_pts;
   pl->tab_count = td->n_tables * td->n_stack * td->n_pts;
+  // FP32 layout: (value, difference) node pairs; finite T: (Z, lambda) node
+  // pairs per stack row plus one zero pair (same bytes as single values)
+  pl->tab32_count = pb->model == FFRG_MODEL_FINITE_T ? td->n_stack * td->n_pts + 1 : pl->tab_count;
   int outer_total, rows_per_outer;
   if (pb->model == FFRG_MODEL_D4_VERTEX) {
     pl->jb = pl->na2;
@@ -218,9 +222,43 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   pl->cr = chunk(2 * kThreads);
   pl->n_chunks = (outer_total + pl->cr - 1) / pl->cr;
   pl->n_items = pl->n_ext * pl->n_chunks;
-  pl->fcr = pb->model == FFRG_MODEL_D4_VERTEX ? chunk(8 * 32) : pl->cr;
-  pl->fn_chunks = (outer_total + pl->fcr - 1) / pl->fcr;
-  pl->fn_items = pl->n_ext * pl->fn_chunks;
+  // Forward (warp-sized) items.  d=4: rows (radial, first angle), about
+  // eight per lane.  d=3 / finite T: rows = outer index x block of angle
+  // nodes; a warp item takes a multiple of 32 rows (1..8 per lane), sized for
+  // about eight items per resident warp of a 152-SM GPU.  The mixed kernels
+  // keep whole angle rules per row (splitting them was measured slower, also
+  // for the serving kernels, which use this geometry so that they compute
+  // exactly what the single-flow kernels do).  The FP64 kernels split the
+  // angle rule into blocks of at least 4 nodes until there is a row per
+  // resident lane: small FP64 problems are bound by each lane's FP64 chain.
+  auto forward = [&](bool fp64, int &fcr, int &fn_chunks, int &fn_items, int &fjb) {
+    if (pb->model == FFRG_MODEL_D4_VERTEX) {
+      fjb = pl->na2;
+      fcr = chunk(8 * 32);
+      fn_chunks = (outer_total + fcr - 1) / fcr;
+    } else {
+      const long long total_outer = (long long)pl->n_ext * outer_total;
+      const long long kRowsWanted = 152LL * 2048;
+      long long nblk = fp64 ? (kRowsWanted + total_outer - 1) / total_outer : 1;
+      nblk = std::max<long long>(1, std::min<long long>(nblk, (pl->na1 + 3) / 4));
+      fjb = (int)((pl->na1 + nblk - 1) / nblk);
+      nblk = (pl->na1 + fjb - 1) / fjb;
+      const int rows_ext = outer_total * (int)nblk;
+      const long long kTargetItems = 8LL * 152 * 32;
+      long long rpi = ((long long)pl->n_ext * rows_ext + kTargetItems - 1) / kTargetItems;
+      rpi = std::min<long long>(std::max<long long>((rpi + 31) / 32 * 32, 32), 256);
+      fcr = (int)std::min<long long>(rpi, rows_ext);
+      fn_chunks = (rows_ext + fcr - 1) / fcr;
+    }
+    fn_items = pl->n_ext * fn_chunks;
+  };
+  forward(false, pl->fcr, pl->fn_chunks, pl->fn_items, pl->fjb);
+  forward(true, pl->fcr64, pl->fn_chunks64, pl->fn_items64, pl->fjb64);
+  // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
+  auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  const size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
+  pl->smem64 = al16((size_t)pl->tab_count * 8) + al16(ang * 8);
+  pl->smem32 = al16((size_t)pl->tab32_count * 8) + al16(ang * 4);
 }
 
 int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {
@@ -259,24 +297,21 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   st = st ? st : upload_rule(ctx, wp, &pl->psi_w);
   size_t nF = (size_t)pl->nr * (2 * pl->N + 1);
   if (!st) st = dev_alloc(ctx, (void **)&pl->radF, nF * sizeof(double));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->radF32, nF * sizeof(float));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq, pl->nr * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq32, pl->nr * sizeof(float));
   if (!st) st = dev_alloc(ctx, (void **)&pl->work_ctr, sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_done, (size_t)pl->n_ext * sizeof(unsigned));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->kconst, kKConstBytes);
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
-  if (!st) st = dev_alloc(ctx, (void **)&pl->partial, (size_t)pl->fn_items * sizeof(double));
+  if (!st)
+    st = dev_alloc(ctx, (void **)&pl->partial, (size_t)std::max(pl->fn_items, pl->fn_items64) * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->tab32, (size_t)pl->tab_count * sizeof(float2));
   if (st) {
     plan_free(ctx, pl);
     return st;
   }
-  // shared memory: tables (FP64 values or FP32 node pairs, 8 bytes a node) +
-  // angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
-  auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
-  pl->smem64 = al16((size_t)pl->tab_count * 8) + al16(ang * 8);
-  pl->smem32 = al16((size_t)pl->tab_count * 8) + al16(ang * 4);
   *out = pl;
   ctx->plans[key] = pl;
   return FFRG_OK;
@@ -302,7 +337,8 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.cr = pl->fcr;
   a.n_chunks = pl->fn_chunks;
   a.n_items = pl->fn_items;
-  a.jb = pl->jb;
+  a.jb = pl->fjb;
+  a.tab32_count = pl->tab32_count;
   a.k = k;
   a.m2_over_k2 = pb->m2_over_k2;
   a.m2_shift = pb->m2_shift;
@@ -333,8 +369,10 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.radF = pl->radF;
   a.radq = pl->radq;
   a.radq32 = pl->radq32;
+  a.radF32 = pl->radF32;
   a.work_ctr = pl->work_ctr;
   a.ext_done = pl->ext_done;
+  a.kconst = pl->kconst;
   a.ext_pd = pl->ext_pd;
   a.psi_s = pl->psi_s;
   a.partial = pl->partial;
@@ -391,6 +429,8 @@ int ffrg_destroy(ffrg_ctx *ctx) {
     cudaFree(pl->radq32);
     cudaFree(pl->work_ctr);
     cudaFree(pl->ext_done);
+    cudaFree(pl->kconst);
+    cudaFree(pl->radF32);
     delete pl;
   }
   ctx->plans.clear();

@@ -30,15 +30,19 @@ constexpr int kMaxNodes = 65536;
 // ---------------------------------------------------------------------------
 // Kernel argument block (passed by value).
 // ---------------------------------------------------------------------------
+// bytes of the per-RHS constant block (FP32 and FP64 scale constants)
+constexpr int kKConstBytes = 256;
+
 struct RhsArgs {
   int model, reg;
   int nr, na1, na2;
   int n_ext_p, n_ext_ang, N, include_p0, n_ext;
   int n_tables, n_stack, n_pts, tab_count;
-  int cr;          // outer rows (radial, or Matsubara x radial) per work item
+  int tab32_count; // float2 entries of the FP32 table layout
+  int cr;          // rows per work item (d=4: outer rows)
   int n_chunks;    // work items per external point
   int n_items;     // n_ext * n_chunks
-  int jb;          // angle nodes per row (D3 / FINITE_T)
+  int jb;          // angle nodes per row (D3 / FINITE_T; rows = outer index x angle block)
   double k, m2_over_k2, m2_shift, T;
   double p_min, p_ratio_step;  // p_i = p_min * exp(i * p_ratio_step)
   double qmax_over_k;
@@ -58,9 +62,11 @@ struct RhsArgs {
   double *radD;                // optional: d radF / d Z(q) (adjoint)
   double *radF;                // per-(n, r) factor
   double *radq;                // per-r momentum q
-  float *radq32;               // per-r momentum q in FP32 (optional, D4)
+  float *radq32;               // per-r momentum q in FP32
+  float *radF32;               // radF in FP32 (mixed kernels)
   unsigned *work_ctr;          // optional: dynamic work-item counter, reset by the precompute kernel
-  unsigned *ext_done;          // optional: finished items per external point (D4), reset likewise
+  unsigned *ext_done;          // finished items per external point, reset likewise
+  void *kconst;                // kKConstBytes: scale constants of the RHS, written by the precompute kernel
   double *ext_pd;              // per external |p| index: p_i (written by the precompute kernel)
   double *psi_s;               // per external angle: sin(psi) (D4)
   double *partial;             // [n_ext][n_chunks]
@@ -324,14 +330,18 @@ struct Plan {
   int nr, na1, na2, n_ext_ang, n_ext_p, N, include_p0, n_ext;
   int n_tables, n_stack, n_pts, tab_count;
   int cr, n_chunks, n_items, jb;  // block-sized work items (adjoint kernels)
-  int fcr, fn_chunks, fn_items;   // work items of the forward RHS kernels (warp-sized for D4)
+  int fcr, fn_chunks, fn_items;   // warp-sized work items of the mixed forward kernels (and serving)
+  int fjb;                        // angle nodes per forward row (D3 / FINITE_T)
+  int fcr64, fn_chunks64, fn_items64, fjb64;  // the same for the FP64 forward kernels
+  int tab32_count;                // float2 entries of the FP32 table layout
   int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
   size_t smem64, smem32;    // dynamic shared memory bytes
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;
   double sum_w2;
   double *radF, *radq, *partial, *ext_pd, *psi_s;
-  float *radq32;
+  float *radq32, *radF32;
   unsigned *work_ctr, *ext_done;
+  void *kconst;
   float2 *tab32;
   double *radD, *gpart;     // adjoint scratch (allocated on first use)
   double *jrows;            // Jacobian rows per work item (allocated on first use)

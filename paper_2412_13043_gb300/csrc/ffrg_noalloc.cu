@@ -101,19 +101,17 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.radF = sc.take<double>((size_t)pl.nr * (2 * pl.N + 1));
   pl.radq = sc.take<double>(pl.nr);
   pl.radq32 = sc.take<float>(pl.nr);
+  pl.radF32 = sc.take<float>((size_t)pl.nr * (2 * pl.N + 1));
   pl.work_ctr = sc.take<unsigned>(4);
   pl.ext_done = sc.take<unsigned>(pl.n_ext);
+  pl.kconst = sc.take<double>(kKConstBytes / sizeof(double));
   pl.ext_pd = sc.take<double>(pl.n_ext_p);
   pl.psi_s = sc.take<double>(npsi);
-  pl.partial = sc.take<double>(pl.fn_items);
-  pl.tab32 = sc.take<float2>((size_t)pl.tab_count);
+  pl.partial = sc.take<double>(std::max(pl.fn_items, pl.fn_items64));
+  pl.tab32 = sc.take<float2>((size_t)pl.tab32_count);
   if (sc.used > kNoallocScratchBytes) return FFRG_EINVAL;  // problem needs more than the 4 MiB scratch
 
-  auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-  size_t ang = (size_t)pl.na1 * 3 + (size_t)pl.na2 * 2;
-  const bool mixed = precision == FFRG_MIXED;
-  const size_t smem = mixed ? al16((size_t)pl.tab_count * 8) + al16(ang * 4)
-                            : al16((size_t)pl.tab_count * 8) + al16(ang * 8);
+  const size_t smem = precision == FFRG_MIXED ? pl.smem32 : pl.smem64;
   if (smem > 227 * 1024) return FFRG_EINVAL;
 
   cudaStream_t s = (cudaStream_t)stream;
@@ -142,8 +140,6 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   lc.profiling = 0;
   lc.prof_used = 0;
   if (cudaDeviceGetAttribute(&lc.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FFRG_ECUDA;
-  pl.smem64 = al16((size_t)pl.tab_count * 8) + al16(ang * 8);
-  pl.smem32 = al16((size_t)pl.tab_count * 8) + al16(ang * 4);
   pl.grid64 = 0;
   pl.grid32 = 0;
   RhsArgs a;

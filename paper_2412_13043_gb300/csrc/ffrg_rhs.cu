@@ -81,18 +81,28 @@ __device__ __noinline__ float pole_ft(const RhsArgs *a, int e, int n, int r, int
   return pole_prop(a, a->tab + (size_t)srow * a->n_pts, q * q + p * p + 2.0 * q * p * c, om * om);
 }
 
-// Scale-dependent constants of one RHS in the kernel precision (computed once
-// per kernel, or per flow in the batched kernels).  us/uo: table coordinate
+// Scale-dependent constants of one RHS in the kernel precision, computed once
+// per RHS by the precompute kernel into a small device block (RhsArgs::kconst)
+// that every CTA of the main kernel loads.  us/uo: table coordinate
 // (divided by n-1 in FP32); plim = -2 m^2 (near-pole test).  The kernels pass
 // squared momenta to the propagator as y = sy s^2 and omega^2 as som omega^2:
 // FP64 sy = som = 1; FP32 sy = log2(e)/k^2 (the regulator's exp2 argument)
 // and som = 1/(k^2 ln 2), with the FP32 Z table pre-scaled by k^2 ln 2
-// (see reg_g).  lnsy = ln(sy) shifts table coordinates taken in y.
+// (see reg_g).
+// uy1..uy4: offsets of table coordinates taken in y of S0^2 = (sum of c
+// squares)/c (c = 1..4; ln(sy) and ln c folded in); twopiT = 2 pi T;
+// sw2 = sum of the second-angle weights.
 template <typename T>
 struct KConst {
   T k2, inv_k2, m2, us, uo, plim, sy, som;
-  double lnsy;
+  T uy1, uy2, uy3, uy4, twopiT, sw2;
 };
+
+struct KConstPair {
+  KConst<float> f;
+  KConst<double> d;
+};
+static_assert(sizeof(KConstPair) <= kKConstBytes, "constant block too small");
 
 template <typename T>
 __device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
@@ -107,8 +117,26 @@ __device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
   const bool f32 = sizeof(T) == 4;
   c.sy = (T)(f32 ? 1.4426950408889634074 / (kd * kd) : 1.0);
   c.som = (T)(f32 ? 1.0 / (kd * kd * 0.6931471805599453094) : 1.0);
-  c.lnsy = f32 ? log(1.4426950408889634074 / (kd * kd)) : 0.0;
+  const double lnsy = f32 ? log(1.4426950408889634074 / (kd * kd)) : 0.0;
+  // S0^2 = (sum of squares)/c: the 1/c is a shift of the coordinate, -u_scale ln c
+  c.uy1 = lerp_off<T>(a.u_off - a.u_scale * lnsy, a.n_pts);
+  c.uy2 = lerp_off<T>(a.u_off - a.u_scale * (0.69314718055994530942 + lnsy), a.n_pts);
+  c.uy3 = lerp_off<T>(a.u_off - a.u_scale * (1.09861228866810969140 + lnsy), a.n_pts);
+  c.uy4 = lerp_off<T>(a.u_off - a.u_scale * (1.38629436111989061883 + lnsy), a.n_pts);
+  c.twopiT = (T)(2.0 * kPi * a.T);
+  c.sw2 = (T)a.sum_w2;
   return c;
+}
+
+template <typename T>
+__device__ __forceinline__ KConst<T> load_kconst(const RhsArgs &a);
+template <>
+__device__ __forceinline__ KConst<float> load_kconst<float>(const RhsArgs &a) {
+  return ((const KConstPair *)a.kconst)->f;
+}
+template <>
+__device__ __forceinline__ KConst<double> load_kconst<double>(const RhsArgs &a) {
+  return ((const KConstPair *)a.kconst)->d;
 }
 
 // FP32 regulator in propagator form.  With x = s^2/k^2 the kinetic part of the
@@ -170,7 +198,13 @@ struct MinBlocks<float> {
 __device__ __forceinline__ bool skipped(const RhsArgs &a) { return a.skip && *(volatile const int *)a.skip; }
 
 __device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int stride) {
-  if (a.work_ctr && tid0 == 0) *a.work_ctr = 0u;  // the main kernel runs after this one (stream order)
+  // the main kernel runs after this one (stream order)
+  if (tid0 == 0 && a.work_ctr) *a.work_ctr = 0u;
+  if (a.kconst && tid0 < 2) {
+    KConstPair *kp = (KConstPair *)a.kconst;
+    if (tid0 == 0) kp->f = make_kconst<float>(a);
+    else kp->d = make_kconst<double>(a);
+  }
   const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
   const double L = a.qmax_over_k * k;
   const int total = (2 * a.N + 1) * a.nr;
@@ -208,16 +242,25 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int 
       }
     }
     a.radF[idx] = F;
+    if (a.radF32) a.radF32[idx] = (float)F;
   }
-  // FP32 node pairs; the Z table (table 0, every stack row) carries the factor
-  // k^2 ln 2 of the FP32 propagator form
+  // FP32 tables; the Z table (table 0, every stack row) carries the factor
+  // k^2 ln 2 of the FP32 propagator form.  d=3, d=4: (value, difference to
+  // the next node; 0 at a row end) pairs.  Finite T: (Z, lambda) pairs per
+  // node of each stack row, then one zero pair (the upper neighbour of the
+  // last node, read with weight 0).
   const double kh = k2 * 0.6931471805599453094;
   const int z_count = a.n_stack * a.n_pts;
-  for (int i = tid0; i < a.tab_count; i += stride) {
-    const double f = i < z_count ? kh : 1.0;
-    const float v = (float)(f * a.tab[i]);
-    const float d = (i % a.n_pts == a.n_pts - 1) ? 0.0f : (float)(f * a.tab[i + 1]) - v;
-    a.tab32[i] = make_float2(v, d);
+  if (a.model == FFRG_MODEL_FINITE_T) {
+    for (int i = tid0; i <= z_count; i += stride)
+      a.tab32[i] = i < z_count ? make_float2((float)(kh * a.tab[i]), (float)a.tab[z_count + i]) : make_float2(0.f, 0.f);
+  } else {
+    for (int i = tid0; i < a.tab_count; i += stride) {
+      const double f = i < z_count ? kh : 1.0;
+      const float v = (float)(f * a.tab[i]);
+      const float d = (i % a.n_pts == a.n_pts - 1) ? 0.0f : (float)(f * a.tab[i + 1]) - v;
+      a.tab32[i] = make_float2(v, d);
+    }
   }
   if (a.ext_done)
     for (int i = tid0; i < a.n_ext; i += stride) a.ext_done[i] = 0u;
@@ -265,9 +308,11 @@ struct SmemLayout {
   Tab *tab;
   P2 *cw2;
   T *c1, *s1, *w1;
+  // table entries in shared memory: FP64 values, or the FP32 layout
+  static __device__ int entries(const RhsArgs &a) { return sizeof(T) == 4 ? a.tab32_count : a.tab_count; }
   __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
     tab = (Tab *)base;
-    size_t off = ((size_t)a.tab_count * sizeof(Tab) + 15) & ~(size_t)15;
+    size_t off = ((size_t)entries(a) * sizeof(Tab) + 15) & ~(size_t)15;
     cw2 = (P2 *)(base + off);
     c1 = (T *)(cw2 + a.na2);
     s1 = c1 + a.na1;
@@ -302,74 +347,258 @@ __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S)
 
 template <typename T>
 __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
-  bool ok = stage_to_smem<typename TabOf<T>::type>(S.tab, table_src<T>(a), a.tab_count, bar, a.status);
+  bool ok = stage_to_smem<typename TabOf<T>::type>(S.tab, table_src<T>(a), SmemLayout<T>::entries(a), bar,
+                                                   a.status);
   stage_angles<T>(a, S);
   __syncthreads();
   return ok;
 }
 
 // ---------------------------------------------------------------------------
-// 2a. d=3, T=0:  row (r, angle block): sum_j v_j G(|q+p|)
-// One work item: partial sum of external point e over a chunk of radial rows
-// (returned in thread 0).  `sa` is the argument block the near-pole path reads.
+// 2. main kernels.  Work items are warp-sized: external point e x a chunk of
+// `cr` outer rows (d=3: radial nodes; finite T: (Matsubara n, radial node)
+// pairs; d=4: (radial node, first-angle node) pairs).  Lane l takes rows
+// l, l+32, ... of its item and loops over the remaining angle nodes of each
+// row in the kernel precision; each row sum, times the row's radial factor,
+// enters the lane's accumulator (RowAcc), and the warp reduces its item with
+// shuffles.
+// The single-flow kernels take items from a device counter; the warp that
+// completes the last item of an external point writes that output.  The
+// serving kernel walks per-flow item ranges (outputs by a finalize kernel).
+// One warp sums each item in a fixed order, so results depend neither on
+// which warp took it nor on the grid.  `sa` is the argument block in shared
+// memory that the out-of-line near-pole path reads.  Squared momenta enter
+// lookups and propagators as y = sy s^2 (table offsets uy1..uy4).
 // ---------------------------------------------------------------------------
+// Per-lane accumulation of radial factor x row sum, then the warp's item sum
+// (valid in lane 0).  FP64 kernels: FP64 FMA and an FP64 shuffle tree.  FP32
+// kernels: Kahan-compensated FP32 over the lane's rows (error ~2u of the lane
+// sum), then a shuffle tree on (hi, lo) FP32 pairs with an error-free
+// two-sum at every level (Knuth's TwoSum), rounded to FP64 at the end: no
+// FP64 arithmetic per row or per tree level.
 template <typename T>
-__device__ __forceinline__ double d3_item(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
-                                          const KConst<T> &kc, int item, double *red) {
-  const T us = kc.us, uo = kc.uo;
-  const int np = a.n_pts, nblk = (a.na1 + a.jb - 1) / a.jb;
-  const int e = item / a.n_chunks, c = item - e * a.n_chunks;
-  const double pd = (e < a.n_ext_p) ? a.ext_pd[e] : 0.0;
-  const T p = (T)pd;
-  const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
-  const int rows = (o1 - o0) * nblk;
-  double acc = 0.0;
-  for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-    const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
-    const double qd = a.radq[o];
-    const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
-    T rs = 0;
-    for (int j = jb0; j < jb1; ++j) {
-      const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
-      T Z = lerp(S.tab, s2, us, uo, np);
-      auto pole = [&]() { return pole_d3(sa, e, o, j); };
-      rs += S.w1[j] * inv_prop(a, Z, s2 * kc.sy, (T)0, kc, pole);
+struct RowAcc;
+template <>
+struct RowAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double F, double x) { s = fma(F, x, s); }
+  __device__ __forceinline__ double item_sum() const {
+    double v = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+  }
+};
+template <>
+struct RowAcc<float> {
+  float s = 0.f, c = 0.f;  // running sum and Kahan compensation (value = s - c)
+  __device__ __forceinline__ void add(float F, float x) {
+    const float y = fmaf(F, x, -c);
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double item_sum() const {
+    float hi = s, lo = -c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+      const float S = hi + h2, bp = S - hi;
+      const float err = (hi - (S - bp)) + (h2 - bp);  // hi + h2 = S + err exactly
+      lo = lo + l2 + err;
+      hi = S;
     }
-    acc = fma(a.radF[o], (double)rs, acc);
+    return (double)hi + (double)lo;
   }
-  return block_sum(acc, red);
-}
+};
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d3_main(RhsArgs a) {
-  if (skipped(a)) return;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar;
-  __shared__ double red[kThreads / 32];
-  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
-  if (threadIdx.x == 0) sa = a;
-  SmemLayout<T> S(smem, a);
-  if (!main_prologue<T>(a, S, &bar)) return;
-  const KConst<T> kc = make_kconst<T>(a);
-  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    double t = d3_item<T>(a, &sa, S, kc, item, red);
-    if (threadIdx.x == 0) a.partial[item] = t;
-  }
-}
+__device__ __forceinline__ T radial_F(const RhsArgs &a, int o);
+template <>
+__device__ __forceinline__ double radial_F<double>(const RhsArgs &a, int o) { return a.radF[o]; }
+template <>
+__device__ __forceinline__ float radial_F<float>(const RhsArgs &a, int o) { return a.radF32[o]; }
 
-// ---------------------------------------------------------------------------
-// 2b. d=4 vertex expansion: row (r, c1 node), inner loop over c2 nodes.
-// Work items are warp-sized (about eight rows per lane) and are handed out by
-// a device counter, the three-point items (the 16x more expensive ones) first.
-// Each item is summed by one warp in a fixed order (rows by lane, then a
-// shuffle tree), so the result does not depend on which warp took it.
-// ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T radial_q(const RhsArgs &a, int r);
 template <>
 __device__ __forceinline__ double radial_q<double>(const RhsArgs &a, int r) { return a.radq[r]; }
 template <>
 __device__ __forceinline__ float radial_q<float>(const RhsArgs &a, int r) { return a.radq32[r]; }
+
+// d=3, T=0: row = (radial node o, block of jb angle nodes);
+// sum_j v_j G(|q+p|)
+template <typename T, bool POLE>
+__device__ __forceinline__ RowAcc<T> d3_witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                           const KConst<T> &kc, int e, int c, int lane) {
+  const T us = kc.us, uy1 = kc.uy1, sy = kc.sy;
+  const int np = a.n_pts, na1 = a.na1, jb = a.jb, nblk = (na1 + jb - 1) / jb;
+  const T p = (T)((e < a.n_ext_p) ? a.ext_pd[e] : 0.0);
+  const int r0 = c * a.cr, r1 = min(r0 + a.cr, a.nr * nblk);
+  RowAcc<T> acc;
+  for (int rr = r0 + lane; rr < r1; rr += 32) {
+    const int o = rr / nblk, j0 = (rr - o * nblk) * jb, j1 = min(j0 + jb, na1);
+    const T q = radial_q<T>(a, o);
+    const T by = (q * q + p * p) * sy, ty = (T)2 * q * p * sy;
+    T rs = 0;
+    for (int j = j0; j < j1; ++j) {
+      const T y = by + ty * S.c1[j];   // sy |q+p|^2, >= 0 up to rounding; lookups clamp
+      const T Z = lerp(S.tab, y, us, uy1, np);
+      auto pole = [&]() { return pole_d3(sa, e, o, j); };
+      rs += S.w1[j] * inv_prop<POLE>(a, Z, y, (T)0, kc, pole);
+    }
+    acc.add(radial_F<T>(a, o), rs);
+  }
+  return acc;
+}
+
+// finite-T lookups of Z and lambda at stack row srow: FP64 tables [table][row][pt];
+// FP32 (Z, lambda) node pairs [row][pt] (+ one zero pair)
+__device__ __forceinline__ void zl_lookup(const double *tab, const RhsArgs &a, int srow, int i0, double w, double &Z,
+                                          double &L) {
+  Z = lerp_at(tab + (size_t)srow * a.n_pts, i0, w);
+  L = lerp_at(tab + ((size_t)a.n_stack + srow) * a.n_pts, i0, w);
+}
+__device__ __forceinline__ void zl_lookup(const float2 *tab, const RhsArgs &a, int srow, int i0, float w, float &Z,
+                                          float &L) {
+  const float2 *row = tab + (size_t)srow * a.n_pts;
+  const float2 v0 = row[i0], v1 = row[i0 + 1];
+  Z = fmaf(w, v1.x - v0.x, v0.x);
+  L = fmaf(w, v1.y - v0.y, v0.y);
+}
+
+// finite T: row = ((Matsubara n, radial node r), block of jb angle nodes);
+// sum_j v_j lam(n+m, s) G(n+m, s), s = |q+p|
+template <typename T, bool POLE>
+__device__ __forceinline__ RowAcc<T> ft_witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                           const KConst<T> &kc, int e, int c, int lane) {
+  const T us = kc.us, uy1 = kc.uy1, sy = kc.sy;
+  const int np = a.n_pts, nm = a.n_ext_ang, na1 = a.na1, nr = a.nr, jb = a.jb, nblk = (na1 + jb - 1) / jb;
+  const int outer_total = (2 * a.N + 1) * nr;
+  const int ip = e / nm, m = e - ip * nm;
+  const T p = (T)a.ext_pd[ip], p2 = p * p;
+  const int r0 = c * a.cr, r1 = min(r0 + a.cr, outer_total * nblk);
+  RowAcc<T> acc;
+  for (int rr = r0 + lane; rr < r1; rr += 32) {
+    const int o = rr / nblk, j0 = (rr - o * nblk) * jb, j1 = min(j0 + jb, na1);
+    const int nn = o / nr, r = o - nn * nr, n = nn - a.N;
+    const int srow = min(abs(n + m), a.n_stack - 1);
+    const T om = kc.twopiT * (T)(n + m);
+    const T om2s = om * om * kc.som;
+    const T q = radial_q<T>(a, r);
+    const T by = (q * q + p2) * sy, ty = (T)2 * q * p * sy;
+    T rs = 0;
+    for (int j = j0; j < j1; ++j) {
+      const T y = by + ty * S.c1[j];
+      int i0;
+      T w, Z, Lv;
+      lerp_pos(y, us, uy1, np, i0, w);
+      zl_lookup(S.tab, a, srow, i0, w, Z, Lv);
+      auto pole = [&]() { return pole_ft(sa, e, n, r, j); };
+      rs += S.w1[j] * Lv * inv_prop<POLE>(a, Z, y, om2s, kc, pole);
+    }
+    acc.add(radial_F<T>(a, o), rs);
+  }
+  return acc;
+}
+
+// d=4 vertex expansion: row = (radial node r, first-angle node ia), inner loop
+// over the second-angle nodes for the three-point block
+template <typename T, bool POLE>
+__device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                           const KConst<T> &kc, int e, int c, int lane) {
+  const T us = kc.us, sy = kc.sy;
+  const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang, na1 = a.na1;
+  const auto *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
+  int block, ip, jp = 0;
+  if (e <= np_) {
+    block = 0;
+    ip = e;
+  } else if (e < np_ + 1 + np_ * npsi) {
+    block = 1;
+    ip = (e - np_ - 1) / npsi;
+    jp = (e - np_ - 1) - ip * npsi;
+  } else {
+    block = 2;
+    ip = e - np_ - 1 - np_ * npsi;
+  }
+  const double pd = (block == 0 && ip == np_) ? 0.0 : a.ext_pd[ip];
+  const T p = (T)pd, p2 = p * p;
+  const T cpsi = (T)(block == 1 ? a.psi_x[jp] : 1.0), spsi = (T)(block == 1 ? a.psi_s[jp] : 0.0);
+  const T C2 = (T)2 * p2 * ((T)1 + cpsi);
+  const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
+  const int rows = (o1 - o0) * na1;
+  const int dr = 32 / na1, dia = 32 % na1;  // row step of one lane in (r, ia)
+  RowAcc<T> acc;
+  int r = o0 + lane / na1, ia = lane % na1;
+  for (int row = lane; row < rows; row += 32) {
+    const T q = radial_q<T>(a, r), q2 = q * q, qp = q * p, c1 = S.c1[ia];
+    const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
+    const T Ay = A2 * sy;
+    const T ZA = lerp(Zt, Ay, us, kc.uy1, np);
+    auto pole_a = [&]() { return pole_d4(sa, e, r, ia, -1); };
+    const T GA = inv_prop<POLE>(a, ZA, Ay, (T)0, kc, pole_a);
+    T v;
+    if (block == 0) {
+      const T l4 = lerp(L4, (q2 + p2) * sy, us, kc.uy2, np);
+      const T l3 = lerp(L3, (q2 + A2 + p2) * sy, us, kc.uy3, np);
+      v = kc.sw2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
+    } else if (block == 2) {
+      const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * sy, us, kc.uy4, np);
+      v = kc.sw2 * GA * l4 * l4;
+    } else {
+      const T uy1 = kc.uy1, uy3 = kc.uy3;
+      const T la = lerp(L3, (q2 + A2 + p2) * sy, us, uy3, np);
+      const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
+      const T by = base * sy, b0 = (base - t1) * sy, t2y = t2 * sy, sy_ab = (A2 + C2) * sy;
+      T rs = 0;
+      for (int b = 0; b < a.na2; ++b) {
+        const auto cw = S.cw2[b];
+        const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
+        const T ZB = lerp(Zt, By, us, uy1, np);
+        auto pole_b = [&]() { return pole_d4(sa, e, r, ia, b); };
+        const T GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
+        const T lb = lerp(L3, by + By, us, uy3, np);
+        const T lc = lerp(L3, sy_ab + By, us, uy3, np);
+        rs += cw.y * GB * lb * lc;
+      }
+      v = GA * la * rs;
+    }
+    acc.add(radial_F<T>(a, r), S.w1[ia] * v);
+    r += dr;
+    ia += dia;
+    if (ia >= na1) {
+      ia -= na1;
+      ++r;
+    }
+  }
+  return acc;
+}
+
+template <int MODEL, typename T, bool POLE>
+__device__ __forceinline__ RowAcc<T> witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                        const KConst<T> &kc, int e, int c, int lane) {
+  if constexpr (MODEL == FFRG_MODEL_D3) return d3_witem<T, POLE>(a, sa, S, kc, e, c, lane);
+  else if constexpr (MODEL == FFRG_MODEL_D4_VERTEX) return d4_witem<T, POLE>(a, sa, S, kc, e, c, lane);
+  else return ft_witem<T, POLE>(a, sa, S, kc, e, c, lane);
+}
+
+// warp sum in a fixed order (valid in lane 0)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The near-pole test can only fire with m^2 < 0 or a negative Z node (table
+// 0, every stack row).  Block-wide: every thread of the CTA must call it.
+template <typename T>
+__device__ __forceinline__ bool pole_possible(const RhsArgs &a, const SmemLayout<T> &S, const KConst<T> &kc) {
+  int neg = 0;
+  const int nz = a.n_stack * a.n_pts;
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) neg |= table_value(S.tab[i]) < (T)0;
+  return __syncthreads_or(neg) || kc.m2 < (T)0;
+}
 
 // Output of external point e from the sum s of its partials: diagram
 // coefficient (d=4: 1, 3, 3/2 for the Z, lambda3, lambda4 blocks), overall
@@ -386,116 +615,48 @@ __device__ __forceinline__ void write_output(const RhsArgs &a, int e, double s) 
   if (!isfinite(v)) raise_status(a.status, kStatusNonFinite);
 }
 
-// Work loop of the d=4 kernel.  All squared momenta are taken as y = sy s^2;
-// table coordinates in y use offsets shifted by -u_scale ln(sy).
-template <typename T, bool POLE>
-__device__ __forceinline__ void d4_items(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
-                                         const KConst<T> &kc) {
-  const T us = kc.us, sy = kc.sy;
-  // S0^2 = (sum of squares)/c: the 1/c is a shift of the coordinate, -u_scale ln c
-  const T uo1 = lerp_off<T>(a.u_off - a.u_scale * kc.lnsy, a.n_pts);
-  const T uo2 = lerp_off<T>(a.u_off - a.u_scale * (0.69314718055994530942 + kc.lnsy), a.n_pts);
-  const T uo3 = lerp_off<T>(a.u_off - a.u_scale * (1.09861228866810969140 + kc.lnsy), a.n_pts);
-  const T uo4 = lerp_off<T>(a.u_off - a.u_scale * (1.38629436111989061883 + kc.lnsy), a.n_pts);
-  const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang, na1 = a.na1;
-  const auto *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
-  const T sum_w2 = (T)a.sum_w2;
+// Sum of the partials of one external point in a fixed order: lane l adds
+// chunks l, l+32, ..., then the warp tree (valid in lane 0).  The single-flow
+// and serving kernels share it, so both give bitwise the same outputs.
+__device__ __forceinline__ double sum_partials(const RhsArgs &a, int e, int lane) {
+  const double *pp = a.partial + (size_t)e * a.n_chunks;
+  double t = 0.0;
+  for (int j = lane; j < a.n_chunks; j += 32) t += __ldcg(pp + j);
+  return warp_sum(t);
+}
+
+// Single-flow work loop: items from the device counter (d=4: the three-point
+// block, 16x more work per item, first), outputs by the warp that completes
+// an external point (fixed-order sum of its partials).
+template <int MODEL, typename T, bool POLE>
+__device__ __forceinline__ void item_loop(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                          const KConst<T> &kc) {
   const int lane = threadIdx.x & 31;
-  const int dr = 32 / na1, dia = 32 % na1;  // row step of one lane in (r, ia)
+  const int rot = MODEL == FFRG_MODEL_D4_VERTEX ? a.n_ext_p + 1 : 0;
   for (;;) {
     int d = 0;
     if (lane == 0) d = (int)atomicAdd(a.work_ctr, 1u);
     d = __shfl_sync(0xffffffffu, d, 0);
     if (d >= a.n_items) break;
-    // rank d -> external point: rotate so that the three-point block comes first
-    const int c = d % a.n_chunks;
-    const int e = (d / a.n_chunks + np_ + 1) % a.n_ext;
-    const int item = e * a.n_chunks + c;
-    int block, ip, jp = 0;
-    if (e <= np_) {
-      block = 0;
-      ip = e;
-    } else if (e < np_ + 1 + np_ * npsi) {
-      block = 1;
-      ip = (e - np_ - 1) / npsi;
-      jp = (e - np_ - 1) - ip * npsi;
-    } else {
-      block = 2;
-      ip = e - np_ - 1 - np_ * npsi;
-    }
-    const double pd = (block == 0 && ip == np_) ? 0.0 : a.ext_pd[ip];
-    const double cpsid = block == 1 ? a.psi_x[jp] : 1.0;
-    const double spsid = block == 1 ? a.psi_s[jp] : 0.0;
-    const T p = (T)pd, p2 = p * p, cpsi = (T)cpsid, spsi = (T)spsid;
-    const T C2 = (T)2 * p2 * ((T)1 + cpsi);
-    const int o0 = c * a.cr, o1 = min(o0 + a.cr, a.nr);
-    const int rows = (o1 - o0) * na1;
-    double acc = 0.0;
-    int r = o0 + lane / na1, ia = lane % na1;
-    for (int row = lane; row < rows; row += 32) {
-      const T q = radial_q<T>(a, r), q2 = q * q, qp = q * p, c1 = S.c1[ia];
-      const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
-      const T Ay = A2 * sy;
-      const T ZA = lerp(Zt, Ay, us, uo1, np);
-      auto pole_a = [&]() { return pole_d4(sa, e, r, ia, -1); };
-      const T GA = inv_prop<POLE>(a, ZA, Ay, (T)0, kc, pole_a);
-      T v;
-      if (block == 0) {
-        const T l4 = lerp(L4, (q2 + p2) * sy, us, uo2, np);
-        const T l3 = lerp(L3, (q2 + A2 + p2) * sy, us, uo3, np);
-        v = sum_w2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
-      } else if (block == 2) {
-        const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * sy, us, uo4, np);
-        v = sum_w2 * GA * l4 * l4;
-      } else {
-        const T la = lerp(L3, (q2 + A2 + p2) * sy, us, uo3, np);
-        const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
-        const T by = base * sy, b0 = (base - t1) * sy, t2y = t2 * sy, sy_ab = (A2 + C2) * sy;
-        T rs = 0;
-        for (int b = 0; b < a.na2; ++b) {
-          const auto cw = S.cw2[b];
-          const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
-          const T ZB = lerp(Zt, By, us, uo1, np);
-          auto pole_b = [&]() { return pole_d4(sa, e, r, ia, b); };
-          const T GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
-          const T lb = lerp(L3, by + By, us, uo3, np);
-          const T lc = lerp(L3, sy_ab + By, us, uo3, np);
-          rs += cw.y * GB * lb * lc;
-        }
-        v = GA * la * rs;
-      }
-      acc = fma(a.radF[r], (double)(S.w1[ia] * v), acc);
-      r += dr;
-      ia += dia;
-      if (ia >= na1) {
-        ia -= na1;
-        ++r;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    // the warp that completes external point e sums its partials (fixed order)
+    const int c = d % a.n_chunks, e = (d / a.n_chunks + rot) % a.n_ext;
+    const double acc = witem<MODEL, T, POLE>(a, sa, S, kc, e, c, lane).item_sum();
     unsigned done = 0;
     if (lane == 0) {
-      a.partial[item] = acc;
+      a.partial[(size_t)e * a.n_chunks + c] = acc;
       __threadfence();
       done = atomicAdd(a.ext_done + e, 1u);
     }
     done = __shfl_sync(0xffffffffu, done, 0);
     if (done == (unsigned)a.n_chunks - 1u) {
       __threadfence();
-      const double *pp = a.partial + (size_t)e * a.n_chunks;
-      double t = 0.0;
-      for (int j = lane; j < a.n_chunks; j += 32) t += __ldcg(pp + j);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      const double t = sum_partials(a, e, lane);
       if (lane == 0) write_output(a, e, t);
     }
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs a) {
+template <int MODEL, typename T>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) rhs_main(RhsArgs a) {
   if (skipped(a)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
@@ -503,91 +664,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) d4_main(RhsArgs
   if (threadIdx.x == 0) sa = a;
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
-  const KConst<T> kc = make_kconst<T>(a);
-  // the near-pole test can only fire with m^2 < 0 or a negative Z node
-  int neg = 0;
-  for (int i = threadIdx.x; i < a.n_pts; i += blockDim.x) neg |= table_value(S.tab[i]) < (T)0;
-  const bool may_pole = __syncthreads_or(neg) || kc.m2 < (T)0;
-  if (may_pole) d4_items<T, true>(a, &sa, S, kc);
-  else d4_items<T, false>(a, &sa, S, kc);
+  const KConst<T> kc = load_kconst<T>(a);
+  if (pole_possible<T>(a, S, kc)) item_loop<MODEL, T, true>(a, &sa, S, kc);
+  else item_loop<MODEL, T, false>(a, &sa, S, kc);
 }
 
-// ---------------------------------------------------------------------------
-// 2c. finite T: row (Matsubara n, r, angle block)
-//     sum_j v_j lam(n+m, s) G(n+m, s), s = |q+p|
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ double ft_item(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
-                                          const KConst<T> &kc, int item, double *red) {
-  const T us = kc.us, uo = kc.uo;
-  const int np = a.n_pts, nm = a.n_ext_ang, nblk = (a.na1 + a.jb - 1) / a.jb;
-  const int outer_total = (2 * a.N + 1) * a.nr;
-  const int e = item / a.n_chunks, c = item - e * a.n_chunks;
-  const int ip = e / nm, m = e - ip * nm;
-  const double pd = a.ext_pd[ip];
-  const T p = (T)pd;
-  const int o0 = c * a.cr, o1 = min(o0 + a.cr, outer_total);
-  const int rows = (o1 - o0) * nblk;
-  double acc = 0.0;
-  for (int row = threadIdx.x; row < rows; row += blockDim.x) {
-    const int o = o0 + row / nblk, jb0 = (row % nblk) * a.jb, jb1 = min(jb0 + a.jb, a.na1);
-    const int n = o / a.nr - a.N, r = o % a.nr;
-    const int srow = min(abs(n + m), a.n_stack - 1);
-    const auto *Zr = S.tab + (size_t)srow * np, *Lr = S.tab + ((size_t)a.n_stack + srow) * np;
-    const double omd = 2.0 * kPi * a.T * (double)(n + m);
-    const T om2s = (T)(omd * omd) * kc.som;
-    const double qd = a.radq[r];
-    const T q = (T)qd, q2 = q * q, base = q2 + p * p, tqp = (T)2 * q * p;
-    T rs = 0;
-    for (int j = jb0; j < jb1; ++j) {
-      const T s2 = base + tqp * S.c1[j];   // >= 0 up to rounding; lookups clamp
-      int i0;
-      T w;
-      lerp_pos(s2, us, uo, np, i0, w);
-      const T Z = lerp_at(Zr, i0, w), Lv = lerp_at(Lr, i0, w);
-      auto pole = [&]() { return pole_ft(sa, e, n, r, j); };
-      rs += S.w1[j] * Lv * inv_prop(a, Z, s2 * kc.sy, om2s, kc, pole);
-    }
-    acc = fma(a.radF[o], (double)rs, acc);
-  }
-  return block_sum(acc, red);
-}
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) ft_main(RhsArgs a) {
-  if (skipped(a)) return;
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ uint64_t bar;
-  __shared__ double red[kThreads / 32];
-  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
-  if (threadIdx.x == 0) sa = a;
-  SmemLayout<T> S(smem, a);
-  if (!main_prologue<T>(a, S, &bar)) return;
-  const KConst<T> kc = make_kconst<T>(a);
-  for (int item = blockIdx.x; item < a.n_items; item += gridDim.x) {
-    double t = ft_item<T>(a, &sa, S, kc, item, red);
-    if (threadIdx.x == 0) a.partial[item] = t;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// 3. finalize: fixed-order sum over chunks, normalisation, finiteness
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void finalize_body(const RhsArgs &a, int e) {
-  if (e >= a.n_ext) return;
-  double s = 0.0;
-  const double *pp = a.partial + (size_t)e * a.n_chunks;
-  for (int c = 0; c < a.n_chunks; ++c) s += pp[c];
-  write_output(a, e, s);
-}
-
-__global__ void finalize_kernel(RhsArgs a) {
-  if (skipped(a)) return;
-  finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-// ---------------------------------------------------------------------------
-// launch
 // ---------------------------------------------------------------------------
 template <typename K>
 static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int *grid) {
@@ -605,7 +687,9 @@ static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int 
     ctx->last_error = "RHS kernel cannot be resident";
     return FFRG_EINVAL;
   }
-  *grid = std::max(1, std::min(items, per_sm * ctx->num_sms));
+  // one warp-sized item per warp is the most a CTA can start with
+  const int ctas = (items + kThreads / 32 - 1) / (kThreads / 32);
+  *grid = std::max(1, std::min(ctas, per_sm * ctx->num_sms));
   return FFRG_OK;
 }
 
@@ -616,20 +700,29 @@ int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s) {
   return set_cuda_error(ctx, cudaGetLastError(), "precompute launch");
 }
 
-int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision, cudaStream_t s) {
+int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precision, cudaStream_t s) {
   Plan *pl = const_cast<Plan *>(pl_c);
   const bool mixed = precision == FFRG_MIXED;
+  RhsArgs a = a_in;  // forward geometry of this precision
+  if (!mixed) {
+    a.cr = pl->fcr64;
+    a.n_chunks = pl->fn_chunks64;
+    a.n_items = pl->fn_items64;
+    a.jb = pl->fjb64;
+  }
   int st;
   int &grid = mixed ? pl->grid32 : pl->grid64;
   const size_t smem = mixed ? pl->smem32 : pl->smem64;
   void (*kern)(RhsArgs) = nullptr;
   switch (a.model) {
-  case FFRG_MODEL_D3: kern = mixed ? d3_main<float> : d3_main<double>; break;
-  case FFRG_MODEL_D4_VERTEX: kern = mixed ? d4_main<float> : d4_main<double>; break;
-  default: kern = mixed ? ft_main<float> : ft_main<double>; break;
+  case FFRG_MODEL_D3: kern = mixed ? rhs_main<FFRG_MODEL_D3, float> : rhs_main<FFRG_MODEL_D3, double>; break;
+  case FFRG_MODEL_D4_VERTEX:
+    kern = mixed ? rhs_main<FFRG_MODEL_D4_VERTEX, float> : rhs_main<FFRG_MODEL_D4_VERTEX, double>;
+    break;
+  default: kern = mixed ? rhs_main<FFRG_MODEL_FINITE_T, float> : rhs_main<FFRG_MODEL_FINITE_T, double>; break;
   }
-  if (a.model == FFRG_MODEL_D4_VERTEX && (!a.work_ctr || !a.radq32 || !a.ext_done)) {
-    ctx->last_error = "d=4 plan without work counter or FP32 radial nodes";
+  if (!a.work_ctr || !a.radq32 || !a.ext_done || !a.kconst) {
+    ctx->last_error = "plan without work counters, FP32 radial nodes or constant block";
     return FFRG_EINVAL;
   }
   if (grid == 0) {
@@ -649,9 +742,7 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a, int precision,
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;
   }
-  // the d=4 kernel writes its outputs itself (last warp per external point)
-  if (a.model != FFRG_MODEL_D4_VERTEX)
-    finalize_kernel<<<(a.n_ext + kThreads - 1) / kThreads, kThreads, 0, s>>>(a);
+  // the main kernel writes the outputs (last warp per external point)
   return set_cuda_error(ctx, cudaGetLastError(), "rhs launch");
 }
 
@@ -669,50 +760,53 @@ __global__ void __launch_bounds__(kThreads) batched_precompute_kernel(const RhsA
   precompute_body(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
+// one warp per external point of flow blockIdx.y
 __global__ void batched_finalize_kernel(const RhsArgs *descs) {
   const RhsArgs &a = descs[blockIdx.y];
   if (skipped(a)) return;
-  finalize_body(a, blockIdx.x * blockDim.x + threadIdx.x);
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (e >= a.n_ext) return;
+  const double t = sum_partials(a, e, lane);
+  if (lane == 0) write_output(a, e, t);
 }
 
-// Each CTA walks a contiguous range of the combined item list; when the range
-// crosses into another flow it copies that flow's descriptor and FP32 tables
-// into shared memory (plain loads) before continuing.
+// Each CTA walks a contiguous range of the combined item list, one flow
+// segment at a time: it copies the flow's descriptor, FP32 tables and angle
+// rules into shared memory (plain loads), then its warps take the segment's
+// warp-sized items in turn.
 template <int MODEL>
 __global__ void __launch_bounds__(kThreads, 4)
     batched_main_kernel(const RhsArgs *descs, const int *flows, const int *start, int n_fl, int total, int per) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double red[kThreads / 32];
   __shared__ RhsArgs sa;
+  __shared__ int skip;
   const int g0 = blockIdx.x * per, g1 = min(g0 + per, total);
-  int cur = -1, lo = 0, hi = 0;
-  SmemLayout<float> S(smem, descs[flows[0]]);
-  KConst<float> kc;
-  bool skip = false;
-  for (int g = g0; g < g1; ++g) {
-    if (g >= hi) {  // next flow: find f with start[f] <= g < start[f+1]
-      int f = (cur < 0) ? 0 : cur + 1;
-      while (f < n_fl && start[f + 1] <= g) ++f;
-      cur = f;
-      lo = start[f];
-      hi = start[f + 1];
-      __syncthreads();
-      if (threadIdx.x == 0) sa = descs[flows[f]];
-      __syncthreads();
-      skip = sa.skip && *(volatile const int *)sa.skip;
-      if (!skip) {
-        S = SmemLayout<float>(smem, sa);
-        for (int i = threadIdx.x; i < sa.tab_count; i += blockDim.x) S.tab[i] = sa.tab32[i];
-        stage_angles<float>(sa, S);
-        kc = make_kconst<float>(sa);
-      }
-      __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int f = 0;
+  while (f < n_fl && start[f + 1] <= g0) ++f;
+  for (; f < n_fl && start[f] < g1; ++f) {
+    const int lo = max(g0, start[f]), hi = min(g1, start[f + 1]);
+    if (lo >= hi) continue;
+    __syncthreads();  // the previous segment's tables are no longer read
+    if (threadIdx.x == 0) {
+      sa = descs[flows[f]];
+      skip = skipped(sa);
     }
+    __syncthreads();
     if (skip) continue;
-    const int item = g - lo;
-    double t = (MODEL == FFRG_MODEL_D3) ? d3_item<float>(sa, &sa, S, kc, item, red)
-                                        : ft_item<float>(sa, &sa, S, kc, item, red);
-    if (threadIdx.x == 0) sa.partial[item] = t;
+    SmemLayout<float> S(smem, sa);
+    for (int i = threadIdx.x; i < sa.tab32_count; i += blockDim.x) S.tab[i] = sa.tab32[i];
+    stage_angles<float>(sa, S);
+    __syncthreads();
+    const KConst<float> kc = load_kconst<float>(sa);
+    const bool pole = pole_possible<float>(sa, S, kc);
+    for (int g = lo + warp; g < hi; g += nw) {
+      const int item = g - start[f];
+      const int e = item / sa.n_chunks, c = item - e * sa.n_chunks;
+      const double acc = pole ? witem<MODEL, float, true>(sa, &sa, S, kc, e, c, lane).item_sum()
+                              : witem<MODEL, float, false>(sa, &sa, S, kc, e, c, lane).item_sum();
+      if (lane == 0) sa.partial[item] = acc;
+    }
   }
 }
 
@@ -726,7 +820,8 @@ static int launch_batched_main(ffrg_ctx *ctx, const BatchList &bl, const int *fl
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
-  const int grid = std::max(1, std::min(total, per_sm * ctx->num_sms));
+  const int ctas = (total + kThreads / 32 - 1) / (kThreads / 32);
+  const int grid = std::max(1, std::min(ctas, per_sm * ctx->num_sms));
   const int per = (total + grid - 1) / grid;
   kern<<<(total + per - 1) / per, kThreads, smem, s>>>(bl.descs, flows, start, n, total, per);
   return FFRG_OK;
@@ -741,7 +836,8 @@ int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s) {
   if (!st) st = launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl, bl.ft_flows, bl.ft_start, bl.n_ft, bl.ft_items,
                                                          bl.smem_ft, s);
   if (st) return st;
-  batched_finalize_kernel<<<dim3((bl.max_ext + kThreads - 1) / kThreads, bl.n_flows), kThreads, 0, s>>>(bl.descs);
+  const int fin_blocks = (bl.max_ext + kThreads / 32 - 1) / (kThreads / 32);
+  batched_finalize_kernel<<<dim3(fin_blocks, bl.n_flows), kThreads, 0, s>>>(bl.descs);
   return set_cuda_error(ctx, cudaGetLastError(), "batched rhs launch");
 }
 

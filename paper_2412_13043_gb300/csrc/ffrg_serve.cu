@@ -55,7 +55,7 @@ struct SlotLayout {
   Plan pl;
   int ny, npsi;
   size_t bytes;
-  size_t o_tab, o_tab32, o_y, o_ys, o_K, o_raw, o_radF, o_radq, o_extp, o_psis, o_part;
+  size_t o_tab, o_tab32, o_y, o_ys, o_K, o_raw, o_radF, o_radF32, o_radq, o_radq32, o_kc, o_extp, o_psis, o_part;
   size_t o_rx, o_rw, o_a1x, o_a1w, o_a2x, o_a2w, o_psx, o_psw;
 };
 
@@ -75,16 +75,19 @@ static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotL
   const size_t d = sizeof(double);
   size_t u = 0;
   L.o_tab = seg(u, (size_t)pl.tab_count * d);
-  L.o_tab32 = seg(u, (size_t)pl.tab_count * sizeof(float2));
+  L.o_tab32 = seg(u, (size_t)pl.tab32_count * sizeof(float2));
   L.o_y = seg(u, (size_t)L.ny * d);
   L.o_ys = seg(u, (size_t)L.ny * d);
   L.o_K = seg(u, (size_t)7 * L.ny * d);
   L.o_raw = seg(u, (size_t)pl.n_ext * d);
   L.o_radF = seg(u, (size_t)pl.nr * (2 * pl.N + 1) * d);
   L.o_radq = seg(u, (size_t)pl.nr * d);
+  L.o_radq32 = seg(u, (size_t)pl.nr * sizeof(float));
+  L.o_radF32 = seg(u, (size_t)pl.nr * (2 * pl.N + 1) * sizeof(float));
+  L.o_kc = seg(u, kKConstBytes);
   L.o_extp = seg(u, (size_t)pl.n_ext_p * d);
   L.o_psis = seg(u, (size_t)L.npsi * d);
-  L.o_part = seg(u, (size_t)pl.n_items * d);
+  L.o_part = seg(u, (size_t)pl.fn_items * d);
   L.o_rx = seg(u, (size_t)pl.nr * d);
   L.o_rw = seg(u, (size_t)pl.nr * d);
   L.o_a1x = seg(u, (size_t)pl.na1 * d);
@@ -164,6 +167,9 @@ static int slot_setup(Server &S, int si) {
   pl.psi_w = (double *)(b + L.o_psw);
   pl.radF = (double *)(b + L.o_radF);
   pl.radq = (double *)(b + L.o_radq);
+  pl.radq32 = (float *)(b + L.o_radq32);
+  pl.radF32 = (float *)(b + L.o_radF32);
+  pl.kconst = b + L.o_kc;
   pl.ext_pd = (double *)(b + L.o_extp);
   pl.psi_s = (double *)(b + L.o_psis);
   pl.partial = (double *)(b + L.o_part);
@@ -222,8 +228,7 @@ static int slot_setup(Server &S, int si) {
 }
 
 static size_t smem32_of(const Plan &pl) {
-  auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
-  return al16((size_t)pl.tab_count * 8) + al16((size_t)pl.na1 * 3 * 4 + 2 * 4);
+  return pl.smem32;
 }
 
 // Upload the descriptors of the given slots as one compact launch set.
@@ -253,12 +258,12 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
                                                std::max(sl.L.pl.tab_count, sl.L.pl.n_ext_p)));
     if (sl.L.pl.model == FFRG_MODEL_D3) {
       d3f[n3++] = i;
-      it3 += sl.L.pl.n_items;
+      it3 += sl.L.pl.fn_items;
       d3s[n3] = it3;
       bl.smem_d3 = std::max(bl.smem_d3, smem32_of(sl.L.pl));
     } else {
       ftf[nf++] = i;
-      itf += sl.L.pl.n_items;
+      itf += sl.L.pl.fn_items;
       fts[nf] = itf;
       bl.smem_ft = std::max(bl.smem_ft, smem32_of(sl.L.pl));
     }
