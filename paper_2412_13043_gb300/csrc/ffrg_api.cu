@@ -356,6 +356,15 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.u_scale = 0.5 * (td->n_pts - 1) / lr;
   a.u_off = -(td->n_pts - 1) * log(td->x_min) / lr;
   a.x_min2 = td->x_min * td->x_min;
+  // k-independent parts of the table coordinates (the kernels add the k-dependent shift)
+  const double nm1 = td->n_pts - 1;
+  a.us1f = (float)(a.u_scale * 0.6931471805599453094 / nm1);
+  a.us1 = a.u_scale / nm1;
+  for (int c = 1; c <= 4; ++c) {
+    a.uoc[c - 1] = a.u_off - a.u_scale * log((double)c);
+    a.uoc1[c - 1] = a.uoc[c - 1] / nm1;
+  }
+  a.twopiT = 2.0 * kPi * pb->T;
   a.sum_w2 = pl->sum_w2;
   a.tab = tab;
   a.tab32 = pl->tab32;

@@ -48,6 +48,11 @@ struct RhsArgs {
   double qmax_over_k;
   double norm;                 // overall factor applied in finalize
   double u_scale, u_off;       // u = u_scale ln(s^2) + u_off
+  double uoc[4];               // u_off - u_scale ln c, c = 1..4 (coordinate of S0^2 = sum of c squares / c)
+  float us1f;                  // FP32 coordinate: u_scale ln 2 / (n_pts - 1) (multiplies log2)
+  double uoc1[4];              // uoc[c-1] / (n_pts - 1)
+  double us1;                  // u_scale / (n_pts - 1)
+  double twopiT;               // 2 pi T
   double x_min2;               // x_min^2 (lookups below x_min return the first node)
   double sum_w2;               // sum of the second-angle weights (D4)
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
@@ -94,6 +99,28 @@ __device__ __forceinline__ double reg_rdot(int reg, double x) {
   return 2.0 * x * x * exp(-x) / (em * em);
 }
 
+// Both shapes from one exponential: with em = e^{-x} - 1 (expm1, exact near 0),
+// r = x e^{-x} / (1 - e^{-x}) = x/(e^x - 1) and rdot = 2 x^2 e^{-x}/(1 - e^{-x})^2.
+__device__ __forceinline__ void reg_r_rdot(int reg, double x, double &r, double &rdot) {
+  if (reg == FFRG_REG_LITIM) {
+    r = x < 1.0 ? 1.0 - x : 0.0;
+    rdot = x < 1.0 ? 2.0 : 0.0;
+    return;
+  }
+  if (x > 700.0) {
+    r = rdot = 0.0;
+    return;
+  }
+  if (x < 1e-100) {
+    r = 1.0;
+    rdot = 2.0;
+    return;
+  }
+  const double em = expm1(-x), inv = 1.0 / em, e = em + 1.0;
+  r = -x * e * inv;
+  rdot = 2.0 * x * x * e * inv * inv;
+}
+
 // Hardware special-function instructions (PTX ISA: lg2/ex2/rcp .approx.ftz.f32).
 __device__ __forceinline__ float hw_lg2(float x) {
   float y;
@@ -125,8 +152,8 @@ __device__ __forceinline__ void lerp_pos(double s2, double u_scale, double u_off
 }
 
 // FP32 coordinate, normalised: u1 = u / (n-1) = sat(u_scale1 log2(s^2) + u_off1)
-// in one saturating FMA (the caller passes u_scale ln 2 / (n-1) and
-// u_off / (n-1), see lerp_scale / lerp_off).  s^2 <= 0 gives log2 = -inf or
+// in one saturating FMA (the caller passes u_scale ln 2 / (n-1) and the
+// offset divided by n-1).  s^2 <= 0 gives log2 = -inf or
 // NaN, both saturated to 0 (the first node, as for s < x_min).  floor(u) comes
 // from u1 (n-1) + 1.5*2^23 rounded towards -inf: the low mantissa bits of the
 // sum hold floor(u), so no float<->int conversion is needed.  At u = n-1 this
@@ -139,25 +166,6 @@ __device__ __forceinline__ void lerp_pos(float s2, float u_scale1, float u_off1,
   const float t = __fmaf_rd(u1, nm1, magic);
   i0 = __float_as_int(t) - 0x4B400000;
   w = fmaf(u1, nm1, magic - t);
-}
-
-// Scale and offset of the table coordinate for each precision: ln(s^2) and
-// u_off for FP64; log2(s^2) (factor ln 2 folded in) divided by n-1 for FP32.
-template <typename T>
-__device__ __forceinline__ T lerp_scale(double u_scale, int n);
-template <>
-__device__ __forceinline__ double lerp_scale<double>(double u_scale, int) { return u_scale; }
-template <>
-__device__ __forceinline__ float lerp_scale<float>(double u_scale, int n) {
-  return (float)(u_scale * 0.6931471805599453094 / (double)(n - 1));
-}
-template <typename T>
-__device__ __forceinline__ T lerp_off(double u_off, int n);
-template <>
-__device__ __forceinline__ double lerp_off<double>(double u_off, int) { return u_off; }
-template <>
-__device__ __forceinline__ float lerp_off<float>(double u_off, int n) {
-  return (float)(u_off / (double)(n - 1));
 }
 
 // FP32 lookup on node pairs: one 8-byte shared load and one FMA
@@ -365,10 +373,12 @@ struct BatchList {
   const RhsArgs *descs;          // [n_flows], device
   int n_flows;
   const int *d3_flows, *d3_start;  // device: indices into descs, cumulative items (n_d3 + 1)
+  const long long *d3_cost;        // device: cumulative estimated cost at the flow boundaries (n_d3 + 1)
   int n_d3, d3_items;
   const int *ft_flows, *ft_start;
+  const long long *ft_cost;
   int n_ft, ft_items;
-  int max_ext, max_pre;          // largest n_ext and precompute range among the flows
+  int max_ext, max_pre;          // largest n_ext and precompute block count among the flows
   size_t smem_d3, smem_ft;       // largest shared-memory need per model (FP32 path)
 };
 int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s);
@@ -410,6 +420,8 @@ int host_gauss_chebyshev2(int n, double *x, double *w);
 // kernels launched from several translation units (ffrg_rhs.cu)
 int launch_rhs(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s);
 int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s);
+// blocks of the precompute kernel for one RHS (at most cap)
+int precompute_blocks(const RhsArgs &a, int cap);
 int launch_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, const double *tab, double k,
                     double *J, cudaStream_t s);
 

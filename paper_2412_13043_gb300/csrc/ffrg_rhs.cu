@@ -104,27 +104,53 @@ struct KConstPair {
 };
 static_assert(sizeof(KConstPair) <= kKConstBytes, "constant block too small");
 
+// The k-dependent constants from the scale k (a division and one log; the
+// k-independent parts of the coordinates come from the host): FP64 work is
+// slow on this part, and these run once per RHS on one thread.  The FP32
+// coordinate offsets are formed in FP64 and rounded once (an error of a few
+// FP32 ulps there would move lookups by ~1e-5 of a node).
 template <typename T>
-__device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a) {
+__device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a);
+template <>
+__device__ __forceinline__ KConst<float> make_kconst<float>(const RhsArgs &a) {
+  const double kd = scale_k(a), k2d = kd * kd, inv_k2d = 1.0 / k2d;
+  KConst<float> c;
+  c.k2 = (float)k2d;
+  c.inv_k2 = (float)inv_k2d;
+  c.m2 = (float)mass2(a, kd);
+  c.plim = -2.0f * c.m2;
+  c.us = a.us1f;
+  c.uo = (float)a.uoc1[0];
+  c.sy = (float)(1.4426950408889634074 * inv_k2d);
+  c.som = c.sy;  // 1/(k^2 ln 2) = log2(e)/k^2
+  // coordinates taken in y = sy s^2: shift by -u_scale ln(sy) / (n-1)
+  const double lnsy = 0.36651292058166432701 - log(k2d);  // ln(log2 e) - ln k^2
+  c.uy1 = (float)(a.uoc1[0] - a.us1 * lnsy);
+  c.uy2 = (float)(a.uoc1[1] - a.us1 * lnsy);
+  c.uy3 = (float)(a.uoc1[2] - a.us1 * lnsy);
+  c.uy4 = (float)(a.uoc1[3] - a.us1 * lnsy);
+  c.twopiT = (float)a.twopiT;
+  c.sw2 = (float)a.sum_w2;
+  return c;
+}
+template <>
+__device__ __forceinline__ KConst<double> make_kconst<double>(const RhsArgs &a) {
   const double kd = scale_k(a), m2d = mass2(a, kd);
-  KConst<T> c;
-  c.k2 = (T)(kd * kd);
-  c.inv_k2 = (T)(1.0 / (kd * kd));
-  c.m2 = (T)m2d;
-  c.us = lerp_scale<T>(a.u_scale, a.n_pts);
-  c.uo = lerp_off<T>(a.u_off, a.n_pts);
-  c.plim = (T)(-2.0 * m2d);
-  const bool f32 = sizeof(T) == 4;
-  c.sy = (T)(f32 ? 1.4426950408889634074 / (kd * kd) : 1.0);
-  c.som = (T)(f32 ? 1.0 / (kd * kd * 0.6931471805599453094) : 1.0);
-  const double lnsy = f32 ? log(1.4426950408889634074 / (kd * kd)) : 0.0;
-  // S0^2 = (sum of squares)/c: the 1/c is a shift of the coordinate, -u_scale ln c
-  c.uy1 = lerp_off<T>(a.u_off - a.u_scale * lnsy, a.n_pts);
-  c.uy2 = lerp_off<T>(a.u_off - a.u_scale * (0.69314718055994530942 + lnsy), a.n_pts);
-  c.uy3 = lerp_off<T>(a.u_off - a.u_scale * (1.09861228866810969140 + lnsy), a.n_pts);
-  c.uy4 = lerp_off<T>(a.u_off - a.u_scale * (1.38629436111989061883 + lnsy), a.n_pts);
-  c.twopiT = (T)(2.0 * kPi * a.T);
-  c.sw2 = (T)a.sum_w2;
+  KConst<double> c;
+  c.k2 = kd * kd;
+  c.inv_k2 = 1.0 / c.k2;
+  c.m2 = m2d;
+  c.plim = -2.0 * m2d;
+  c.us = a.u_scale;
+  c.uo = a.u_off;
+  c.sy = 1.0;
+  c.som = 1.0;
+  c.uy1 = a.uoc[0];
+  c.uy2 = a.uoc[1];
+  c.uy3 = a.uoc[2];
+  c.uy4 = a.uoc[3];
+  c.twopiT = a.twopiT;
+  c.sw2 = a.sum_w2;
   return c;
 }
 
@@ -176,9 +202,11 @@ __device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double y,
 template <bool POLE = true, typename Pole>
 __device__ __forceinline__ float inv_prop(const RhsArgs &a, float Zs, float y, float om2s, const KConst<float> &kc,
                                           Pole &&pole) {
-  const float P = Zs * (reg_g(a.reg, y) + om2s);
-  if (POLE && P < kc.plim) return pole();
-  return hw_rcp(P + kc.m2);
+  // the denominator is one explicit FMA in both variants, so that kernels with
+  // and without the test (serving, single flow) round it identically
+  const float t = reg_g(a.reg, y) + om2s;
+  if (POLE && Zs * t < kc.plim) return pole();
+  return hw_rcp(fmaf(Zs, t, kc.m2));
 }
 
 // resident CTAs per SM requested from the compiler: the FP32 kernels are held
@@ -197,52 +225,85 @@ struct MinBlocks<float> {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool skipped(const RhsArgs &a) { return a.skip && *(volatile const int *)a.skip; }
 
-__device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int stride) {
+// blocks of the per-radial precompute: radial nodes x values of |n|
+constexpr int kPreR = 64, kPreN = 8;
+
+// Every thread of a block of the calling grid (blockIdx.x over the grid,
+// blockDim.x threads) must run it: it synchronises the block.
+__device__ __forceinline__ void precompute_body(const RhsArgs &a) {
+  const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
+  const double L = a.qmax_over_k * k;
+  // The scalar and flat work starts at the first block without per-radial
+  // work (blocks 0 .. n_rt n_nb - 1 have some), so that no block has both.
+  const int n_phase = ((a.nr + kPreR - 1) / kPreR) * (a.N / kPreN + 1);
+  const int first_free = n_phase % gridDim.x;
+  const int stride = gridDim.x * blockDim.x;
+  const int tid0 = ((blockIdx.x + gridDim.x - first_free) % gridDim.x) * blockDim.x + threadIdx.x;
   // the main kernel runs after this one (stream order)
   if (tid0 == 0 && a.work_ctr) *a.work_ctr = 0u;
-  if (a.kconst && tid0 < 2) {
+  if (a.kconst && (tid0 == 0 || tid0 == 32)) {  // two warps, in parallel
     KConstPair *kp = (KConstPair *)a.kconst;
     if (tid0 == 0) kp->f = make_kconst<float>(a);
     else kp->d = make_kconst<double>(a);
   }
-  const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
-  const double L = a.qmax_over_k * k;
-  const int total = (2 * a.N + 1) * a.nr;
-  for (int idx = tid0; idx < total; idx += stride) {
-    int n = idx / a.nr - a.N, r = idx % a.nr;
-    double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q;
-    if (n == -a.N) {
-      a.radq[r] = q;
-      if (a.radq32) a.radq32[r] = (float)q;
-    }
-    double F;
-    if (a.model == FFRG_MODEL_FINITE_T) {
-      int row = min(abs(n), a.n_stack - 1);
-      const double *zr = a.tab + (size_t)row * a.n_pts;
-      const double *lr = a.tab + ((size_t)a.n_stack + row) * a.n_pts;
-      int i0;
-      double wl;
-      lerp_pos(q2, a.u_scale, a.u_off, a.n_pts, i0, wl);
-      double Z = lerp_at(zr, i0, wl), Lq = lerp_at(lr, i0, wl);
-      double om = 2.0 * kPi * a.T * n;
-      double G = 1.0 / prop_den(a.reg, Z, om * om, q2, m2, k2, inv_k2);
-      double dR = Z * k2 * reg_rdot(a.reg, q2 * inv_k2);
-      F = w * q2 * dR * G * G * Lq;
-    } else {
-      double Z = lerp(a.tab, q2, a.u_scale, a.u_off, a.n_pts);
-      double G = 1.0 / prop_den(a.reg, Z, 0.0, q2, m2, k2, inv_k2);
-      double rd = k2 * reg_rdot(a.reg, q2 * inv_k2);
-      double dR = Z * rd;
-      double meas = (a.model == FFRG_MODEL_D4_VERTEX) ? q2 * q : q2;
-      F = w * meas * dR * G * G;
-      if (a.radD) {
-        // d F / d Z(q): dR = Z k^2 rdot, G = 1/(Z P + m^2) with P = q^2 + k^2 r
-        double P = q2 + k2 * reg_r(a.reg, q2 * inv_k2);
-        a.radD[idx] = w * meas * rd * G * G * (1.0 - 2.0 * Z * G * P);
+  // Per-radial factors F(n, r), in blocks of kPreR radial nodes x kPreN values
+  // of |n|.  Phase A: the n-independent part of each node (q^2, weight x
+  // measure, k^2 r(x), k^2 rdot(x), the table position of q^2) once per block
+  // into shared memory.  Phase B: F for n >= 0, written to n and -n (the
+  // tables are indexed by |n| and omega_n^2 is even in n).
+  const int nr = a.nr, N = a.N;
+  const int n_rt = (nr + kPreR - 1) / kPreR, n_nb = N / kPreN + 1;
+  __shared__ double s_q2[kPreR], s_wm[kPreR], s_kr[kPreR], s_rd[kPreR], s_wl[kPreR];
+  __shared__ int s_i0[kPreR];
+  for (int pb = blockIdx.x; pb < n_rt * n_nb; pb += gridDim.x) {
+    const int rt = pb % n_rt, nb = pb / n_rt;
+    const int r0 = rt * kPreR, rn = min(kPreR, nr - r0);
+    __syncthreads();  // the previous block's shared values are no longer read
+    for (int i = threadIdx.x; i < rn; i += blockDim.x) {
+      const int r = r0 + i;
+      const double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q, x = q2 * inv_k2;
+      s_q2[i] = q2;
+      s_wm[i] = w * ((a.model == FFRG_MODEL_D4_VERTEX) ? q2 * q : q2);
+      double rx, rdx;
+      reg_r_rdot(a.reg, x, rx, rdx);
+      s_kr[i] = k2 * rx;
+      s_rd[i] = k2 * rdx;
+      lerp_pos(q2, a.u_scale, a.u_off, a.n_pts, s_i0[i], s_wl[i]);
+      if (nb == 0) {
+        a.radq[r] = q;
+        if (a.radq32) a.radq32[r] = (float)q;
       }
     }
-    a.radF[idx] = F;
-    if (a.radF32) a.radF32[idx] = (float)F;
+    __syncthreads();
+    const int n0 = nb * kPreN, n1 = min(n0 + kPreN, N + 1);
+    for (int j = threadIdx.x; j < (n1 - n0) * rn; j += blockDim.x) {
+      const int n = n0 + j / rn, i = j - (j / rn) * rn, r = r0 + i;
+      const double q2 = s_q2[i], wl = s_wl[i], rd = s_rd[i];
+      const int i0 = s_i0[i];
+      double F;
+      if (a.model == FFRG_MODEL_FINITE_T) {
+        const int row = min(n, a.n_stack - 1);
+        const double Z = lerp_at(a.tab + (size_t)row * a.n_pts, i0, wl);
+        const double Lq = lerp_at(a.tab + ((size_t)a.n_stack + row) * a.n_pts, i0, wl);
+        const double om = 2.0 * kPi * a.T * n;
+        const double G = 1.0 / (Z * (om * om + q2 + s_kr[i]) + m2);
+        F = s_wm[i] * (Z * rd) * G * G * Lq;
+      } else {
+        const double Z = lerp_at(a.tab, i0, wl);
+        const double P = q2 + s_kr[i];
+        const double G = 1.0 / (Z * P + m2);
+        F = s_wm[i] * (Z * rd) * G * G;
+        // d F / d Z(q): dR = Z k^2 rdot, G = 1/(Z P + m^2) with P = q^2 + k^2 r
+        if (a.radD) a.radD[r] = s_wm[i] * rd * G * G * (1.0 - 2.0 * Z * G * P);
+      }
+      const int ip = (N + n) * nr + r, im = (N - n) * nr + r;
+      a.radF[ip] = F;
+      a.radF[im] = F;
+      if (a.radF32) {
+        a.radF32[ip] = (float)F;
+        a.radF32[im] = (float)F;
+      }
+    }
   }
   // FP32 tables; the Z table (table 0, every stack row) carries the factor
   // k^2 ln 2 of the FP32 propagator form.  d=3, d=4: (value, difference to
@@ -276,7 +337,7 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a, int tid0, int 
 
 __global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
   if (skipped(a)) return;
-  precompute_body(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  precompute_body(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -693,10 +754,15 @@ static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int 
   return FFRG_OK;
 }
 
+int precompute_blocks(const RhsArgs &a, int cap) {
+  const int n_rt = (a.nr + kPreR - 1) / kPreR, n_nb = a.N / kPreN + 1;
+  const int flat = std::max(std::max(a.tab_count, a.n_ext), a.n_ext_p);
+  // blocks with per-radial work, then blocks for the scalar and flat work
+  return std::max(1, std::min(n_rt * n_nb + (flat + kThreads - 1) / kThreads, cap));
+}
+
 int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s) {
-  const int pre_total = std::max((2 * a.N + 1) * a.nr, a.tab_count);
-  const int pre_blocks = std::min((pre_total + kThreads - 1) / kThreads, 4 * ctx->num_sms);
-  precompute_kernel<<<pre_blocks, kThreads, 0, s>>>(a);
+  precompute_kernel<<<precompute_blocks(a, 4 * ctx->num_sms), kThreads, 0, s>>>(a);
   return set_cuda_error(ctx, cudaGetLastError(), "precompute launch");
 }
 
@@ -729,9 +795,7 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
     st = persistent_grid(ctx, kern, smem, a.n_items, &grid);
     if (st) return st;
   }
-  const int pre_total = std::max((2 * a.N + 1) * a.nr, a.tab_count);
-  const int pre_blocks = std::min((pre_total + kThreads - 1) / kThreads, 4 * ctx->num_sms);
-  precompute_kernel<<<pre_blocks, kThreads, 0, s>>>(a);
+  precompute_kernel<<<precompute_blocks(a, 4 * ctx->num_sms), kThreads, 0, s>>>(a);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   const bool prof = ctx->profiling && cap == cudaStreamCaptureStatusNone &&
@@ -757,7 +821,7 @@ namespace ffrg {
 __global__ void __launch_bounds__(kThreads) batched_precompute_kernel(const RhsArgs *descs) {
   const RhsArgs &a = descs[blockIdx.y];
   if (skipped(a)) return;
-  precompute_body(a, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  precompute_body(a);
 }
 
 // one warp per external point of flow blockIdx.y
@@ -770,18 +834,32 @@ __global__ void batched_finalize_kernel(const RhsArgs *descs) {
   if (lane == 0) write_output(a, e, t);
 }
 
-// Each CTA walks a contiguous range of the combined item list, one flow
-// segment at a time: it copies the flow's descriptor, FP32 tables and angle
-// rules into shared memory (plain loads), then its warps take the segment's
-// warp-sized items in turn.
+// Each CTA takes a contiguous range of the combined item list holding an
+// equal share of the estimated cost (cost[f] is cumulative at the flow
+// boundaries, uniform per item within a flow), so that flows with longer
+// rows do not leave other CTAs idle.  For each flow segment of its range the
+// CTA copies the flow's descriptor, FP32 tables and angle rules into shared
+// memory (plain loads); its warps then take the segment's warp-sized items.
+__device__ __forceinline__ int item_at_cost(const int *start, const long long *cost, int n_fl, long long x) {
+  int f = 0;
+  while (f + 1 < n_fl && cost[f + 1] <= x) ++f;
+  const int items = start[f + 1] - start[f];
+  const long long w = cost[f + 1] - cost[f];
+  if (w <= 0) return start[f];
+  return start[f] + (int)min((long long)items, (x - cost[f]) * items / w);
+}
+
 template <int MODEL>
 __global__ void __launch_bounds__(kThreads, 4)
-    batched_main_kernel(const RhsArgs *descs, const int *flows, const int *start, int n_fl, int total, int per) {
+    batched_main_kernel(const RhsArgs *descs, const int *flows, const int *start, const long long *cost, int n_fl) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ RhsArgs sa;
   __shared__ int skip;
-  const int g0 = blockIdx.x * per, g1 = min(g0 + per, total);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long W = cost[n_fl];
+  const int g0 = blockIdx.x == 0 ? 0 : item_at_cost(start, cost, n_fl, W * blockIdx.x / gridDim.x);
+  const int g1 = blockIdx.x + 1 == gridDim.x ? start[n_fl]
+                                             : item_at_cost(start, cost, n_fl, W * (blockIdx.x + 1) / gridDim.x);
   int f = 0;
   while (f < n_fl && start[f + 1] <= g0) ++f;
   for (; f < n_fl && start[f] < g1; ++f) {
@@ -811,10 +889,10 @@ __global__ void __launch_bounds__(kThreads, 4)
 }
 
 template <int MODEL>
-static int launch_batched_main(ffrg_ctx *ctx, const BatchList &bl, const int *flows, const int *start, int n,
-                               int total, size_t smem, cudaStream_t s) {
+static int launch_batched_main(ffrg_ctx *ctx, const BatchList &bl, const int *flows, const int *start,
+                               const long long *cost, int n, int total, size_t smem, cudaStream_t s) {
   if (n == 0 || total == 0) return FFRG_OK;
-  void (*kern)(const RhsArgs *, const int *, const int *, int, int, int) = batched_main_kernel<MODEL>;
+  void (*kern)(const RhsArgs *, const int *, const int *, const long long *, int) = batched_main_kernel<MODEL>;
   int st = ensure_smem_limit(ctx, (const void *)kern, smem);
   if (st) return st;
   int per_sm = 0;
@@ -822,19 +900,18 @@ static int launch_batched_main(ffrg_ctx *ctx, const BatchList &bl, const int *fl
   if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
   const int ctas = (total + kThreads / 32 - 1) / (kThreads / 32);
   const int grid = std::max(1, std::min(ctas, per_sm * ctx->num_sms));
-  const int per = (total + grid - 1) / grid;
-  kern<<<(total + per - 1) / per, kThreads, smem, s>>>(bl.descs, flows, start, n, total, per);
+  kern<<<grid, kThreads, smem, s>>>(bl.descs, flows, start, cost, n);
   return FFRG_OK;
 }
 
 int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s) {
   if (bl.n_flows == 0) return FFRG_OK;
-  const int pre_blocks = std::max(1, std::min((bl.max_pre + kThreads - 1) / kThreads, 64));
-  batched_precompute_kernel<<<dim3(pre_blocks, bl.n_flows), kThreads, 0, s>>>(bl.descs);
-  int st = launch_batched_main<FFRG_MODEL_D3>(ctx, bl, bl.d3_flows, bl.d3_start, bl.n_d3, bl.d3_items,
+  batched_precompute_kernel<<<dim3(std::max(1, bl.max_pre), bl.n_flows), kThreads, 0, s>>>(bl.descs);
+  int st = launch_batched_main<FFRG_MODEL_D3>(ctx, bl, bl.d3_flows, bl.d3_start, bl.d3_cost, bl.n_d3, bl.d3_items,
                                               bl.smem_d3, s);
-  if (!st) st = launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl, bl.ft_flows, bl.ft_start, bl.n_ft, bl.ft_items,
-                                                         bl.smem_ft, s);
+  if (!st)
+    st = launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl, bl.ft_flows, bl.ft_start, bl.ft_cost, bl.n_ft,
+                                                  bl.ft_items, bl.smem_ft, s);
   if (st) return st;
   const int fin_blocks = (bl.max_ext + kThreads / 32 - 1) / (kThreads / 32);
   batched_finalize_kernel<<<dim3(fin_blocks, bl.n_flows), kThreads, 0, s>>>(bl.descs);

@@ -231,6 +231,15 @@ static size_t smem32_of(const Plan &pl) {
   return pl.smem32;
 }
 
+// Launch set layout: descs | fa | lists (5 cap + 2 ints, padded to an even
+// count so that what follows is 8-byte aligned) | cost prefixes (2 (cap + 1)
+// long longs).
+static int list_ints(int cap) { return (5 * cap + 3) & ~1; }
+static size_t set_bytes_of(int cap) {
+  return (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap + sizeof(int) * list_ints(cap) +
+         sizeof(long long) * 2 * (cap + 1);
+}
+
 // Upload the descriptors of the given slots as one compact launch set.
 static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
   const int n = (int)ids.size(), cap = (int)S.slots.size();
@@ -244,9 +253,12 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
   FlowArgs *hf = (FlowArgs *)(S.stage_host + sizeof(RhsArgs) * cap);
   int *hl = (int *)(S.stage_host + (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap);
   int *d3f = hl + cap, *d3s = d3f + cap, *ftf = d3s + cap + 1, *fts = ftf + cap;
+  long long *d3c = (long long *)(hl + list_ints(cap)), *ftc = d3c + cap + 1;
   int n3 = 0, nf = 0, it3 = 0, itf = 0;
   d3s[0] = 0;
   fts[0] = 0;
+  d3c[0] = 0;
+  ftc[0] = 0;
   for (int i = 0; i < n; ++i) {
     const Slot &sl = S.slots[ids[i]];
     hd[i] = sl.ra;
@@ -254,22 +266,24 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
     hl[i] = ids[i];
     ls.max_ny = std::max(ls.max_ny, sl.L.ny);
     bl.max_ext = std::max(bl.max_ext, sl.L.pl.n_ext);
-    bl.max_pre = std::max(bl.max_pre, std::max((2 * sl.L.pl.N + 1) * sl.L.pl.nr,
-                                               std::max(sl.L.pl.tab_count, sl.L.pl.n_ext_p)));
+    bl.max_pre = std::max(bl.max_pre, precompute_blocks(sl.ra, 64));
+    // estimated cost of one item: rows x (angle nodes per row + per-row work)
+    const long long cost = (long long)sl.L.pl.fn_items * sl.L.pl.fcr * (sl.L.pl.fjb + 1);
     if (sl.L.pl.model == FFRG_MODEL_D3) {
       d3f[n3++] = i;
       it3 += sl.L.pl.fn_items;
       d3s[n3] = it3;
+      d3c[n3] = d3c[n3 - 1] + cost;
       bl.smem_d3 = std::max(bl.smem_d3, smem32_of(sl.L.pl));
     } else {
       ftf[nf++] = i;
       itf += sl.L.pl.fn_items;
       fts[nf] = itf;
+      ftc[nf] = ftc[nf - 1] + cost;
       bl.smem_ft = std::max(bl.smem_ft, smem32_of(sl.L.pl));
     }
   }
-  const size_t bytes = (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap + sizeof(int) * (5 * cap + 2);
-  cudaError_t e = cudaMemcpyAsync(ls.descs, S.stage_host, bytes, cudaMemcpyHostToDevice, S.st);
+  cudaError_t e = cudaMemcpyAsync(ls.descs, S.stage_host, set_bytes_of(cap), cudaMemcpyHostToDevice, S.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);  // the staging buffer is reused
   if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve descriptor upload");
   int *dl = ls.lists;
@@ -283,6 +297,8 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
   bl.ft_start = dl + 4 * cap + 1;
   bl.n_ft = nf;
   bl.ft_items = itf;
+  bl.d3_cost = (const long long *)(dl + list_ints(cap));
+  bl.ft_cost = bl.d3_cost + cap + 1;
   return FFRG_OK;
 }
 
@@ -495,7 +511,7 @@ extern "C" int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts) {
   S->lc.prof_used = 0;
   const int cap = opts->max_slots;
   S->slots.resize(cap);
-  const size_t set_bytes = (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap + sizeof(int) * (5 * cap + 2);
+  const size_t set_bytes = set_bytes_of(cap);
   S->stage_bytes = set_bytes;
   cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc((void **)&S->ctl_dev, sizeof(FlowCtl) * cap);
