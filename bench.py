@@ -427,7 +427,7 @@ def main():
     roofline = {"bound": "alu", "pipe": "MUFU (special-function unit)", "achieved": achieved / 1e12,
                 "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": achieved / sfu_peak, "traffic": None,
                 "peak_source": f"{SFU_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock of measured)",
-                "kernel": "d4_main<float>", "kernel_ms": kern_s * 1e3, "ops_per_launch": sfu_ops,
+                "kernel": "rhs_main<2, float>", "kernel_ms": kern_s * 1e3, "ops_per_launch": sfu_ops,
                 "kernel_share_of_step": (main_ms / max(1, launches)) / (sum(step_ms) / K)}
 
     # ---------------- full flows (d=3 two-point flow k: 10 -> 0.01) ----------------
