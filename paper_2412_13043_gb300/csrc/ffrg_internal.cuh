@@ -369,18 +369,27 @@ int ensure_smem_limit(ffrg_ctx *ctx, const void *func, size_t bytes);
 // Several flows' RHS in one set of launches (serving).  Descriptors live in
 // device memory; work items of the flows of one model are numbered
 // consecutively (flow f owns items start[f] .. start[f+1]-1).
+// Flows of one model whose shared-memory need allows the same number of
+// resident CTAs per SM run in one main-kernel launch (a flow with large
+// tables would otherwise set the occupancy of all).
+struct BatchGroup {
+  int model;
+  const int *flows, *start;  // device: indices into descs, cumulative items (n + 1)
+  const long long *cost;     // device: cumulative estimated cost at the flow boundaries (n + 1)
+  int n, items;
+  size_t smem;               // largest shared-memory need in the group (FP32 path)
+};
+constexpr int kMaxBatchGroups = 8;  // 2 models x 4 occupancy classes
+
 struct BatchList {
   const RhsArgs *descs;          // [n_flows], device
   int n_flows;
-  const int *d3_flows, *d3_start;  // device: indices into descs, cumulative items (n_d3 + 1)
-  const long long *d3_cost;        // device: cumulative estimated cost at the flow boundaries (n_d3 + 1)
-  int n_d3, d3_items;
-  const int *ft_flows, *ft_start;
-  const long long *ft_cost;
-  int n_ft, ft_items;
+  BatchGroup groups[kMaxBatchGroups];
+  int n_groups;
   int max_ext, max_pre;          // largest n_ext and precompute block count among the flows
-  size_t smem_d3, smem_ft;       // largest shared-memory need per model (FP32 path)
 };
+// resident CTAs per SM of the serving main kernel of `model` with `smem` bytes
+int batched_ctas_per_sm(ffrg_ctx *ctx, int model, size_t smem);
 int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s);
 
 // Device control block and argument block of one DP5(4) flow.

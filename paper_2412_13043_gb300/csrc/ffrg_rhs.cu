@@ -889,29 +889,43 @@ __global__ void __launch_bounds__(kThreads, 4)
 }
 
 template <int MODEL>
-static int launch_batched_main(ffrg_ctx *ctx, const BatchList &bl, const int *flows, const int *start,
-                               const long long *cost, int n, int total, size_t smem, cudaStream_t s) {
-  if (n == 0 || total == 0) return FFRG_OK;
+static int batched_occupancy(ffrg_ctx *ctx, size_t smem, int *per_sm) {
   void (*kern)(const RhsArgs *, const int *, const int *, const long long *, int) = batched_main_kernel<MODEL>;
   int st = ensure_smem_limit(ctx, (const void *)kern, smem);
   if (st) return st;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess || *per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
+  return FFRG_OK;
+}
+
+int batched_ctas_per_sm(ffrg_ctx *ctx, int model, size_t smem) {
+  int per_sm = 1;
+  const int st = model == FFRG_MODEL_D3 ? batched_occupancy<FFRG_MODEL_D3>(ctx, smem, &per_sm)
+                                        : batched_occupancy<FFRG_MODEL_FINITE_T>(ctx, smem, &per_sm);
+  return st ? 1 : per_sm;
+}
+
+template <int MODEL>
+static int launch_batched_main(ffrg_ctx *ctx, const RhsArgs *descs, const BatchGroup &G, cudaStream_t s) {
+  if (G.n == 0 || G.items == 0) return FFRG_OK;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
-  const int ctas = (total + kThreads / 32 - 1) / (kThreads / 32);
+  int st = batched_occupancy<MODEL>(ctx, G.smem, &per_sm);
+  if (st) return st;
+  const int ctas = (G.items + kThreads / 32 - 1) / (kThreads / 32);
   const int grid = std::max(1, std::min(ctas, per_sm * ctx->num_sms));
-  kern<<<grid, kThreads, smem, s>>>(bl.descs, flows, start, cost, n);
+  batched_main_kernel<MODEL><<<grid, kThreads, G.smem, s>>>(descs, G.flows, G.start, G.cost, G.n);
   return FFRG_OK;
 }
 
 int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s) {
   if (bl.n_flows == 0) return FFRG_OK;
   batched_precompute_kernel<<<dim3(std::max(1, bl.max_pre), bl.n_flows), kThreads, 0, s>>>(bl.descs);
-  int st = launch_batched_main<FFRG_MODEL_D3>(ctx, bl, bl.d3_flows, bl.d3_start, bl.d3_cost, bl.n_d3, bl.d3_items,
-                                              bl.smem_d3, s);
-  if (!st)
-    st = launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl, bl.ft_flows, bl.ft_start, bl.ft_cost, bl.n_ft,
-                                                  bl.ft_items, bl.smem_ft, s);
+  int st = FFRG_OK;
+  for (int g = 0; g < bl.n_groups && !st; ++g) {
+    const BatchGroup &G = bl.groups[g];
+    st = G.model == FFRG_MODEL_D3 ? launch_batched_main<FFRG_MODEL_D3>(ctx, bl.descs, G, s)
+                                  : launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl.descs, G, s);
+  }
   if (st) return st;
   const int fin_blocks = (bl.max_ext + kThreads / 32 - 1) / (kThreads / 32);
   batched_finalize_kernel<<<dim3(fin_blocks, bl.n_flows), kThreads, 0, s>>>(bl.descs);

@@ -231,13 +231,13 @@ static size_t smem32_of(const Plan &pl) {
   return pl.smem32;
 }
 
-// Launch set layout: descs | fa | lists (5 cap + 2 ints, padded to an even
-// count so that what follows is 8-byte aligned) | cost prefixes (2 (cap + 1)
-// long longs).
-static int list_ints(int cap) { return (5 * cap + 3) & ~1; }
+// Launch set layout: descs | fa | lists (cap ints: all flows, then per group
+// cap flow indices and cap + 1 item offsets; padded to an even count so that
+// what follows is 8-byte aligned) | per group cap + 1 cost prefixes.
+static int list_ints(int cap) { return (cap + kMaxBatchGroups * (2 * cap + 1) + 1) & ~1; }
 static size_t set_bytes_of(int cap) {
   return (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap + sizeof(int) * list_ints(cap) +
-         sizeof(long long) * 2 * (cap + 1);
+         sizeof(long long) * kMaxBatchGroups * (cap + 1);
 }
 
 // Upload the descriptors of the given slots as one compact launch set.
@@ -248,17 +248,20 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
   BatchList &bl = ls.bl;
   bl = BatchList();
   if (n == 0) return FFRG_OK;
-  // host staging: descs | fa | lists
+  // host staging: descs | fa | lists | costs
   RhsArgs *hd = (RhsArgs *)S.stage_host;
   FlowArgs *hf = (FlowArgs *)(S.stage_host + sizeof(RhsArgs) * cap);
   int *hl = (int *)(S.stage_host + (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap);
-  int *d3f = hl + cap, *d3s = d3f + cap, *ftf = d3s + cap + 1, *fts = ftf + cap;
-  long long *d3c = (long long *)(hl + list_ints(cap)), *ftc = d3c + cap + 1;
-  int n3 = 0, nf = 0, it3 = 0, itf = 0;
-  d3s[0] = 0;
-  fts[0] = 0;
-  d3c[0] = 0;
-  ftc[0] = 0;
+  long long *hc = (long long *)(hl + list_ints(cap));
+  int gn[kMaxBatchGroups] = {}, gitems[kMaxBatchGroups] = {};
+  size_t gsmem[kMaxBatchGroups] = {};
+  auto gflows = [&](int g) { return hl + cap + g * (2 * cap + 1); };
+  auto gstart = [&](int g) { return gflows(g) + cap; };
+  auto gcost = [&](int g) { return hc + (size_t)g * (cap + 1); };
+  for (int g = 0; g < kMaxBatchGroups; ++g) {
+    gstart(g)[0] = 0;
+    gcost(g)[0] = 0;
+  }
   for (int i = 0; i < n; ++i) {
     const Slot &sl = S.slots[ids[i]];
     hd[i] = sl.ra;
@@ -267,38 +270,36 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
     ls.max_ny = std::max(ls.max_ny, sl.L.ny);
     bl.max_ext = std::max(bl.max_ext, sl.L.pl.n_ext);
     bl.max_pre = std::max(bl.max_pre, precompute_blocks(sl.ra, 64));
+    const size_t smem = smem32_of(sl.L.pl);
+    const int occ = std::max(1, std::min(4, batched_ctas_per_sm(&S.lc, sl.L.pl.model, smem)));
+    const int g = (sl.L.pl.model == FFRG_MODEL_D3 ? 0 : 4) + occ - 1;
     // estimated cost of one item: rows x (angle nodes per row + per-row work)
     const long long cost = (long long)sl.L.pl.fn_items * sl.L.pl.fcr * (sl.L.pl.fjb + 1);
-    if (sl.L.pl.model == FFRG_MODEL_D3) {
-      d3f[n3++] = i;
-      it3 += sl.L.pl.fn_items;
-      d3s[n3] = it3;
-      d3c[n3] = d3c[n3 - 1] + cost;
-      bl.smem_d3 = std::max(bl.smem_d3, smem32_of(sl.L.pl));
-    } else {
-      ftf[nf++] = i;
-      itf += sl.L.pl.fn_items;
-      fts[nf] = itf;
-      ftc[nf] = ftc[nf - 1] + cost;
-      bl.smem_ft = std::max(bl.smem_ft, smem32_of(sl.L.pl));
-    }
+    const int k = gn[g]++;
+    gflows(g)[k] = i;
+    gitems[g] += sl.L.pl.fn_items;
+    gstart(g)[k + 1] = gitems[g];
+    gcost(g)[k + 1] = gcost(g)[k] + cost;
+    gsmem[g] = std::max(gsmem[g], smem);
   }
   cudaError_t e = cudaMemcpyAsync(ls.descs, S.stage_host, set_bytes_of(cap), cudaMemcpyHostToDevice, S.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);  // the staging buffer is reused
   if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve descriptor upload");
   int *dl = ls.lists;
+  const long long *dc = (const long long *)(dl + list_ints(cap));
   bl.descs = ls.descs;
   bl.n_flows = n;
-  bl.d3_flows = dl + cap;
-  bl.d3_start = dl + 2 * cap;
-  bl.n_d3 = n3;
-  bl.d3_items = it3;
-  bl.ft_flows = dl + 3 * cap + 1;
-  bl.ft_start = dl + 4 * cap + 1;
-  bl.n_ft = nf;
-  bl.ft_items = itf;
-  bl.d3_cost = (const long long *)(dl + list_ints(cap));
-  bl.ft_cost = bl.d3_cost + cap + 1;
+  for (int g = 0; g < kMaxBatchGroups; ++g) {
+    if (gn[g] == 0) continue;
+    BatchGroup &G = bl.groups[bl.n_groups++];
+    G.model = g < 4 ? FFRG_MODEL_D3 : FFRG_MODEL_FINITE_T;
+    G.flows = dl + cap + g * (2 * cap + 1);
+    G.start = G.flows + cap;
+    G.cost = dc + (size_t)g * (cap + 1);
+    G.n = gn[g];
+    G.items = gitems[g];
+    G.smem = gsmem[g];
+  }
   return FFRG_OK;
 }
 
