@@ -27,10 +27,13 @@ MASK64 = (1 << 64) - 1
 # model identifiers (same numbering on both sides of the parity tests)
 MODEL_D3 = 1          # d=3, T=0 scalar two-point flow
 MODEL_D4_VERTEX = 2   # d=4, three coupled dressing tables (Z, lambda3, lambda4)
-MODEL_FINITE_T = 3    # d=3 spatial + bosonic Matsubara sum
+MODEL_FINITE_T = 3    # d=3 spatial + Matsubara sum (bosonic or fermionic loop)
 
 REG_EXP = 0
 REG_LITIM = 1
+
+STAT_BOSE = 0
+STAT_FERMI = 1
 
 
 class SplitMix64:
@@ -77,6 +80,8 @@ class Problem:
     n_stack: int = 1
     x_min: float = 1e-3
     x_max: float = 10.0
+    # finite T: loop frequencies bosonic (STAT_BOSE) or fermionic (STAT_FERMI)
+    statistics: int = 0
 
     def n_ext(self) -> int:
         if self.model == MODEL_D3:
@@ -92,7 +97,7 @@ class Problem:
         if self.model == MODEL_D4_VERTEX:
             n *= self.n_ang2
         if self.model == MODEL_FINITE_T:
-            n *= 2 * self.n_matsubara + 1
+            n *= 2 * self.n_matsubara + 1 + (1 if self.statistics == STAT_FERMI else 0)
         return n
 
     def evals(self) -> int:
@@ -178,8 +183,9 @@ def make_d4(seed: int = 2, n_pts: int = 128, n_ext_ang: int = 8, n_rad: int = 12
 
 def make_finite_t(seed: int = 3, N: int = 16, T: float = 0.002, n_pts: int = 64, n_ext_p: int = 64,
                   n_ext_m: int = 9, n_rad: int = 96, n_ang: int = 48, Lambda: float = 10.0,
-                  k_end: float = 0.01, regulator: int = REG_EXP) -> Workload:
-    """Finite T: tables Z(n,|p|) and lam(n,|p|) stacked over |n| <= N+8 (bosonic frequencies)."""
+                  k_end: float = 0.01, regulator: int = REG_EXP, fermionic: bool = False) -> Workload:
+    """Finite T: tables Z(j,|p|) and lam(j,|p|) stacked over the loop frequency index j <= N+8:
+    bosonic omega_j = 2 pi T j, or (fermionic=True) nu_j = (2j+1) pi T."""
     rng = SplitMix64(seed)
     a = rng.uniform(0.0, 0.2)
     b = rng.uniform(0.5, 2.0)
@@ -189,9 +195,10 @@ def make_finite_t(seed: int = 3, N: int = 16, T: float = 0.002, n_pts: int = 64,
     n_stack = N + n_ext_m
     pb = Problem(model=MODEL_FINITE_T, n_rad=n_rad, n_ang1=n_ang, n_ext_p=n_ext_p, n_ext_ang=n_ext_m,
                  n_matsubara=N, regulator=regulator, m2_over_k2=0.5, T=T,
-                 n_tables=2, n_pts=n_pts, n_stack=n_stack)
+                 n_tables=2, n_pts=n_pts, n_stack=n_stack, statistics=STAT_FERMI if fermionic else STAT_BOSE)
     xs = log_grid(n_pts, pb.x_min, pb.x_max)
-    om2 = (2.0 * math.pi * T * np.arange(n_stack, dtype=np.float64)) ** 2
+    j = np.arange(n_stack, dtype=np.float64)
+    om2 = (math.pi * T * (2.0 * j + 1.0) if fermionic else 2.0 * math.pi * T * j) ** 2
     e2 = xs[None, :] ** 2 + om2[:, None]
     tables = np.stack([_bump(e2, a, b), g * _bump(e2, c, bl)])
     ps = log_grid(n_ext_p, pb.p_min, pb.p_max)

@@ -43,6 +43,7 @@ class _Problem(ctypes.Structure):
         ("n_ext_p", ctypes.c_int), ("n_ext_ang", ctypes.c_int), ("n_matsubara", ctypes.c_int),
         ("include_p0", ctypes.c_int),
         ("n_tables", ctypes.c_int), ("n_pts", ctypes.c_int), ("n_stack", ctypes.c_int),
+        ("statistics", ctypes.c_int),
         ("m2_over_k2", ctypes.c_double), ("m2_shift", ctypes.c_double), ("lam", ctypes.c_double),
         ("T", ctypes.c_double), ("p_min", ctypes.c_double), ("p_max", ctypes.c_double),
         ("qmax_over_k", ctypes.c_double), ("prefactor", ctypes.c_double),

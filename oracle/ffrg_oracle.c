@@ -52,6 +52,7 @@ typedef struct {
   int n_rad, n_ang1, n_ang2;
   int n_ext_p, n_ext_ang, n_matsubara, include_p0;
   int n_tables, n_pts, n_stack;
+  int statistics; /* finite T: 0 bosonic loop frequencies, 1 fermionic */
   double m2_over_k2, m2_shift, lam, T;
   double p_min, p_max, qmax_over_k, prefactor;
   double x_min, x_max;
@@ -259,6 +260,7 @@ static int check_problem(const orc_problem *pb) {
   if (pb->model == ORC_FINITE_T && (pb->n_ext_ang < 1 || pb->n_matsubara < 0 || pb->n_tables < 2 || pb->n_stack < 1))
     return ORC_EINVAL;
   if (pb->model == ORC_D3 && pb->n_tables < 1) return ORC_EINVAL;
+  if (pb->statistics != 0 && (pb->statistics != 1 || pb->model != ORC_FINITE_T)) return ORC_EINVAL;
   if (!(pb->x_min > 0.0) || !(pb->x_max > pb->x_min) || !(pb->p_min > 0.0)) return ORC_EINVAL;
   return ORC_OK;
 }
@@ -514,16 +516,28 @@ static int rhs_d4(const orc_problem *pb, const double *tab, const double *dtab, 
 }
 
 /* ------------------------------------------------------------------ */
-/* Model finite T (Quadratureq0, Sec. 5.3.2): spatial regulator (Sec. 3.1), */
-/* bosonic frequencies omega_n = 2 pi T n, |n| <= N, tables stacked over   */
-/* |n| (App. F BosonicCoordinates1DFiniteT stack), index clamped.          */
+/* Model finite T (Quadratureq0, Sec. 5.3.2): spatial regulator (Sec. 3.1). */
+/* Bosonic loop: omega_n = 2 pi T n, |n| <= N, tables stacked over |n|     */
+/* (App. F BosonicCoordinates1DFiniteT stack).  Fermionic loop: nu_n =     */
+/* (2n+1) pi T, -N-1 <= n <= N (2N+2 frequencies, symmetric about 0),      */
+/* tables stacked over j = n (n >= 0) or -n-1 (n < 0), so that row j holds */
+/* nu_j = (2j+1) pi T (App. F FermionicCoordinates1DFiniteT stack).  The   */
+/* external frequency is bosonic, omega_m = 2 pi T m; the shifted line     */
+/* carries nu_n + omega_m = nu_{n+m}.  Stack indices are clamped.          */
 /*   I(m,p) = pref lam^2 T sum_n int d^3q/(2pi)^3                          */
 /*            dR(n,q) G(n,q)^2 L(n,q) L(n+m,|q+p|) G(n+m,|q+p|)            */
 /* ------------------------------------------------------------------ */
 static const double *stack_row(const double *tab, const orc_problem *pb, int t, int n) {
-  int a = n < 0 ? -n : n;
+  int a;
+  if (pb->statistics) a = n >= 0 ? n : -n - 1;
+  else a = n < 0 ? -n : n;
   if (a > pb->n_stack - 1) a = pb->n_stack - 1;
   return tab + ((size_t)t * pb->n_stack + a) * pb->n_pts;
+}
+
+/* Matsubara frequency of loop index n */
+static double matsubara(const orc_problem *pb, int n) {
+  return pb->statistics ? (2.0 * n + 1.0) * ORC_PI * pb->T : 2.0 * ORC_PI * pb->T * n;
 }
 
 double orc_ft_summand(const orc_problem *pb, const double *tab, double k, int n, int m, double q2, double s2) {
@@ -531,7 +545,7 @@ double orc_ft_summand(const orc_problem *pb, const double *tab, double k, int n,
   double k2 = k * k, m2 = m2_of(pb, k);
   if (s2 < 0.0) s2 = 0.0;
   double q = sqrt(q2), s = sqrt(s2);
-  double wn = 2.0 * ORC_PI * pb->T * n, wnm = 2.0 * ORC_PI * pb->T * (n + m);
+  double wn = matsubara(pb, n), wnm = matsubara(pb, n + m);
   double Zq = orc_lerp_log(stack_row(tab, pb, 0, n), np, pb->x_min, pb->x_max, q);
   double Lq = orc_lerp_log(stack_row(tab, pb, 1, n), np, pb->x_min, pb->x_max, q);
   double Zs = orc_lerp_log(stack_row(tab, pb, 0, n + m), np, pb->x_min, pb->x_max, s);
@@ -558,7 +572,7 @@ static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *ou
     int ip = e / nm, m = e % nm;
     double p = ext_p(pb, ip);
     acc_t acc = {0, 0};
-    for (int n = -N; n <= N; ++n) {
+    for (int n = pb->statistics ? -N - 1 : -N; n <= N; ++n) {
       for (int i = 0; i < nr; ++i) {
         double q = xr[i];
         for (int j = 0; j < na; ++j) {

@@ -596,3 +596,79 @@ def test_ros2_d4_feedback_flow_matches_dp45():
     y, st = oracle.ros2_flow(pb, wl.y0, wl.Lambda, t1, rtol=1e-8, atol=1e-12)
     assert np.max(np.abs(y - ref) / np.abs(ref)) < 2e-6, np.max(np.abs(y - ref) / np.abs(ref))
     assert st["steps"] > 3
+
+
+# --------------------------------------------------------------------------
+# fermionic loop frequencies nu_n = (2n+1) pi T (App. F fermionic stacks)
+# --------------------------------------------------------------------------
+def _fermionic_litim_sum(T, N, E2, m):
+    """T sum_{n=-N-1}^{N} 1/((nu_n^2+E^2)^2 (nu_{n+m}^2+E^2)), nu_n = (2n+1) pi T (mpmath)."""
+    T = mpmath.mpf(T)
+    s = mpmath.mpf(0)
+    for n in range(-N - 1, N + 1):
+        vn = (2 * n + 1) * mpmath.pi * T
+        vm = (2 * (n + m) + 1) * mpmath.pi * T
+        s += 1 / ((vn ** 2 + E2) ** 2 * (vm ** 2 + E2))
+    return T * s
+
+
+def _fermionic_litim_problem(T, N, n_ext_m, k_pts=8):
+    return fi.Problem(model=fi.MODEL_FINITE_T, n_rad=k_pts, n_ang1=3, n_ext_p=1, n_ext_ang=n_ext_m,
+                      n_matsubara=N, regulator=fi.REG_LITIM, m2_over_k2=0.5, T=T, qmax_over_k=1.0,
+                      n_tables=2, n_pts=8, n_stack=N + n_ext_m + 1, p_min=1e-200, p_max=1e-200,
+                      statistics=fi.STAT_FERMI)
+
+
+@pytest.mark.parametrize("T,N", [(0.05, 4), (0.3, 16), (1.0, 2)])
+def test_finite_t_fermionic_litim_truncated_matsubara(T, N):
+    """Fermionic loop, spatial flat regulator, Z = lam = 1, p -> 0: the 2N+2
+    frequencies nu_n, n = -N-1..N, against an independent rational sum."""
+    k, w = 1.3, 0.5
+    pb = _fermionic_litim_problem(T, N, 3)
+    out = oracle.rhs(pb, fi.constant_tables(pb, [1.0, 1.0]), k)
+    E2 = k * k * (1 + w)
+    for m in range(3):
+        exact = float(k ** 3 / (6 * mpmath.pi ** 2) * 2 * k * k * _fermionic_litim_sum(T, N, E2, m))
+        assert abs(out[m] - exact) / exact < 1e-13, m
+
+
+def test_finite_t_fermionic_infinite_sum_limit():
+    """N -> infinity: T sum_n (nu_n^2+E^2)^-3 = (1/2) d^2/d(E^2)^2 [tanh(E/2T)/(2E)]."""
+    k, w, T, N = 1.0, 0.5, 0.4, 400
+    pb = _fermionic_litim_problem(T, N, 1, k_pts=4)
+    out = oracle.rhs(pb, fi.constant_tables(pb, [1.0, 1.0]), k)
+    S1 = lambda e2: mpmath.tanh(mpmath.sqrt(e2) / (2 * T)) / (2 * mpmath.sqrt(e2))
+    E2 = mpmath.mpf(k * k * (1 + w))
+    exact = float(k ** 3 / (6 * mpmath.pi ** 2) * 2 * k * k * mpmath.diff(S1, E2, 2) / 2)
+    assert abs(out[0] - exact) / exact < 1e-11
+
+
+def test_finite_t_fermionic_stack_index_and_low_T_limit():
+    """Row j of a fermionic stack holds nu_j = (2j+1) pi T and serves n = j and
+    n = -j-1: with Z rows that grow in j the sum is even under n -> -n-1 only if
+    both members of a pair read the same row.  At T -> 0 both statistics approach
+    the continuum frequency integral int dnu/(2 pi) (nu^2+E^2)^-3 = 3/(16 E^5)."""
+    k, w, T, N = 1.0, 0.5, 0.3, 6
+    pb = _fermionic_litim_problem(T, N, 1)
+    tab = fi.constant_tables(pb, [1.0, 1.0])
+    tab[0] = (1.0 + 0.1 * np.arange(pb.n_stack))[:, None]      # Z_j = 1 + j/10
+    out = oracle.rhs(pb, tab, k)[0]
+    E2 = k * k * (1 + w)
+    s = mpmath.mpf(0)
+    for n in range(-N - 1, N + 1):
+        j = n if n >= 0 else -n - 1
+        Z = 1 + mpmath.mpf(j) / 10
+        vn2 = ((2 * n + 1) * mpmath.pi * T) ** 2
+        den = Z * (vn2 + k * k) + k * k * w            # flat regulator: q^2 + R = k^2 for q < k
+        s += Z * 2 * k * k / den ** 3                  # dR = Z 2 k^2
+    exact = float(k ** 3 / (6 * mpmath.pi ** 2) * T * s)
+    assert abs(out - exact) / exact < 1e-13
+    # low temperature: bosonic and fermionic sums both -> the continuum integral
+    Tl, Nl = 0.002, 4000
+    for stat in (fi.STAT_BOSE, fi.STAT_FERMI):
+        pl = fi.Problem(model=fi.MODEL_FINITE_T, n_rad=2, n_ang1=1, n_ext_p=1, n_ext_ang=1, n_matsubara=Nl,
+                        regulator=fi.REG_LITIM, m2_over_k2=w, T=Tl, qmax_over_k=1.0, n_tables=2, n_pts=4,
+                        n_stack=2, p_min=1e-200, p_max=1e-200, statistics=stat)
+        o = oracle.rhs(pl, fi.constant_tables(pl, [1.0, 1.0]), k)[0]
+        cont = k ** 3 / (6 * math.pi ** 2) * 2 * k * k * 3 / (16 * E2 ** 2.5)
+        assert abs(o - cont) / cont < 1e-6, stat
