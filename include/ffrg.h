@@ -81,6 +81,7 @@ typedef enum { FFRG_FP64 = 0, FFRG_MIXED = 1 } ffrg_precision;
 typedef enum { FFRG_RULE_GL = 0, FFRG_RULE_GC2 = 1 } ffrg_rule;
 typedef enum { FFRG_MODEL_D3 = 1, FFRG_MODEL_D4_VERTEX = 2, FFRG_MODEL_FINITE_T = 3 } ffrg_model;
 typedef enum { FFRG_REG_EXP = 0, FFRG_REG_LITIM = 1 } ffrg_regulator;
+typedef enum { FFRG_STAT_BOSE = 0, FFRG_STAT_FERMI = 1 } ffrg_statistics;
 
 /* One right-hand-side problem (kernel descriptor: Type/Angles/d of App. F).
  * Quadrature: radial Gauss-Legendre with n_rad nodes on [0, qmax_over_k k];
@@ -92,13 +93,20 @@ typedef enum { FFRG_REG_EXP = 0, FFRG_REG_LITIM = 1 } ffrg_regulator;
  *   D4:       [Z: p_0..p_{n-1}, p=0][lambda3: p_i x psi_j][lambda4: p_i],
  *             psi_j = n_ext_ang GL nodes in cos(psi) between the two legs
  *   FINITE_T: [p_i][m], m = 0..n_ext_ang-1 external bosonic frequencies
- *             p0_m = 2 pi T m; Matsubara sum over |n| <= n_matsubara. */
+ *             p0_m = 2 pi T m; Matsubara sum of the loop over
+ *             statistics FFRG_STAT_BOSE: omega_n = 2 pi T n, |n| <= n_matsubara
+ *             (2N+1 terms), tables stacked over |n|;
+ *             statistics FFRG_STAT_FERMI: nu_n = (2n+1) pi T, -N-1 <= n <= N
+ *             (2N+2 terms), tables stacked over j = n (n >= 0) or -n-1, row j
+ *             at nu_j = (2j+1) pi T (App. F bosonic / fermionic finite-T
+ *             coordinate stacks).  The shifted line carries frequency n+m.
+ *             Stack indices beyond n_stack-1 are clamped to it. */
 typedef struct {
   int model;        /* ffrg_model */
   int regulator;    /* ffrg_regulator */
   int n_rad, n_ang1, n_ang2;
   int n_ext_p, n_ext_ang, n_matsubara, include_p0;
-  int reserved0;
+  int statistics;   /* ffrg_statistics of the loop frequencies (FINITE_T; 0 otherwise) */
   double m2_over_k2, m2_shift; /* m^2 = m2_over_k2 k^2 + m2_shift */
   double lam;                  /* coupling: lam^2 multiplies D3 and FINITE_T */
   double T;                    /* temperature (FINITE_T) */

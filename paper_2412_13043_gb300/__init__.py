@@ -23,6 +23,7 @@ FP64, MIXED = 0, 1
 RULE_GL, RULE_GC2 = 0, 1
 MODEL_D3, MODEL_D4_VERTEX, MODEL_FINITE_T = 1, 2, 3
 REG_EXP, REG_LITIM = 0, 1
+STAT_BOSE, STAT_FERMI = 0, 1
 
 
 class FfrgError(RuntimeError):
@@ -39,7 +40,7 @@ class Problem(ctypes.Structure):
         ("model", ctypes.c_int), ("regulator", ctypes.c_int),
         ("n_rad", ctypes.c_int), ("n_ang1", ctypes.c_int), ("n_ang2", ctypes.c_int),
         ("n_ext_p", ctypes.c_int), ("n_ext_ang", ctypes.c_int), ("n_matsubara", ctypes.c_int),
-        ("include_p0", ctypes.c_int), ("reserved0", ctypes.c_int),
+        ("include_p0", ctypes.c_int), ("statistics", ctypes.c_int),
         ("m2_over_k2", ctypes.c_double), ("m2_shift", ctypes.c_double), ("lam", ctypes.c_double),
         ("T", ctypes.c_double), ("p_min", ctypes.c_double), ("p_max", ctypes.c_double),
         ("qmax_over_k", ctypes.c_double), ("prefactor", ctypes.c_double),
@@ -160,9 +161,7 @@ def to_problem(pb) -> Problem:
     """Build the C struct from any object with the problem's attribute names."""
     c = Problem()
     for name, _ in Problem._fields_:
-        if name == "reserved0":
-            continue
-        setattr(c, name, getattr(pb, name))
+        setattr(c, name, getattr(pb, name, 0) if name == "statistics" else getattr(pb, name))
     return c
 
 

@@ -330,7 +330,7 @@ static int adjoint_setup(ffrg_ctx *ctx, Plan *pl, int model, void (**kern_out)(A
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, smem);
   if (e != cudaSuccess || per_sm < 1) return set_cuda_error(ctx, e ? e : cudaErrorInvalidConfiguration, "occupancy");
   int grid = std::max(1, std::min(pl->n_items, per_sm * ctx->num_sms));
-  st = dev_alloc(ctx, (void **)&pl->radD, (size_t)pl->nr * (2 * pl->N + 1) * sizeof(double));
+  st = dev_alloc(ctx, (void **)&pl->radD, (size_t)pl->nr * pl->nfreq * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->gpart, (size_t)grid * pl->tab_count * sizeof(double));
   if (st) return st;
   pl->adj_smem = smem;

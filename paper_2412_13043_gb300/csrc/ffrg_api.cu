@@ -153,6 +153,9 @@ int validate_problem(const ffrg_problem *pb, const ffrg_table_desc *td) {
   if (pb->model == FFRG_MODEL_FINITE_T) {
     if (pb->n_ext_ang < 1 || pb->n_ext_ang > 1024 || pb->n_matsubara < 0 || pb->n_matsubara > 4096) return FFRG_EINVAL;
     if (!(pb->T > 0.0) || !isfinite(pb->T)) return FFRG_EINVAL;
+    if (pb->statistics != FFRG_STAT_BOSE && pb->statistics != FFRG_STAT_FERMI) return FFRG_EINVAL;
+  } else if (pb->statistics != FFRG_STAT_BOSE) {
+    return FFRG_EINVAL;
   }
   if (td) {
     if (!desc_ok(td)) return FFRG_EINVAL;
@@ -197,6 +200,8 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   pl->n_ext_ang = pb->n_ext_ang;
   pl->n_ext_p = pb->n_ext_p;
   pl->N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
+  pl->stat = pb->model == FFRG_MODEL_FINITE_T ? pb->statistics : FFRG_STAT_BOSE;
+  pl->nfreq = 2 * pl->N + 1 + (pl->stat == FFRG_STAT_FERMI ? 1 : 0);
   pl->include_p0 = pb->include_p0;
   pl->n_ext = ffrg_n_ext(pb);
   pl->n_tables = td->n_tables;
@@ -213,7 +218,7 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
     rows_per_outer = pl->na1;
   } else {
     pl->jb = std::min(pl->na1, 8);
-    outer_total = pl->nr * (2 * pl->N + 1);
+    outer_total = pl->nr * pl->nfreq;
     rows_per_outer = (pl->na1 + pl->jb - 1) / pl->jb;
   }
   auto chunk = [&](int target_rows) {
@@ -263,7 +268,8 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
 
 int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {
   std::vector<long long> key = {pb->model, pb->n_rad, pb->n_ang1, pb->n_ang2, pb->n_ext_p, pb->n_ext_ang,
-                                pb->n_matsubara, pb->include_p0, td->n_tables, td->n_stack, td->n_pts};
+                                pb->n_matsubara, pb->include_p0, td->n_tables, td->n_stack, td->n_pts,
+                                pb->model == FFRG_MODEL_FINITE_T ? pb->statistics : 0};
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     *out = it->second;
@@ -295,7 +301,7 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   pl->psi_w_host = wp;
   st = st ? st : upload_rule(ctx, xp, &pl->psi_x);
   st = st ? st : upload_rule(ctx, wp, &pl->psi_w);
-  size_t nF = (size_t)pl->nr * (2 * pl->N + 1);
+  size_t nF = (size_t)pl->nr * pl->nfreq;
   if (!st) st = dev_alloc(ctx, (void **)&pl->radF, nF * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radF32, nF * sizeof(float));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq, pl->nr * sizeof(double));
@@ -328,6 +334,8 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.n_ext_p = pl->n_ext_p;
   a.n_ext_ang = pl->n_ext_ang;
   a.N = pl->N;
+  a.stat = pl->stat;
+  a.nfreq = pl->nfreq;
   a.include_p0 = pl->include_p0;
   a.n_ext = pl->n_ext;
   a.n_tables = td->n_tables;
@@ -526,7 +534,8 @@ double ffrg_evals(const ffrg_problem *pb) {
   if (ne < 0) return -1.0;
   double nodes = (double)pb->n_rad * pb->n_ang1;
   if (pb->model == FFRG_MODEL_D4_VERTEX) nodes *= pb->n_ang2;
-  if (pb->model == FFRG_MODEL_FINITE_T) nodes *= (2.0 * pb->n_matsubara + 1.0);
+  if (pb->model == FFRG_MODEL_FINITE_T)
+    nodes *= (2.0 * pb->n_matsubara + 1.0 + (pb->statistics == FFRG_STAT_FERMI ? 1.0 : 0.0));
   return (double)ne * nodes;
 }
 

@@ -37,6 +37,7 @@ struct RhsArgs {
   int model, reg;
   int nr, na1, na2;
   int n_ext_p, n_ext_ang, N, include_p0, n_ext;
+  int stat, nfreq;  // loop statistics (ffrg_statistics) and frequency rows: 2N+1 (bosonic), 2N+2 (fermionic)
   int n_tables, n_stack, n_pts, tab_count;
   int tab32_count; // float2 entries of the FP32 table layout
   int cr;          // rows per work item (d=4: outer rows)
@@ -336,6 +337,7 @@ struct Plan {
   std::vector<long long> key;
   int model;
   int nr, na1, na2, n_ext_ang, n_ext_p, N, include_p0, n_ext;
+  int stat, nfreq;          // loop statistics and frequency rows (2N+1 bosonic, 2N+2 fermionic)
   int n_tables, n_stack, n_pts, tab_count;
   int cr, n_chunks, n_items, jb;  // block-sized work items (adjoint kernels)
   int fcr, fn_chunks, fn_items;   // warp-sized work items of the mixed forward kernels (and serving)

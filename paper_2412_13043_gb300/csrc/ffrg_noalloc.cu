@@ -98,10 +98,10 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.a2_w = sc.take<double>(pl.na2);
   pl.psi_x = sc.take<double>(npsi);
   pl.psi_w = sc.take<double>(npsi);
-  pl.radF = sc.take<double>((size_t)pl.nr * (2 * pl.N + 1));
+  pl.radF = sc.take<double>((size_t)pl.nr * pl.nfreq);
   pl.radq = sc.take<double>(pl.nr);
   pl.radq32 = sc.take<float>(pl.nr);
-  pl.radF32 = sc.take<float>((size_t)pl.nr * (2 * pl.N + 1));
+  pl.radF32 = sc.take<float>((size_t)pl.nr * pl.nfreq);
   pl.work_ctr = sc.take<unsigned>(4);
   pl.ext_done = sc.take<unsigned>(pl.n_ext);
   pl.kconst = sc.take<double>(kKConstBytes / sizeof(double));

@@ -73,11 +73,14 @@ __device__ __noinline__ float pole_d4(const RhsArgs *a, int e, int r, int ia, in
   return pole_prop(a, a->tab, s2, 0.0);
 }
 
+// stack row of loop frequency index n: |n| (bosonic), n or -n-1 (fermionic)
+__device__ __forceinline__ int stack_index(int stat, int n) { return stat ? (n >= 0 ? n : -n - 1) : abs(n); }
+
 __device__ __noinline__ float pole_ft(const RhsArgs *a, int e, int n, int r, int j) {
   const int nm = a->n_ext_ang, ip = e / nm, m = e - ip * nm;
   const double p = ext_momentum(*a, ip), q = a->radq[r], c = a->a1_x[j];
-  const int srow = min(abs(n + m), a->n_stack - 1);
-  const double om = 2.0 * kPi * a->T * (double)(n + m);
+  const int srow = min(stack_index(a->stat, n + m), a->n_stack - 1);
+  const double om = kPi * a->T * (2.0 * (double)(n + m) + (a->stat ? 1.0 : 0.0));
   return pole_prop(a, a->tab + (size_t)srow * a->n_pts, q * q + p * p + 2.0 * q * p * c, om * om);
 }
 
@@ -246,11 +249,13 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
     if (tid0 == 0) kp->f = make_kconst<float>(a);
     else kp->d = make_kconst<double>(a);
   }
-  // Per-radial factors F(n, r), in blocks of kPreR radial nodes x kPreN values
-  // of |n|.  Phase A: the n-independent part of each node (q^2, weight x
-  // measure, k^2 r(x), k^2 rdot(x), the table position of q^2) once per block
-  // into shared memory.  Phase B: F for n >= 0, written to n and -n (the
-  // tables are indexed by |n| and omega_n^2 is even in n).
+  // Per-radial factors F(n, r), in blocks of kPreR radial nodes x kPreN
+  // stack rows j.  Phase A: the n-independent part of each node (q^2, weight
+  // x measure, k^2 r(x), k^2 rdot(x), the table position of q^2) once per
+  // block into shared memory.  Phase B: F for stack row j, written to both
+  // loop indices that read row j and share its frequency^2: n = j and
+  // n = -j (bosonic, omega_j = 2 pi T j) or n = -j-1 (fermionic, nu_j =
+  // (2j+1) pi T).  Row of loop index n in radF: n + N + stat.
   const int nr = a.nr, N = a.N;
   const int n_rt = (nr + kPreR - 1) / kPreR, n_nb = N / kPreN + 1;
   __shared__ double s_q2[kPreR], s_wm[kPreR], s_kr[kPreR], s_rd[kPreR], s_wl[kPreR];
@@ -285,7 +290,7 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
         const int row = min(n, a.n_stack - 1);
         const double Z = lerp_at(a.tab + (size_t)row * a.n_pts, i0, wl);
         const double Lq = lerp_at(a.tab + ((size_t)a.n_stack + row) * a.n_pts, i0, wl);
-        const double om = 2.0 * kPi * a.T * n;
+        const double om = a.stat ? (2.0 * n + 1.0) * kPi * a.T : 2.0 * kPi * a.T * n;
         const double G = 1.0 / (Z * (om * om + q2 + s_kr[i]) + m2);
         F = s_wm[i] * (Z * rd) * G * G * Lq;
       } else {
@@ -296,7 +301,7 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
         // d F / d Z(q): dR = Z k^2 rdot, G = 1/(Z P + m^2) with P = q^2 + k^2 r
         if (a.radD) a.radD[r] = s_wm[i] * rd * G * G * (1.0 - 2.0 * Z * G * P);
       }
-      const int ip = (N + n) * nr + r, im = (N - n) * nr + r;
+      const int ip = (N + a.stat + n) * nr + r, im = (N - n) * nr + r;
       a.radF[ip] = F;
       a.radF[im] = F;
       if (a.radF32) {
@@ -535,16 +540,17 @@ __device__ __forceinline__ RowAcc<T> ft_witem(const RhsArgs &a, const RhsArgs *s
                                            const KConst<T> &kc, int e, int c, int lane) {
   const T us = kc.us, uy1 = kc.uy1, sy = kc.sy;
   const int np = a.n_pts, nm = a.n_ext_ang, na1 = a.na1, nr = a.nr, jb = a.jb, nblk = (na1 + jb - 1) / jb;
-  const int outer_total = (2 * a.N + 1) * nr;
+  const int outer_total = a.nfreq * nr;
   const int ip = e / nm, m = e - ip * nm;
+  const T half = (T)(a.stat ? 0.5 : 0.0);  // fermionic loop: nu = 2 pi T (n + 1/2)
   const T p = (T)a.ext_pd[ip], p2 = p * p;
   const int r0 = c * a.cr, r1 = min(r0 + a.cr, outer_total * nblk);
   RowAcc<T> acc;
   for (int rr = r0 + lane; rr < r1; rr += 32) {
     const int o = rr / nblk, j0 = (rr - o * nblk) * jb, j1 = min(j0 + jb, na1);
-    const int nn = o / nr, r = o - nn * nr, n = nn - a.N;
-    const int srow = min(abs(n + m), a.n_stack - 1);
-    const T om = kc.twopiT * (T)(n + m);
+    const int nn = o / nr, r = o - nn * nr, n = nn - a.N - a.stat;
+    const int srow = min(stack_index(a.stat, n + m), a.n_stack - 1);
+    const T om = kc.twopiT * ((T)(n + m) + half);
     const T om2s = om * om * kc.som;
     const T q = radial_q<T>(a, r);
     const T by = (q * q + p2) * sy, ty = (T)2 * q * p * sy;

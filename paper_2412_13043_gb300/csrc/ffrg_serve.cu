@@ -80,10 +80,10 @@ static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotL
   L.o_ys = seg(u, (size_t)L.ny * d);
   L.o_K = seg(u, (size_t)7 * L.ny * d);
   L.o_raw = seg(u, (size_t)pl.n_ext * d);
-  L.o_radF = seg(u, (size_t)pl.nr * (2 * pl.N + 1) * d);
+  L.o_radF = seg(u, (size_t)pl.nr * pl.nfreq * d);
   L.o_radq = seg(u, (size_t)pl.nr * d);
   L.o_radq32 = seg(u, (size_t)pl.nr * sizeof(float));
-  L.o_radF32 = seg(u, (size_t)pl.nr * (2 * pl.N + 1) * sizeof(float));
+  L.o_radF32 = seg(u, (size_t)pl.nr * pl.nfreq * sizeof(float));
   L.o_kc = seg(u, kKConstBytes);
   L.o_extp = seg(u, (size_t)pl.n_ext_p * d);
   L.o_psis = seg(u, (size_t)L.npsi * d);

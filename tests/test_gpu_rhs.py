@@ -156,6 +156,52 @@ def test_finite_t_full_size_sampled(ctx, N, T_over_kend):
     _check(ctx, wl, 1.0, sel=sel)
 
 
+# ----------------------------------------------------------------------------- fermionic loop
+def test_finite_t_fermionic_small_ragged(ctx):
+    """nu_n = (2n+1) pi T, n = -N-1..N, fermionic stacks (App. F)."""
+    for N, T in ((0, 0.3), (3, 0.05), (5, 0.5)):
+        wl = fi.make_finite_t(seed=61 + N, N=N, T=T, n_pts=16, n_ext_p=7, n_ext_m=4, n_rad=13, n_ang=9,
+                              fermionic=True)
+        for k in (10.0, 0.4):
+            _check(ctx, wl, k)
+
+
+@pytest.mark.parametrize("N,T_over_kend", [(16, 0.05), (64, 1.0)])
+def test_finite_t_fermionic_full_size_sampled(ctx, N, T_over_kend):
+    wl = fi.make_finite_t(seed=4, N=N, T=T_over_kend * 0.01, fermionic=True)   # 96 x 48 x (2N+2)
+    ne = wl.problem.n_ext()
+    sel = [0, 8, 9 * 20 + 4, 9 * 40 + 1, ne - 9, ne - 1]
+    _check(ctx, wl, 1.0, sel=sel)
+
+
+def test_finite_t_fermionic_litim_closed_form_on_gpu(ctx):
+    """Flat regulator, Z = lam = 1, p -> 0: k^5/(3 pi^2) T sum_n (nu_n^2+E^2)^-3
+    summed over the 2N+2 fermionic frequencies (rational sum in mpmath)."""
+    import mpmath
+
+    import paper_2412_13043_gb300 as ffrg
+    k, w, T, N = 1.3, 0.5, 0.3, 16
+    pb = fi.Problem(model=fi.MODEL_FINITE_T, n_rad=8, n_ang1=3, n_ext_p=1, n_ext_ang=1, n_matsubara=N,
+                    regulator=fi.REG_LITIM, m2_over_k2=w, T=T, qmax_over_k=1.0, n_tables=2, n_pts=8,
+                    n_stack=N + 2, p_min=1e-200, p_max=1e-200, statistics=fi.STAT_FERMI)
+    wl = fi.Workload(pb, fi.constant_tables(pb, [1.0, 1.0]), None, 10.0, 0.01, 0, 0, {})
+    E2 = mpmath.mpf(k * k * (1 + w))
+    s = sum(1 / (((2 * n + 1) * mpmath.pi * T) ** 2 + E2) ** 3 for n in range(-N - 1, N + 1))
+    exact = float(k ** 3 / (6 * mpmath.pi ** 2) * 2 * k * k * T * s)
+    g = _run(ctx, wl, k, ffrg.FP64)[0]
+    assert abs(g - exact) / exact < 1e-12
+
+
+def test_fermionic_flag_rejected_outside_finite_t(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d3(seed=1, n_pts=16, n_ext_p=8, n_rad=8, n_ang=4)
+    wl.problem.statistics = fi.STAT_FERMI
+    tabs = ctx.tables(wl.problem, wl.tables)
+    with pytest.raises(ffrg.FfrgError):
+        ctx.rhs(wl.problem, tabs, 1.0)
+    tabs.free()
+
+
 # ----------------------------------------------------------------------------- errors
 def test_nonfinite_table_sets_status(ctx):
     import paper_2412_13043_gb300 as ffrg

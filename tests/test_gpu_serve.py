@@ -146,3 +146,22 @@ def test_cancel_and_unknown_ticket():
     assert ctx.serve_cancel(12345678) == ffrg.ENOTFOUND
     ctx.serve_stop()
     ctx.close()
+
+
+def test_served_fermionic_flows_match_oracle():
+    """Finite-T flows with a fermionic loop through the server."""
+    import paper_2412_13043_gb300 as ffrg
+    wls = [fi.make_finite_t(seed=70 + i, N=n, T=t, n_pts=24, n_ext_p=3, n_ext_m=3, n_rad=12, n_ang=6,
+                            fermionic=True) for i, (n, t) in enumerate(((2, 0.3), (4, 0.15), (1, 0.5)))]
+    ctx = gpu_context()
+    ctx.serve_start(max_slots=3)
+    tks = [_submit(ctx, wl) for wl in wls]
+    res = _wait(ctx, tks, [wl.problem.n_ext() for wl in wls])
+    ctx.serve_stop()
+    ctx.close()
+    for wl, tk in zip(wls, tks):
+        truth, _ = oracle.flow(wl.problem, wl.tables, wl.y0, wl.Lambda, math.log(wl.Lambda / wl.k_end),
+                               rtol=1e-13, atol=1e-16)
+        st, y, _, _ = res[tk]
+        assert st == ffrg.OK
+        assert np.max(np.abs(y - truth) / np.abs(truth)) < 1e-7
