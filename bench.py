@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-flows", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-models", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1024)
     return ap.parse_args()
 
@@ -269,6 +270,53 @@ def implicit_bench(ctx):
             "runs": rows}
 
 
+def model_bench(ctx, steps: int = 5):
+    """Single-RHS throughput of the other model workloads, mixed and FP64:
+    d=3 (64 ext x 64 x 32 nodes), finite T (64 |p| x 9 p0, 96 x 48 x (2N+1))
+    at N = 16/32/64 with T/k_end = 0.05/0.2/1, and the fermionic loop at
+    N = 16 (2N+2 frequencies).  step_ms: one ffrg_rhs (precompute + main);
+    kernel_ms: the main kernel (profiling events); k = 1."""
+    import numpy as np
+    import torch
+
+    import ffrg_inputs as fi
+    import paper_2412_13043_gb300 as ffrg
+    cases = [("d3, 64 ext x (64 x 32)", fi.make_d3(seed=1))]
+    for N, tk in ((16, 0.05), (32, 0.2), (64, 1.0)):
+        cases.append((f"finite T bosonic N={N}, T/k_end={tk}", fi.make_finite_t(seed=3, N=N, T=tk * 0.01)))
+    cases.append(("finite T fermionic N=16, T/k_end=0.05",
+                  fi.make_finite_t(seed=3, N=16, T=0.05 * 0.01, fermionic=True)))
+    rows = []
+    for name, wl in cases:
+        pb = wl.problem
+        tabs = ctx.tables(pb, wl.tables)
+        row = {"workload": name, "evals_per_rhs": pb.evals()}
+        outs = {}
+        for pname, prec in (("mixed", ffrg.MIXED), ("fp64", ffrg.FP64)):
+            out = torch.empty(pb.n_ext(), dtype=torch.float64, device="cuda")
+            for _ in range(3):
+                ctx.rhs(pb, tabs, 1.0, out=out, precision=prec)
+            torch.cuda.synchronize()
+            ctx.set_profiling(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                ctx.rhs(pb, tabs, 1.0, out=out, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            kms, cnt = ctx.profile_read()
+            ctx.set_profiling(False)
+            step_ms = e0.elapsed_time(e1) / steps
+            row[pname] = {"step_ms": step_ms, "kernel_ms": kms / max(cnt, 1),
+                          "evals_per_s": pb.evals() / (step_ms * 1e-3)}
+            outs[pname] = out.cpu().numpy()
+        row["mixed_vs_fp64_max_rel_err"] = float(np.max(np.abs(outs["mixed"] - outs["fp64"]) / np.abs(outs["fp64"])))
+        row["speedup_mixed_over_fp64"] = row["fp64"]["step_ms"] / row["mixed"]["step_ms"]
+        rows.append(row)
+        tabs.free()
+    return rows
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -463,6 +511,10 @@ def main():
     if not args.no_flows:
         implicit = implicit_bench(ctx)
 
+    models = None
+    if not args.no_models:
+        models = model_bench(ctx)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wl, stride=4)
@@ -486,6 +538,7 @@ def main():
             "flows": flows,
             "serving": serving,
             "implicit_vs_explicit": implicit,
+            "models": models,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
