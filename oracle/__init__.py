@@ -104,6 +104,8 @@ def _load():
         lib.orc_dp45_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
         lib.orc_ros2_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
         lib.orc_ros2_flow.argtypes = [pp, D, dp, P(_StepOpts), P(_Stats)]
+        lib.orc_abm_textbook.argtypes = [I, I, D, D, ctypes.c_long, dp, P(ctypes.c_long)]
+        lib.orc_abm_flow.argtypes = [pp, dp, I, D, dp, D, D, ctypes.c_long, I, P(_Stats)]
         lib.orc_flow_state_size.argtypes = [pp, I]
         lib.orc_d3_summand.argtypes = [pp, dp, D, D, D]
         lib.orc_d3_summand.restype = D
@@ -271,6 +273,26 @@ def ros2_textbook(which: int, y0, t1: float, dt0: float = 0.1, dt_min: float = 1
     st = _Stats()
     code = _load().orc_ros2_textbook(int(which), _ptr(y), ctypes.byref(o), ctypes.byref(st))
     return y, dict(steps=st.steps, rejects=st.rejects, jacobians=st.rhs_evals, status=code)
+
+
+def abm_textbook(which: int, order: int, y0, t1: float, n: int, t0: float = 0.0):
+    """Adams-Bashforth-Moulton (PECE, order 2..5, RK4 start) in n fixed steps on a
+    textbook ODE (0-2 as dp45_textbook, 3: y' = 4 t^3)."""
+    y = _f64(y0).copy()
+    ev = ctypes.c_long()
+    _check(_load().orc_abm_textbook(int(which), int(order), t0, t1, int(n), _ptr(y), ctypes.byref(ev)),
+           "abm_textbook")
+    return y, ev.value
+
+
+def abm_flow(pb, tables, y0, Lambda: float, t1: float, n: int, order: int = 4, feedback: int = 0,
+             t0: float = 0.0):
+    """ABM flow of the state from t_+ = t0 to t1 in n fixed steps."""
+    y = _f64(y0).copy()
+    st = _Stats()
+    _check(_load().orc_abm_flow(ctypes.byref(_problem(pb)), _ptr(_f64(tables)), int(feedback), Lambda, _ptr(y),
+                                t0, t1, int(n), int(order), ctypes.byref(st)), "abm_flow")
+    return y, dict(steps=st.steps, rhs_evals=st.rhs_evals)
 
 
 def ros2_flow(pb, y0, Lambda: float, t1: float, dt0: float = 1e-2, dt_min: float = 1e-10, dt_max: float = 0.5,

@@ -672,3 +672,44 @@ def test_finite_t_fermionic_stack_index_and_low_T_limit():
         o = oracle.rhs(pl, fi.constant_tables(pl, [1.0, 1.0]), k)[0]
         cont = k ** 3 / (6 * math.pi ** 2) * 2 * k * k * 3 / (16 * E2 ** 2.5)
         assert abs(o - cont) / cont < 1e-6, stat
+
+
+# --------------------------------------------------------------------------
+# Adams-Bashforth-Moulton (PECE, fixed step, RK4 start)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+def test_abm_order_of_convergence(order):
+    """Global error ~ h^order: error ratio 2^order per halving of h on the
+    harmonic oscillator and (orders 3-5) on y' = y cos t (y = exp(sin t)); for
+    order 2 the latter's error changes sign near t = 3, so it gives no rate."""
+    cases = [(2, [1.0, 0.0], lambda t: [math.cos(t), -math.sin(t)], (80, 160, 320))]
+    if order >= 3:
+        cases.append((0, [1.0], lambda t: [math.exp(math.sin(t))], (160, 320, 640)))
+    for which, y0, exact, ns in cases:
+        t1 = 3.0
+        errs = []
+        for n in ns:
+            y, ev = oracle.abm_textbook(which, order, y0, t1, n)
+            errs.append(np.max(np.abs(y - np.array(exact(t1)))))
+            assert ev == 1 + 4 * (order - 1) + 2 * (n - order + 1)
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+        assert all(order - 0.35 < r < order + 0.6 for r in rates), (which, order, rates)
+
+
+def test_abm4_exact_for_cubic_derivative():
+    """y' = 4 t^3: Simpson-exact RK4 start and AB4/AM4 exact for cubic f."""
+    y, _ = oracle.abm_textbook(3, 4, [0.5], 2.0, 13, t0=0.25)
+    assert abs(y[0] - (0.5 + 2.0 ** 4 - 0.25 ** 4)) < 1e-13
+
+
+def test_abm_flow_matches_dp45_flow():
+    """The ABM flow of a frozen d=3 RHS against a tight DP5(4) flow."""
+    wl = fi.make_d3(seed=3, n_pts=16, n_ext_p=8, n_rad=10, n_ang=6)
+    t1 = math.log(wl.Lambda / wl.k_end)
+    ref, _ = oracle.flow(wl.problem, wl.tables, wl.y0, wl.Lambda, t1, rtol=1e-12, atol=1e-15)
+    errs = []
+    for n in (100, 200):
+        y, st = oracle.abm_flow(wl.problem, wl.tables, wl.y0, wl.Lambda, t1, n, order=4)
+        errs.append(np.max(np.abs(y - ref) / np.abs(ref)))
+        assert st["rhs_evals"] == 1 + 4 * 3 + 2 * (n - 3)
+    assert errs[1] < 1e-6 and errs[0] / errs[1] > 8      # fourth order
