@@ -232,10 +232,11 @@ def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
             "saturation_latency_p50_s": sorted(lat_sat.values())[len(lat_sat) // 2]}
 
 
-def implicit_bench(ctx):
-    """Linearly implicit ROS2 (Jacobian from the adjoint kernels) vs
-    explicit DP5(4), both FP64, on the d=4 feedback flow, at matched endpoint
-    error against a tight DP5(4) reference."""
+def stepper_bench(ctx):
+    """Steppers on the d=4 feedback flow at matched endpoint error against a
+    tight DP5(4) reference, all FP64: adaptive DP5(4) (6 RHS per step),
+    fixed-step Adams-Bashforth-Moulton (PECE, 2 RHS per step) and the linearly
+    implicit ROS2 (Jacobian from the adjoint kernels)."""
     import numpy as np
     import torch
 
@@ -247,24 +248,28 @@ def implicit_bench(ctx):
     t1 = math.log(wl.Lambda / wl.k_end)
     tabs = ctx.tables(pb, wl.tables)
 
-    def run(kind, rtol):
+    def run(kind, par):
         y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t = time.perf_counter()
         if kind == "dp45":
-            st = ctx.flow(pb, tabs, y, wl.Lambda, t1, feedback=1, precision=ffrg.FP64, rtol=rtol, atol=1e-14)
+            st = ctx.flow(pb, tabs, y, wl.Lambda, t1, feedback=1, precision=ffrg.FP64, rtol=par, atol=1e-14)
+        elif kind == "abm4":
+            st = ctx.abm_flow(pb, tabs, y, wl.Lambda, t1, par, order=4, feedback=1, precision=ffrg.FP64)
         else:
-            st = ctx.rosenbrock_flow(pb, tabs, y, wl.Lambda, t1, rtol=rtol, atol=1e-14)
+            st = ctx.rosenbrock_flow(pb, tabs, y, wl.Lambda, t1, rtol=par, atol=1e-14)
         torch.cuda.synchronize()
         return y.cpu().numpy(), time.perf_counter() - t, st
 
     ref, _, _ = run("dp45", 1e-12)
     rows = []
-    for kind, rtol in (("dp45", 1e-6), ("dp45", 1e-8), ("ros2", 1e-5), ("ros2", 1e-6), ("ros2", 1e-7)):
-        y, dt, st = run(kind, rtol)
-        rows.append({"method": kind, "rtol": rtol, "endpoint_rel_err": float(np.max(np.abs(y - ref) / np.abs(ref))),
+    for kind, par in (("dp45", 1e-6), ("dp45", 1e-8), ("abm4", 50), ("abm4", 100), ("abm4", 200), ("abm4", 400),
+                      ("ros2", 1e-5), ("ros2", 1e-6), ("ros2", 1e-7)):
+        y, dt, st = run(kind, par)
+        rows.append({"method": kind, ("steps_requested" if kind == "abm4" else "rtol"): par,
+                     "endpoint_rel_err": float(np.max(np.abs(y - ref) / np.abs(ref))),
                      "steps": st["steps"], "rejects": st["rejects"], "rhs_evals": st["rhs_evals"],
-                     "jacobians": st["jac_evals"], "seconds": dt})
+                     "jacobians": st.get("jac_evals", 0), "seconds": dt})
     tabs.free()
     return {"workload": "d4 feedback flow, 32-pt tables, 4 ext angles, 32 x 16 x 8 nodes, k: 10 -> 0.01, FP64",
             "runs": rows}
@@ -507,9 +512,9 @@ def main():
     if not args.no_serve:
         serving = serving_bench(ctx, args.serve_requests)
 
-    implicit = None
+    steppers = None
     if not args.no_flows:
-        implicit = implicit_bench(ctx)
+        steppers = stepper_bench(ctx)
 
     models = None
     if not args.no_models:
@@ -537,7 +542,7 @@ def main():
             "clocks": clocks,
             "flows": flows,
             "serving": serving,
-            "implicit_vs_explicit": implicit,
+            "steppers": steppers,
             "models": models,
             "cpu_baseline": cpu,
         }

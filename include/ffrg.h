@@ -244,6 +244,19 @@ FFRG_API int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables 
 FFRG_API int ffrg_rhs_jacobian(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
                                double *J_dev, void *stream);
 
+/* Adams-Bashforth-Moulton flow (the paper's Boost_ABM explicit multistep
+ * option, Sec. 5.2.1): n_steps fixed steps h = (t1 - t0)/n_steps in t_+ from
+ * state_dev (overwritten with y(t1)); state, feedback modes, Lambda and
+ * precision as for ffrg_flow.  order 2..5: PECE with the order-`order`
+ * Adams-Bashforth predictor and Adams-Moulton corrector (two RHS per step);
+ * the first order-1 steps are classical fourth-order Runge-Kutta steps.  No
+ * error control: the caller chooses n_steps.  stats: steps = n_steps,
+ * rhs_evals, t_reached; status FFRG_ENONFINITE if the state became NaN/Inf.
+ * Synchronous. */
+FFRG_API int ffrg_abm_flow(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, int feedback,
+                           double Lambda, double *state_dev, double t0, double t1, long long n_steps, int order,
+                           int precision, ffrg_flow_stats *stats, void *stream);
+
 /* Linearly implicit flow of the d=4 feedback state (the three tables, as for
  * ffrg_flow with feedback = 1) with ROS2 (Verwer, Spee, Blom, Hundsdorfer
  * 1999; the paper's implicit steppers use Jacobians, Sec. 5.2.1 / 5.2.2):

@@ -98,6 +98,8 @@ _SIGS = {
     "ffrg_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _I, _D, _P, ctypes.POINTER(StepOpts), _I,
                        ctypes.POINTER(FlowStats), _P]),
     "ffrg_rhs_jacobian": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P]),
+    "ffrg_abm_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _I, _D, _P, _D, _D, ctypes.c_longlong, _I, _I,
+                           ctypes.POINTER(FlowStats), _P]),
     "ffrg_rosenbrock_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, ctypes.POINTER(StepOpts),
                                   ctypes.POINTER(FlowStats), _P]),
     "ffrg_flow_state_size": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(TableDesc), _I]),
@@ -408,6 +410,19 @@ class Context:
         if raise_on_error:
             _check(self.handle, code, "ffrg_rosenbrock_flow")
         return dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals, jac_evals=st.jac_evals,
+                    integrand_evals=st.integrand_evals, t_reached=st.t_reached, status=code)
+
+    def abm_flow(self, pb, tables: Tables, state, Lambda: float, t1: float, n_steps: int, order: int = 4,
+                 feedback: int = 0, precision: int = FP64, t0: float = 0.0, stream=None, raise_on_error: bool = True):
+        """Adams-Bashforth-Moulton flow in n_steps fixed steps (state: CUDA float64 tensor, overwritten)."""
+        c = to_problem(pb)
+        st = FlowStats()
+        code = load().ffrg_abm_flow(self.handle, ctypes.byref(c), tables.handle, int(feedback), float(Lambda),
+                                    _dev_ptr(state, "state"), float(t0), float(t1), int(n_steps), int(order),
+                                    int(precision), ctypes.byref(st), _stream_handle(stream))
+        if raise_on_error:
+            _check(self.handle, code, "ffrg_abm_flow")
+        return dict(steps=st.steps, rejects=st.rejects, rhs_evals=st.rhs_evals,
                     integrand_evals=st.integrand_evals, t_reached=st.t_reached, status=code)
 
     def status_read(self, stream=None) -> int:

@@ -769,3 +769,251 @@ extern "C" int ffrg_rosenbrock_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, co
   dev_free(ctx, piv, ny * sizeof(int));
   return st;
 }
+
+// ---------------------------------------------------------------------------
+// Adams-Bashforth-Moulton (PECE, fixed step; the paper's Boost_ABM option,
+// Sec. 5.2.1).  Standard Adams tables: predictor AB_s with the s newest
+// back values of d_t y, corrector AM_s with the predicted value and s-1
+// back values; the first s-1 steps are classical RK4.
+// ---------------------------------------------------------------------------
+namespace ffrg {
+
+static const double kAbmB[6][5] = {{0},
+                                   {1.0},
+                                   {3.0 / 2.0, -1.0 / 2.0},
+                                   {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0},
+                                   {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0},
+                                   {1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 / 720.0}};
+static const double kAbmA[6][5] = {{0},
+                                   {1.0},
+                                   {1.0 / 2.0, 1.0 / 2.0},
+                                   {5.0 / 12.0, 8.0 / 12.0, -1.0 / 12.0},
+                                   {9.0 / 24.0, 19.0 / 24.0, -5.0 / 24.0, 1.0 / 24.0},
+                                   {251.0 / 720.0, 646.0 / 720.0, -264.0 / 720.0, 106.0 / 720.0, -19.0 / 720.0}};
+
+struct AbmCombo {
+  const double *src[6];
+  double c[6];
+  int n;
+};
+
+// Evaluation state ys = y + h sum_j c_j src_j at t + tf h (write_y: also the
+// new state y); publishes k, the feedback tables and m^2 like a DP5(4) stage.
+__global__ void abm_stage_kernel(FlowArgs f, AbmCombo cb, double h, double tf, int write_y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  FlowCtl *c = f.ctl;
+  if (i == 0) c->k_stage = c->Lambda * exp(-(c->t + tf * h));
+  if (i >= f.ny) return;
+  double v = f.y[i];
+  for (int j = 0; j < cb.n; ++j) v += h * cb.c[j] * cb.src[j][i];
+  if (write_y) f.y[i] = v;
+  f.ys[i] = v;
+  if (f.tabbuf && i >= f.tab_off && i < f.tab_off + f.tab_len) f.tabbuf[i - f.tab_off] = v;
+  if (i == 0 && f.mode == kModeD3Feedback) c->m2_stage = v;
+}
+
+__global__ void abm_deriv_kernel(FlowArgs f, double *dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < f.ny) dst[i] = deriv_component(f, i);
+}
+
+// F[j] <- F[j-1], F[0] <- d_t y at the new point; t = t0 + (steps + 1) h
+__global__ void abm_push_kernel(FlowArgs f, double *F, int order, double h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  FlowCtl *c = f.ctl;
+  if (i < f.ny) {
+    for (int j = order - 1; j >= 1; --j) F[(size_t)j * f.ny + i] = F[(size_t)(j - 1) * f.ny + i];
+    const double d = deriv_component(f, i);
+    F[i] = d;
+    if (!isfinite(d) || !isfinite(f.y[i])) c->status = FFRG_ENONFINITE;
+  }
+  if (i == 0) {
+    c->steps += 1;
+    c->t = c->t0 + (double)c->steps * h;
+  }
+}
+
+}  // namespace ffrg
+
+extern "C" int ffrg_abm_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_tables *tables, int feedback,
+                             double Lambda, double *state_dev, double t0, double t1, long long n_steps, int order,
+                             int precision, ffrg_flow_stats *stats, void *stream) {
+  if (!ctx || !pb_in || !tables || !state_dev) return FFRG_EINVAL;
+  if (precision != FFRG_FP64 && precision != FFRG_MIXED) return FFRG_EINVAL;
+  if (!(Lambda > 0.0) || !isfinite(Lambda) || !isfinite(t0) || !isfinite(t1) || !(t1 >= t0)) return FFRG_EINVAL;
+  if (order < 2 || order > 5 || n_steps < 1 || n_steps > (1LL << 40)) return FFRG_EINVAL;
+  ffrg_problem pb = *pb_in;
+  const ffrg_table_desc *td = &tables->desc;
+  int st = validate_problem(&pb, td);
+  if (st) return st;
+  const int mode = flow_mode(&pb, feedback);
+  if (mode < 0) return FFRG_EINVAL;
+  if (mode != kModeFrozen &&
+      (pb.n_ext_p != td->n_pts || pb.p_min != td->x_min || pb.p_max != td->x_max || td->n_stack != 1))
+    return FFRG_EINVAL;
+  if (mode == kModeD3Feedback) pb.include_p0 = 1;
+  const int ny = ffrg_flow_state_size(&pb, td, feedback);
+  if (ny < 1) return FFRG_EINVAL;
+  cudaSetDevice(ctx->device);
+  Plan *pl = nullptr;
+  st = get_plan(ctx, &pb, td, &pl);
+  if (st) return st;
+  const size_t d = sizeof(double), tab_bytes = ((size_t)pl->tab_count * d + 255) & ~(size_t)255;
+  FlowCtl *ctl = nullptr, *ctl_host = nullptr;
+  double *ys = nullptr, *F = nullptr, *S = nullptr, *raw = nullptr, *tabbuf = nullptr;  // S: 3 scratch derivatives
+  st = dev_alloc(ctx, (void **)&ctl, sizeof(FlowCtl));
+  if (!st) st = dev_alloc(ctx, (void **)&ys, (size_t)ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&F, (size_t)order * ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&S, (size_t)3 * ny * d);
+  if (!st) st = dev_alloc(ctx, (void **)&raw, (size_t)pl->n_ext * d);
+  if (!st && mode != kModeFrozen) st = dev_alloc(ctx, (void **)&tabbuf, tab_bytes);
+  if (!st) st = set_cuda_error(ctx, cudaMallocHost((void **)&ctl_host, sizeof(FlowCtl)), "cudaMallocHost");
+  cudaStream_t user = (cudaStream_t)stream, fs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (!st) st = set_cuda_error(ctx, cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking), "cudaStreamCreate");
+  if (!st) st = set_cuda_error(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+
+  FlowCtl hc;
+  memset(&hc, 0, sizeof(hc));
+  hc.t = t0;
+  hc.t0 = t0;
+  hc.t1 = t1;
+  hc.Lambda = Lambda;
+  hc.status = FFRG_OK;
+  FlowArgs f;
+  memset(&f, 0, sizeof(f));
+  f.ny = ny;
+  f.mode = mode;
+  f.n = td->n_pts;
+  f.npsi = pb.n_ext_ang;
+  f.tab_off = mode == kModeD3Feedback ? 1 : 0;
+  f.tab_len = mode == kModeFrozen ? 0 : pl->tab_count;
+  f.p_min = pb.p_min;
+  f.p_step = pb.n_ext_p > 1 ? log(pb.p_max / pb.p_min) / (pb.n_ext_p - 1) : 0.0;
+  f.psi_w = pl->psi_w;
+  f.y = state_dev;
+  f.ys = ys;
+  f.raw = raw;
+  f.tabbuf = tabbuf;
+  f.ctl = ctl;
+  RhsArgs a;
+  fill_args(pl, &pb, td, mode == kModeFrozen ? tables->dev : tabbuf, Lambda, a);
+  a.out = raw;
+  a.status = ctx->status_dev;
+  a.k_dev = &ctl->k_stage;
+  a.m2_dev = mode == kModeD3Feedback ? &ctl->m2_stage : nullptr;
+  a.skip = &ctl->done;  // never set: fixed steps
+
+  const int eb = 256, eg = (ny + eb - 1) / eb;
+  const double h = (t1 - t0) / (double)n_steps;
+  double *K2 = S, *K3 = S + ny, *K4 = S + 2 * (size_t)ny;  // RK4 stages; K2 also holds the predicted slope
+  auto stage = [&](std::initializer_list<std::pair<const double *, double>> terms, double tf, int write_y) {
+    AbmCombo cb;
+    memset(&cb, 0, sizeof(cb));
+    for (const auto &t : terms) {
+      cb.src[cb.n] = t.first;
+      cb.c[cb.n++] = t.second;
+    }
+    abm_stage_kernel<<<eg, eb, 0, fs>>>(f, cb, h, tf, write_y);
+  };
+  const long long n_rk = std::min<long long>(n_steps, order - 1);
+  if (!st) {
+    st = set_cuda_error(ctx, cudaEventRecord(ev, user), "cudaEventRecord");
+    if (!st) st = set_cuda_error(ctx, cudaStreamWaitEvent(fs, ev, 0), "cudaStreamWaitEvent");
+    if (!st) st = set_cuda_error(ctx, cudaMemcpyAsync(ctl, &hc, sizeof(FlowCtl), cudaMemcpyHostToDevice, fs),
+                                 "cudaMemcpyAsync(ctl)");
+    // d_t y at t0
+    if (!st) {
+      stage({}, 0.0, 0);
+      st = launch_rhs(ctx, pl, a, precision, fs);
+    }
+    if (!st) abm_deriv_kernel<<<eg, eb, 0, fs>>>(f, F);
+    // starting steps: classical RK4 with k1 = F[0]
+    for (long long m = 0; m < n_rk && !st; ++m) {
+      stage({{F, 0.5}}, 0.5, 0);
+      st = launch_rhs(ctx, pl, a, precision, fs);
+      abm_deriv_kernel<<<eg, eb, 0, fs>>>(f, K2);
+      if (!st) {
+        stage({{K2, 0.5}}, 0.5, 0);
+        st = launch_rhs(ctx, pl, a, precision, fs);
+        abm_deriv_kernel<<<eg, eb, 0, fs>>>(f, K3);
+      }
+      if (!st) {
+        stage({{K3, 1.0}}, 1.0, 0);
+        st = launch_rhs(ctx, pl, a, precision, fs);
+        abm_deriv_kernel<<<eg, eb, 0, fs>>>(f, K4);
+      }
+      if (!st) {
+        stage({{F, 1.0 / 6.0}, {K2, 1.0 / 3.0}, {K3, 1.0 / 3.0}, {K4, 1.0 / 6.0}}, 1.0, 1);
+        st = launch_rhs(ctx, pl, a, precision, fs);
+        abm_push_kernel<<<eg, eb, 0, fs>>>(f, F, order, h);
+      }
+    }
+    if (!st) st = set_cuda_error(ctx, cudaGetLastError(), "abm start");
+    // the persistent grids are known before capture (no attribute calls inside)
+    if (!st) st = set_cuda_error(ctx, cudaStreamSynchronize(fs), "abm start sync");
+  }
+  if (!st && n_steps > n_rk) {
+    // capture one PECE step
+    st = set_cuda_error(ctx, cudaStreamBeginCapture(fs, cudaStreamCaptureModeThreadLocal), "BeginCapture");
+    if (!st) {
+      AbmCombo pc, cc;
+      memset(&pc, 0, sizeof(pc));
+      memset(&cc, 0, sizeof(cc));
+      for (int j = 0; j < order; ++j) {
+        pc.src[j] = F + (size_t)j * ny;
+        pc.c[j] = kAbmB[order][j];
+      }
+      pc.n = order;
+      cc.src[0] = K2;
+      cc.c[0] = kAbmA[order][0];
+      for (int j = 1; j < order; ++j) {
+        cc.src[j] = F + (size_t)(j - 1) * ny;
+        cc.c[j] = kAbmA[order][j];
+      }
+      cc.n = order;
+      int cst = FFRG_OK;
+      abm_stage_kernel<<<eg, eb, 0, fs>>>(f, pc, h, 1.0, 0);
+      cst = launch_rhs(ctx, pl, a, precision, fs);
+      abm_deriv_kernel<<<eg, eb, 0, fs>>>(f, K2);
+      abm_stage_kernel<<<eg, eb, 0, fs>>>(f, cc, h, 1.0, 1);
+      if (!cst) cst = launch_rhs(ctx, pl, a, precision, fs);
+      abm_push_kernel<<<eg, eb, 0, fs>>>(f, F, order, h);
+      cudaError_t ce = cudaStreamEndCapture(fs, &graph);
+      st = cst ? cst : set_cuda_error(ctx, ce, "EndCapture");
+    }
+    if (!st) st = set_cuda_error(ctx, cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate");
+    for (long long m = n_rk; m < n_steps && !st; ++m)
+      st = set_cuda_error(ctx, cudaGraphLaunch(exec, fs), "cudaGraphLaunch");
+  }
+  if (!st) st = set_cuda_error(ctx, cudaMemcpyAsync(ctl_host, ctl, sizeof(FlowCtl), cudaMemcpyDeviceToHost, fs),
+                               "cudaMemcpyAsync(ctl)");
+  if (!st) st = set_cuda_error(ctx, cudaStreamSynchronize(fs), "abm sync");
+  if (!st) {
+    if (stats) {
+      stats->steps = n_steps;
+      stats->rejects = 0;
+      stats->rhs_evals = 1 + 4 * n_rk + 2 * (n_steps - n_rk);
+      stats->integrand_evals = (double)stats->rhs_evals * ffrg_evals(&pb);
+      stats->t_reached = ctl_host->t;
+      stats->jac_evals = 0;
+    }
+    st = ctl_host->status;
+    if (cudaEventRecord(ev, fs) == cudaSuccess) cudaStreamWaitEvent(user, ev, 0);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (fs) cudaStreamSynchronize(fs);
+  if (ev) cudaEventDestroy(ev);
+  if (fs) cudaStreamDestroy(fs);
+  if (ctl_host) cudaFreeHost(ctl_host);
+  dev_free(ctx, ctl, sizeof(FlowCtl));
+  dev_free(ctx, ys, (size_t)ny * d);
+  dev_free(ctx, F, (size_t)order * ny * d);
+  dev_free(ctx, S, (size_t)3 * ny * d);
+  dev_free(ctx, raw, (size_t)pl->n_ext * d);
+  dev_free(ctx, tabbuf, tab_bytes);
+  return st;
+}

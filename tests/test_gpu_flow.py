@@ -143,3 +143,71 @@ def test_flow_rejects_bad_options(ctx):
     wl3.feedback = 1
     with pytest.raises(ffrg.FfrgError):
         _gpu_flow(ctx, wl3, ffrg.FP64)
+
+
+# ----------------------------------------------------------------------------- Adams-Bashforth-Moulton
+def _gpu_abm(ctx, wl, n, order, precision, t1):
+    import torch
+    tabs = ctx.tables(wl.problem, wl.tables)
+    y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+    st = ctx.abm_flow(wl.problem, tabs, y, wl.Lambda, t1, n, order=order, feedback=wl.feedback, precision=precision)
+    tabs.free()
+    return y.cpu().numpy(), st
+
+
+ABM_CASES = {
+    "d3_frozen": (lambda: fi.make_d3(seed=21, n_pts=16, n_ext_p=9, n_rad=12, n_ang=6), None),
+    "d3_feedback": (lambda: fi.make_d3(seed=22, n_pts=12, n_ext_p=12, n_rad=10, n_ang=6, feedback=1, x_min=0.05), 3.0),
+    "d4_feedback": (lambda: fi.make_d4(seed=23, n_pts=8, n_ext_ang=2, n_rad=8, n_ang1=4, n_ang2=3), 2.0),
+    "ft_fermionic": (lambda: fi.make_finite_t(seed=24, N=2, T=0.3, n_pts=12, n_ext_p=3, n_ext_m=3, n_rad=8, n_ang=4,
+                                              fermionic=True), None),
+}
+
+
+@pytest.mark.parametrize("name", list(ABM_CASES))
+@pytest.mark.parametrize("order", [2, 4, 5])
+def test_abm_flow_matches_oracle_abm(ctx, name, order):
+    """Same fixed-step PECE method on both sides: the endpoints differ only by
+    RHS rounding (FP64), and by the stated mixed bound (mixed)."""
+    import paper_2412_13043_gb300 as ffrg
+    make, t1 = ABM_CASES[name]
+    wl = make()
+    if name == "d4_feedback":
+        wl.problem.p_min = wl.problem.x_min = 0.05
+    t1 = math.log(wl.Lambda / wl.k_end) if t1 is None else t1
+    n = 60
+    ref, so = oracle.abm_flow(wl.problem, wl.tables, wl.y0, wl.Lambda, t1, n, order=order, feedback=wl.feedback)
+    y, st = _gpu_abm(ctx, wl, n, order, ffrg.FP64, t1)
+    assert st["status"] == ffrg.OK and st["rhs_evals"] == so["rhs_evals"]
+    assert abs(st["t_reached"] - t1) < 1e-12 * max(1.0, t1)
+    assert np.max(np.abs(y - ref) / np.abs(ref)) < 1e-10
+    if order == 4:
+        ym, _ = _gpu_abm(ctx, wl, n, order, ffrg.MIXED, t1)
+        tol = MIXED_FEEDBACK_ENDPOINT_TOL if name == "d4_feedback" else MIXED_ENDPOINT_TOL
+        assert np.max(np.abs(ym - ref) / np.abs(ref)) < tol
+
+
+def test_abm_flow_fourth_order_against_dp45_truth(ctx):
+    import paper_2412_13043_gb300 as ffrg
+    wl = ABM_CASES["d3_frozen"][0]()
+    t1 = math.log(wl.Lambda / wl.k_end)
+    truth, _ = oracle.flow(wl.problem, wl.tables, wl.y0, wl.Lambda, t1, rtol=1e-13, atol=1e-16)
+    errs = []
+    for n in (60, 120, 240):
+        y, _ = _gpu_abm(ctx, wl, n, 4, ffrg.FP64, t1)
+        errs.append(np.max(np.abs(y - truth) / np.abs(truth)))
+    assert errs[0] / errs[1] > 10 and errs[1] / errs[2] > 12, errs
+    assert errs[2] < 1e-8
+
+
+def test_abm_flow_rejects_bad_arguments(ctx):
+    import torch
+
+    import paper_2412_13043_gb300 as ffrg
+    wl = ABM_CASES["d3_frozen"][0]()
+    tabs = ctx.tables(wl.problem, wl.tables)
+    y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+    for order, n in ((1, 10), (6, 10), (4, 0)):
+        with pytest.raises(ffrg.FfrgError):
+            ctx.abm_flow(wl.problem, tabs, y, wl.Lambda, 1.0, n, order=order)
+    tabs.free()
