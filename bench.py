@@ -133,18 +133,31 @@ def measured_peaks():
     return {}
 
 
-def cpu_baseline(wl, stride: int):
-    """The CPU oracle, as it stands, on every `stride`-th external point."""
+def cpu_baseline(wl, stride: int, stride_1t: int = 32):
+    """The CPU oracle, as it stands, on every `stride`-th external point with
+    all host threads (OpenMP over external points), and on every
+    `stride_1t`-th point with one thread."""
     import oracle
     pb = wl.problem
-    sel = list(range(0, pb.n_ext(), stride))
-    t = time.perf_counter()
-    oracle.rhs_subset(pb, wl.tables, 1.0, sel)
-    dt = time.perf_counter() - t
-    ev = len(sel) * pb.n_nodes()
-    return {"value": ev / dt, "unit": "integrand evals/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{len(sel)} of {pb.n_ext()} external points (every {stride}th) of the d4 RHS at k=1, "
-                      f"{ev:.3g} evals, {dt:.2f} s wall"}
+
+    def timed(step):
+        sel = list(range(0, pb.n_ext(), step))
+        t = time.perf_counter()
+        oracle.rhs_subset(pb, wl.tables, 1.0, sel)
+        dt = time.perf_counter() - t
+        ev = len(sel) * pb.n_nodes()
+        return ev / dt, f"{len(sel)} of {pb.n_ext()} external points (every {step}th) of the d4 RHS at k=1, " \
+                        f"{ev:.3g} evals, {dt:.2f} s wall"
+
+    cores = oracle.num_threads()
+    v, sample = timed(stride)
+    oracle.set_threads(1)
+    try:
+        v1, sample1 = timed(stride_1t)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": v, "unit": "integrand evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "single_thread": {"value": v1, "unit": "integrand evals/s", "cores": 1, "sample": sample1}}
 
 
 def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
@@ -522,7 +535,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(wl, stride=4)
+        cpu = cpu_baseline(wl, stride=1)
 
     if rank == 0:
         line = {
