@@ -28,6 +28,7 @@ MASK64 = (1 << 64) - 1
 MODEL_D3 = 1          # d=3, T=0 scalar two-point flow
 MODEL_D4_VERTEX = 2   # d=4, three coupled dressing tables (Z, lambda3, lambda4)
 MODEL_FINITE_T = 3    # d=3 spatial + Matsubara sum (bosonic or fermionic loop)
+MODEL_D4_FULL = 4     # d=4 with the three-point vertex on (S0, two shape variables)
 
 REG_EXP = 0
 REG_LITIM = 1
@@ -82,11 +83,14 @@ class Problem:
     x_max: float = 10.0
     # finite T: loop frequencies bosonic (STAT_BOSE) or fermionic (STAT_FERMI)
     statistics: int = 0
+    # D4_FULL: three-point vertex nodes in its two shape variables (n_stack = n_va n_vb)
+    n_va: int = 1
+    n_vb: int = 1
 
     def n_ext(self) -> int:
         if self.model == MODEL_D3:
             return self.n_ext_p + (1 if self.include_p0 else 0)
-        if self.model == MODEL_D4_VERTEX:
+        if self.model in (MODEL_D4_VERTEX, MODEL_D4_FULL):
             return 2 * self.n_ext_p + 1 + self.n_ext_p * self.n_ext_ang
         if self.model == MODEL_FINITE_T:
             return self.n_ext_p * self.n_ext_ang
@@ -94,7 +98,7 @@ class Problem:
 
     def n_nodes(self) -> int:
         n = self.n_rad * self.n_ang1
-        if self.model == MODEL_D4_VERTEX:
+        if self.model in (MODEL_D4_VERTEX, MODEL_D4_FULL):
             n *= self.n_ang2
         if self.model == MODEL_FINITE_T:
             n *= 2 * self.n_matsubara + 1 + (1 if self.statistics == STAT_FERMI else 0)
@@ -179,6 +183,42 @@ def make_d4(seed: int = 2, n_pts: int = 128, n_ext_ang: int = 8, n_rad: int = 12
     y0 = tables.reshape(-1).copy()
     return Workload(pb, tables, y0, Lambda, k_end, 1, seed,
                     dict(a=a, b=b, g3=g3, c3=c3, b3=b3, g4=g4, c4=c4, b4=b4))
+
+
+def make_d4_full(seed: int = 7, n_pts: int = 96, n_va: int = 8, n_vb: int = 7, n_ext_ang: int = 8,
+                 n_rad: int = 128, n_ang1: int = 64, n_ang2: int = 16, Lambda: float = 10.0, k_end: float = 0.01,
+                 M2: float = 1.0, regulator: int = REG_EXP) -> Workload:
+    """d=4 vertex expansion with the three-point vertex on (S0, a, b): a 96 x 8 x 7 grid by default
+    (log S0 x uniform a, b in [-1, 1]); lambda3 = g3 (1 + c3 exp(-S^2/b3)) (1 + ea a + eb b + eab a b).
+    Tables [3][n_va n_vb][n_pts]: Z and lambda4 in row 0 of tables 0 and 2 (other rows zero),
+    lambda3 in row ia n_vb + ib of table 1.  Frozen-background flow state (ones)."""
+    rng = SplitMix64(seed)
+    a = rng.uniform(0.0, 0.2)
+    b = rng.uniform(0.5, 2.0)
+    g3 = rng.uniform(0.5, 1.5)
+    c3 = rng.uniform(-0.3, 0.3)
+    b3 = rng.uniform(0.5, 2.0)
+    g4 = rng.uniform(0.5, 1.5)
+    c4 = rng.uniform(-0.3, 0.3)
+    b4 = rng.uniform(0.5, 2.0)
+    ea, eb, eab = rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), rng.uniform(-0.1, 0.1)
+    n_stack = n_va * n_vb
+    pb = Problem(model=MODEL_D4_FULL, n_rad=n_rad, n_ang1=n_ang1, n_ang2=n_ang2, n_ext_p=n_pts,
+                 n_ext_ang=n_ext_ang, regulator=regulator, m2_over_k2=0.5, m2_shift=M2,
+                 n_tables=3, n_pts=n_pts, n_stack=n_stack, n_va=n_va, n_vb=n_vb)
+    xs = log_grid(n_pts, pb.x_min, pb.x_max)
+    x2 = xs ** 2
+    av = np.linspace(-1.0, 1.0, n_va) if n_va > 1 else np.zeros(1)
+    bv = np.linspace(-1.0, 1.0, n_vb) if n_vb > 1 else np.zeros(1)
+    tables = np.zeros((3, n_stack, n_pts))
+    tables[0, 0] = _bump(x2, a, b)
+    tables[2, 0] = g4 * _bump(x2, c4, b4)
+    for ia in range(n_va):
+        for ib in range(n_vb):
+            tables[1, ia * n_vb + ib] = g3 * _bump(x2, c3, b3) * (1 + ea * av[ia] + eb * bv[ib] + eab * av[ia] * bv[ib])
+    y0 = np.ones(pb.n_ext())
+    return Workload(pb, tables, y0, Lambda, k_end, 0, seed,
+                    dict(a=a, b=b, g3=g3, c3=c3, b3=b3, g4=g4, c4=c4, b4=b4, ea=ea, eb=eb, eab=eab))
 
 
 def make_finite_t(seed: int = 3, N: int = 16, T: float = 0.002, n_pts: int = 64, n_ext_p: int = 64,

@@ -43,7 +43,7 @@ class _Problem(ctypes.Structure):
         ("n_ext_p", ctypes.c_int), ("n_ext_ang", ctypes.c_int), ("n_matsubara", ctypes.c_int),
         ("include_p0", ctypes.c_int),
         ("n_tables", ctypes.c_int), ("n_pts", ctypes.c_int), ("n_stack", ctypes.c_int),
-        ("statistics", ctypes.c_int),
+        ("statistics", ctypes.c_int), ("n_va", ctypes.c_int), ("n_vb", ctypes.c_int),
         ("m2_over_k2", ctypes.c_double), ("m2_shift", ctypes.c_double), ("lam", ctypes.c_double),
         ("T", ctypes.c_double), ("p_min", ctypes.c_double), ("p_max", ctypes.c_double),
         ("qmax_over_k", ctypes.c_double), ("prefactor", ctypes.c_double),
@@ -105,6 +105,10 @@ def _load():
         lib.orc_ros2_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
         lib.orc_ros2_flow.argtypes = [pp, D, dp, P(_StepOpts), P(_Stats)]
         lib.orc_abm_textbook.argtypes = [I, I, D, D, ctypes.c_long, dp, P(ctypes.c_long)]
+        lib.orc_lam3_full.argtypes = [pp, dp, D, D, D]
+        lib.orc_lam3_full.restype = D
+        lib.orc_d4_shape.argtypes = [D, D, D, I]
+        lib.orc_d4_shape.restype = D
         lib.orc_abm_flow.argtypes = [pp, dp, I, D, dp, D, D, ctypes.c_long, I, P(_Stats)]
         lib.orc_flow_state_size.argtypes = [pp, I]
         lib.orc_d3_summand.argtypes = [pp, dp, D, D, D]
@@ -273,6 +277,17 @@ def ros2_textbook(which: int, y0, t1: float, dt0: float = 0.1, dt_min: float = 1
     st = _Stats()
     code = _load().orc_ros2_textbook(int(which), _ptr(y), ctypes.byref(o), ctypes.byref(st))
     return y, dict(steps=st.steps, rejects=st.rejects, jacobians=st.rhs_evals, status=code)
+
+
+def lam3_full(pb, tables, s1: float, s2: float, s3: float) -> float:
+    """lambda3 of the D4_FULL model at a vertex with squared leg magnitudes s1, s2, s3."""
+    return _load().orc_lam3_full(ctypes.byref(_problem(pb)), _ptr(_f64(tables)), s1, s2, s3)
+
+
+def d4_shape(s1: float, s2: float, s3: float):
+    """(a, b) shape variables of a vertex with squared leg magnitudes s1, s2, s3."""
+    lib = _load()
+    return lib.orc_d4_shape(s1, s2, s3, 0), lib.orc_d4_shape(s1, s2, s3, 1)
 
 
 def abm_textbook(which: int, order: int, y0, t1: float, n: int, t0: float = 0.0):

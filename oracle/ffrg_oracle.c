@@ -40,6 +40,7 @@
 #define ORC_D3 1
 #define ORC_D4_VERTEX 2
 #define ORC_FINITE_T 3
+#define ORC_D4_FULL 4
 
 #define ORC_REG_EXP 0
 #define ORC_REG_LITIM 1
@@ -53,6 +54,7 @@ typedef struct {
   int n_ext_p, n_ext_ang, n_matsubara, include_p0;
   int n_tables, n_pts, n_stack;
   int statistics; /* finite T: 0 bosonic loop frequencies, 1 fermionic */
+  int n_va, n_vb; /* D4_FULL: nodes of the three-point vertex in its two shape variables */
   double m2_over_k2, m2_shift, lam, T;
   double p_min, p_max, qmax_over_k, prefactor;
   double x_min, x_max;
@@ -246,7 +248,8 @@ static double m2_of(const orc_problem *pb, double k) { return pb->m2_over_k2 * k
 int orc_n_ext(const orc_problem *pb) {
   switch (pb->model) {
   case ORC_D3: return pb->n_ext_p + (pb->include_p0 ? 1 : 0);
-  case ORC_D4_VERTEX: return 2 * pb->n_ext_p + 1 + pb->n_ext_p * pb->n_ext_ang;
+  case ORC_D4_VERTEX:
+  case ORC_D4_FULL: return 2 * pb->n_ext_p + 1 + pb->n_ext_p * pb->n_ext_ang;
   case ORC_FINITE_T: return pb->n_ext_p * pb->n_ext_ang;
   default: return -1;
   }
@@ -254,7 +257,10 @@ int orc_n_ext(const orc_problem *pb) {
 
 static int check_problem(const orc_problem *pb) {
   if (!pb) return ORC_EINVAL;
-  if (pb->model < ORC_D3 || pb->model > ORC_FINITE_T) return ORC_EINVAL;
+  if (pb->model < ORC_D3 || pb->model > ORC_D4_FULL) return ORC_EINVAL;
+  if (pb->model == ORC_D4_FULL && (pb->n_va < 1 || pb->n_vb < 1 || pb->n_stack != pb->n_va * pb->n_vb ||
+                                   pb->n_ang2 < 1 || pb->n_ext_ang < 1 || pb->n_tables < 3))
+    return ORC_EINVAL;
   if (pb->n_rad < 1 || pb->n_ang1 < 1 || pb->n_ext_p < 1 || pb->n_pts < 2) return ORC_EINVAL;
   if (pb->model == ORC_D4_VERTEX && (pb->n_ang2 < 1 || pb->n_ext_ang < 1 || pb->n_tables < 3)) return ORC_EINVAL;
   if (pb->model == ORC_FINITE_T && (pb->n_ext_ang < 1 || pb->n_matsubara < 0 || pb->n_tables < 2 || pb->n_stack < 1))
@@ -360,15 +366,69 @@ static int rhs_d3(const orc_problem *pb, const double *tab, const double *dtab, 
 
 /* Propagator-flow diagrams:  dR G(q)^2 [ -1/2 lambda4(S0(q,-q,p,-p))
  *                                        + lambda3(S0(q,q+p,p))^2 G(|q+p|) ]   */
+/* D4_FULL: three-point vertex lambda3(S0, a, b) on the log grid in S0 times
+ * uniform grids of n_va and n_vb nodes on [-1, 1] in its shape variables,
+ * stored as stack rows ia * n_vb + ib of table 1 (the "Full" vertex
+ * dependence of Sec. 3.3 and the 3-D interpolators of App. F).  For a vertex
+ * with legs k1, k2, k3 (k1 + k2 + k3 = 0) and squared magnitudes s1, s2, s3:
+ *   S0^2 = (s1 + s2 + s3)/3,
+ *   a = k1.k2/(|k1||k2|) = (s3 - s1 - s2)/(2 sqrt(s1 s2)),
+ *   b = (s1 - s2)/(s1 + s2),
+ * each of a, b clamped to [-1, 1] (NaN to -1); linear in the value between
+ * nodes in ln S0, a and b (trilinear), clamped at the grid ends. */
+static double clamp_shape(double v) { return v >= -1.0 ? (v <= 1.0 ? v : 1.0) : -1.0; }
+
+static void shape_pos(double v, int m, int *i0, double *w) {
+  if (m < 2) {
+    *i0 = 0;
+    *w = 0.0;
+    return;
+  }
+  double u = 0.5 * (v + 1.0) * (m - 1);
+  int i = (int)u;
+  if (i > m - 2) i = m - 2;
+  *i0 = i;
+  *w = u - i;
+}
+
+double orc_d4_shape(double s1, double s2, double s3, int which) {
+  if (which == 0) return clamp_shape((s3 - s1 - s2) / (2.0 * sqrt(s1 * s2)));
+  return clamp_shape((s1 - s2) / (s1 + s2));
+}
+
+double orc_lam3_full(const orc_problem *pb, const double *tab, double s1, double s2, double s3) {
+  const int n = pb->n_pts, na = pb->n_va, nb = pb->n_vb;
+  const double S = sqrt((s1 + s2 + s3) / 3.0);
+  int ia, ib;
+  double wa, wb;
+  shape_pos(orc_d4_shape(s1, s2, s3, 0), na, &ia, &wa);
+  shape_pos(orc_d4_shape(s1, s2, s3, 1), nb, &ib, &wb);
+  const int da = na > 1 ? nb : 0, db = nb > 1 ? 1 : 0;
+  const double *L3 = tab + (size_t)pb->n_stack * n;
+  const int r = ia * nb + ib;
+  double v00 = orc_lerp_log(L3 + (size_t)r * n, n, pb->x_min, pb->x_max, S);
+  double v01 = orc_lerp_log(L3 + (size_t)(r + db) * n, n, pb->x_min, pb->x_max, S);
+  double v10 = orc_lerp_log(L3 + (size_t)(r + da) * n, n, pb->x_min, pb->x_max, S);
+  double v11 = orc_lerp_log(L3 + (size_t)(r + da + db) * n, n, pb->x_min, pb->x_max, S);
+  return (1.0 - wa) * ((1.0 - wb) * v00 + wb * v01) + wa * ((1.0 - wb) * v10 + wb * v11);
+}
+
+/* lambda3 at the vertex with legs of squared magnitudes s1, s2, s3 */
+static double lam3_at(const orc_problem *pb, const double *tab, double s1, double s2, double s3) {
+  if (pb->model == ORC_D4_FULL) return orc_lam3_full(pb, tab, s1, s2, s3);
+  return orc_lerp_log(tab + (size_t)pb->n_stack * pb->n_pts, pb->n_pts, pb->x_min, pb->x_max,
+                      sqrt((s1 + s2 + s3) / 3.0));
+}
+
 double orc_d4_summand_z(const orc_problem *pb, const double *tab, double k, double q2, double p2, double A2) {
   int n = pb->n_pts, reg = pb->regulator;
-  const double *Zt = tab, *L3 = tab + n, *L4 = tab + 2 * n;
+  const double *Zt = tab, *L4 = tab + (size_t)2 * pb->n_stack * n;
   double k2 = k * k, m2 = m2_of(pb, k);
   if (A2 < 0.0) A2 = 0.0;
   double Zq = orc_lerp_log(Zt, n, pb->x_min, pb->x_max, sqrt(q2));
   double ZA = orc_lerp_log(Zt, n, pb->x_min, pb->x_max, sqrt(A2));
   double l4 = orc_lerp_log(L4, n, pb->x_min, pb->x_max, sqrt((2.0 * q2 + 2.0 * p2) / 4.0));
-  double l3 = orc_lerp_log(L3, n, pb->x_min, pb->x_max, sqrt((q2 + A2 + p2) / 3.0));
+  double l3 = lam3_at(pb, tab, q2, A2, p2);   /* legs q, q+p, p */
   double dR = Zq * k2 * orc_reg_rdot(reg, q2 / k2);
   double Gq = propagator(reg, Zq, 0.0, q2, m2, k);
   double GA = propagator(reg, ZA, 0.0, A2, m2, k);
@@ -380,16 +440,16 @@ double orc_d4_summand_z(const orc_problem *pb, const double *tab, double k, doub
 double orc_d4_summand_3(const orc_problem *pb, const double *tab, double k, double q2, double p2, double A2,
                         double B2, double C2) {
   int n = pb->n_pts, reg = pb->regulator;
-  const double *Zt = tab, *L3 = tab + n;
+  const double *Zt = tab;
   double k2 = k * k, m2 = m2_of(pb, k);
   if (A2 < 0.0) A2 = 0.0;
   if (B2 < 0.0) B2 = 0.0;
   double Zq = orc_lerp_log(Zt, n, pb->x_min, pb->x_max, sqrt(q2));
   double ZA = orc_lerp_log(Zt, n, pb->x_min, pb->x_max, sqrt(A2));
   double ZB = orc_lerp_log(Zt, n, pb->x_min, pb->x_max, sqrt(B2));
-  double la = orc_lerp_log(L3, n, pb->x_min, pb->x_max, sqrt((q2 + A2 + p2) / 3.0));
-  double lb = orc_lerp_log(L3, n, pb->x_min, pb->x_max, sqrt((q2 + B2 + p2) / 3.0));
-  double lc = orc_lerp_log(L3, n, pb->x_min, pb->x_max, sqrt((A2 + B2 + C2) / 3.0));
+  double la = lam3_at(pb, tab, q2, A2, p2);   /* legs q, q+p1, p1 */
+  double lb = lam3_at(pb, tab, q2, B2, p2);   /* legs q, q-p2, p2 */
+  double lc = lam3_at(pb, tab, A2, B2, C2);   /* legs q+p1, q-p2, p1+p2 */
   double dR = Zq * k2 * orc_reg_rdot(reg, q2 / k2);
   double Gq = propagator(reg, Zq, 0.0, q2, m2, k);
   double GA = propagator(reg, ZA, 0.0, A2, m2, k);
@@ -400,7 +460,7 @@ double orc_d4_summand_3(const orc_problem *pb, const double *tab, double k, doub
 /* Four-point-vertex flow:  3/2 dR G(q)^2 G(|q+p|) lambda4(S0(q,q+p,p,p))^2 */
 double orc_d4_summand_4(const orc_problem *pb, const double *tab, double k, double q2, double p2, double A2) {
   int n = pb->n_pts, reg = pb->regulator;
-  const double *Zt = tab, *L4 = tab + 2 * n;
+  const double *Zt = tab, *L4 = tab + (size_t)2 * pb->n_stack * n;
   double k2 = k * k, m2 = m2_of(pb, k);
   if (A2 < 0.0) A2 = 0.0;
   double Zq = orc_lerp_log(Zt, n, pb->x_min, pb->x_max, sqrt(q2));
@@ -596,7 +656,8 @@ int orc_rhs(const orc_problem *pb, const double *tables, double k, double *out) 
   if (!(k > 0.0) || !tables || !out) return ORC_EINVAL;
   switch (pb->model) {
   case ORC_D3: return rhs_d3(pb, tables, NULL, k, out, NULL, NULL, 0);
-  case ORC_D4_VERTEX: return rhs_d4(pb, tables, NULL, k, out, NULL, NULL, 0);
+  case ORC_D4_VERTEX:
+  case ORC_D4_FULL: return rhs_d4(pb, tables, NULL, k, out, NULL, NULL, 0);
   case ORC_FINITE_T: return rhs_ft(pb, tables, k, out, NULL, 0);
   }
   return ORC_EINVAL;
@@ -613,7 +674,8 @@ int orc_rhs_subset(const orc_problem *pb, const double *tables, double k, const 
     if (sel[i] < 0 || sel[i] >= ne) return ORC_EINVAL;
   switch (pb->model) {
   case ORC_D3: return rhs_d3(pb, tables, NULL, k, out, NULL, sel, nsel);
-  case ORC_D4_VERTEX: return rhs_d4(pb, tables, NULL, k, out, NULL, sel, nsel);
+  case ORC_D4_VERTEX:
+  case ORC_D4_FULL: return rhs_d4(pb, tables, NULL, k, out, NULL, sel, nsel);
   case ORC_FINITE_T: return rhs_ft(pb, tables, k, out, sel, nsel);
   }
   return ORC_EINVAL;

@@ -7,6 +7,7 @@ functions), an invariant (rotations of the external momenta) or brute force
 (Monte Carlo in the loop-momentum ball).  Citations give the paper section
 that defines the piece being pinned.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -713,3 +714,56 @@ def test_abm_flow_matches_dp45_flow():
         errs.append(np.max(np.abs(y - ref) / np.abs(ref)))
         assert st["rhs_evals"] == 1 + 4 * 3 + 2 * (n - 3)
     assert errs[1] < 1e-6 and errs[0] / errs[1] > 8      # fourth order
+
+
+# --------------------------------------------------------------------------
+# d=4 with the three-point vertex on (S0, a, b) ("Full" vertex dependence)
+# --------------------------------------------------------------------------
+def test_d4_full_reduces_to_d4_vertex_for_angle_independent_vertex():
+    """With lambda3 rows equal in (a, b) the full model is the vertex model."""
+    wl = fi.make_d4(seed=31, n_pts=12, n_ext_ang=3, n_rad=7, n_ang1=5, n_ang2=4)
+    ref = oracle.rhs(wl.problem, wl.tables, 0.9)
+    na, nb = 3, 4
+    pf = dataclasses.replace(wl.problem, model=fi.MODEL_D4_FULL, n_stack=na * nb, n_va=na, n_vb=nb)
+    tf = np.zeros((3, na * nb, pf.n_pts))
+    tf[0, 0], tf[2, 0] = wl.tables[0, 0], wl.tables[2, 0]
+    tf[1, :] = wl.tables[1, 0]
+    out = oracle.rhs(pf, tf, 0.9)
+    assert np.max(np.abs(out - ref) / np.abs(ref)) < 1e-13
+
+
+def test_d4_full_trilinear_lookup_is_exact_on_trilinear_tables():
+    """Tables of f = c0 + c1 ln S + c2 a + c3 b + c4 a b + c5 a ln S are
+    reproduced exactly by the lookup (linear in ln S, a and b between nodes)."""
+    na, nb, n = 5, 4, 9
+    pb = fi.Problem(model=fi.MODEL_D4_FULL, n_rad=2, n_ang1=2, n_ang2=2, n_ext_p=n, n_ext_ang=1, n_tables=3,
+                    n_pts=n, n_stack=na * nb, n_va=na, n_vb=nb)
+    c = [0.7, 0.3, -0.2, 0.15, 0.05, 0.1]
+    f = lambda S, a, b: c[0] + c[1] * math.log(S) + c[2] * a + c[3] * b + c[4] * a * b + c[5] * a * math.log(S)
+    xs = fi.log_grid(n, pb.x_min, pb.x_max)
+    av, bv = np.linspace(-1, 1, na), np.linspace(-1, 1, nb)
+    tab = np.zeros((3, na * nb, n))
+    for ia in range(na):
+        for ib in range(nb):
+            tab[1, ia * nb + ib] = [f(x, av[ia], bv[ib]) for x in xs]
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        s1, s2, s3 = rng.uniform(0.01, 30.0, 3)
+        S = math.sqrt((s1 + s2 + s3) / 3)
+        if not (pb.x_min <= S <= pb.x_max):
+            continue
+        a, b = oracle.d4_shape(s1, s2, s3)
+        assert abs(oracle.lam3_full(pb, tab, s1, s2, s3) - f(S, a, b)) < 1e-13
+
+
+def test_d4_full_shape_variables_from_vectors():
+    """a is the cosine between legs 1 and 2, b = (k1^2 - k2^2)/(k1^2 + k2^2),
+    for random 4-vectors with k3 = -k1 - k2 (clamped to [-1, 1])."""
+    rng = np.random.default_rng(7)
+    for _ in range(100):
+        k1, k2 = rng.normal(size=4), rng.normal(size=4)
+        k3 = -k1 - k2
+        a, b = oracle.d4_shape(k1 @ k1, k2 @ k2, k3 @ k3)
+        assert abs(a - k1 @ k2 / math.sqrt((k1 @ k1) * (k2 @ k2))) < 1e-12
+        assert abs(b - (k1 @ k1 - k2 @ k2) / (k1 @ k1 + k2 @ k2)) < 1e-13
+    assert oracle.d4_shape(1.0, 1.0, 9.0)[0] == 1.0 and oracle.d4_shape(1.0, 1.0, -5.0)[0] == -1.0
