@@ -291,8 +291,9 @@ def stepper_bench(ctx):
 def model_bench(ctx, steps: int = 5):
     """Single-RHS throughput of the other model workloads, mixed and FP64:
     d=3 (64 ext x 64 x 32 nodes), finite T (64 |p| x 9 p0, 96 x 48 x (2N+1))
-    at N = 16/32/64 with T/k_end = 0.05/0.2/1, and the fermionic loop at
-    N = 16 (2N+2 frequencies).  step_ms: one ffrg_rhs (precompute + main);
+    at N = 16/32/64 with T/k_end = 0.05/0.2/1, the d=4 model with the
+    three-point vertex on a 96 x 8 x 7 (S0, a, b) grid, and the fermionic
+    loop at N = 16 (2N+2 frequencies).  step_ms: one ffrg_rhs (precompute + main);
     kernel_ms: the main kernel (profiling events); k = 1."""
     import numpy as np
     import torch
@@ -302,6 +303,8 @@ def model_bench(ctx, steps: int = 5):
     cases = [("d3, 64 ext x (64 x 32)", fi.make_d3(seed=1))]
     for N, tk in ((16, 0.05), (32, 0.2), (64, 1.0)):
         cases.append((f"finite T bosonic N={N}, T/k_end={tk}", fi.make_finite_t(seed=3, N=N, T=tk * 0.01)))
+    cases.append(("d4 full vertex: lambda3 on 96 x 8 x 7 (S0, a, b), 1281 ext x (128 x 64 x 16)",
+                  fi.make_d4_full()))
     cases.append(("finite T fermionic N=16, T/k_end=0.05",
                   fi.make_finite_t(seed=3, N=16, T=0.05 * 0.01, fermionic=True)))
     rows = []
@@ -329,6 +332,18 @@ def model_bench(ctx, steps: int = 5):
                           "evals_per_s": pb.evals() / (step_ms * 1e-3)}
             outs[pname] = out.cpu().numpy()
         row["mixed_vs_fp64_max_rel_err"] = float(np.max(np.abs(outs["mixed"] - outs["fp64"]) / np.abs(outs["fp64"])))
+        # d=4 models: the Z block (D2 = int dR G^2 [-lam4/2 + lam3^2 G]) can cross
+        # zero; its error is also given against |lam4 = 0 part| + |lam3 = 0 part|
+        if pb.model in (fi.MODEL_D4_VERTEX, fi.MODEL_D4_FULL):
+            n = pb.n_ext_p + 1
+            scale = np.abs(outs["fp64"]).copy()
+            scale[:n] = 0.0
+            for zero in (2, 1):
+                t = ctx.tables(pb, np.where(np.arange(3)[:, None, None] == zero, 0.0, wl.tables))
+                scale[:n] += np.abs(ctx.rhs(pb, t, 1.0, precision=ffrg.FP64).cpu().numpy()[:n])
+                t.free()
+            row["mixed_vs_fp64_max_err_termwise"] = float(np.max(np.abs(outs["mixed"] - outs["fp64"]) / scale))
+
         row["speedup_mixed_over_fp64"] = row["fp64"]["step_ms"] / row["mixed"]["step_ms"]
         rows.append(row)
         tabs.free()

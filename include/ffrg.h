@@ -79,7 +79,7 @@ typedef enum {
 
 typedef enum { FFRG_FP64 = 0, FFRG_MIXED = 1 } ffrg_precision;
 typedef enum { FFRG_RULE_GL = 0, FFRG_RULE_GC2 = 1 } ffrg_rule;
-typedef enum { FFRG_MODEL_D3 = 1, FFRG_MODEL_D4_VERTEX = 2, FFRG_MODEL_FINITE_T = 3 } ffrg_model;
+typedef enum { FFRG_MODEL_D3 = 1, FFRG_MODEL_D4_VERTEX = 2, FFRG_MODEL_FINITE_T = 3, FFRG_MODEL_D4_FULL = 4 } ffrg_model;
 typedef enum { FFRG_REG_EXP = 0, FFRG_REG_LITIM = 1 } ffrg_regulator;
 typedef enum { FFRG_STAT_BOSE = 0, FFRG_STAT_FERMI = 1 } ffrg_statistics;
 
@@ -92,6 +92,14 @@ typedef enum { FFRG_STAT_BOSE = 0, FFRG_STAT_FERMI = 1 } ffrg_statistics;
  *   D3:       [p_0 .. p_{n_ext_p-1}] then, if include_p0, the point p = 0
  *   D4:       [Z: p_0..p_{n-1}, p=0][lambda3: p_i x psi_j][lambda4: p_i],
  *             psi_j = n_ext_ang GL nodes in cos(psi) between the two legs
+ *   D4_FULL:  as D4; the three-point vertex is tabulated on (S0, a, b) (the
+ *             "Full" vertex dependence of Sec. 3.3): for a vertex with legs
+ *             k1, k2, k3 (sum 0), S0^2 = (k1^2+k2^2+k3^2)/3, a = cosine
+ *             between k1 and k2, b = (k1^2-k2^2)/(k1^2+k2^2); n_va x n_vb
+ *             uniform nodes on [-1, 1] in a and b, interpolated linearly in
+ *             ln S0, a and b.  Tables: n_tables = 3, n_stack = n_va n_vb;
+ *             Z and lambda4 in row 0 of tables 0 and 2 (other rows unused),
+ *             lambda3 at (a_i, b_j) in row i n_vb + j of table 1.
  *   FINITE_T: [p_i][m], m = 0..n_ext_ang-1 external bosonic frequencies
  *             p0_m = 2 pi T m; Matsubara sum of the loop over
  *             statistics FFRG_STAT_BOSE: omega_n = 2 pi T n, |n| <= n_matsubara
@@ -113,6 +121,7 @@ typedef struct {
   double p_min, p_max;         /* external log grid */
   double qmax_over_k;          /* radial domain [0, qmax_over_k k] */
   double prefactor;            /* overall multiplier */
+  int n_va, n_vb;              /* D4_FULL: vertex nodes in a and b (1 otherwise) */
 } ffrg_problem;
 
 /* Dressing tables values[table][stack][pt] (doubles, row-major) on the log grid

@@ -21,8 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libffrg.so")
  ECANCELED) = range(12)
 FP64, MIXED = 0, 1
 RULE_GL, RULE_GC2 = 0, 1
-MODEL_D3, MODEL_D4_VERTEX, MODEL_FINITE_T = 1, 2, 3
 REG_EXP, REG_LITIM = 0, 1
+MODEL_D3, MODEL_D4_VERTEX, MODEL_FINITE_T, MODEL_D4_FULL = 1, 2, 3, 4
 STAT_BOSE, STAT_FERMI = 0, 1
 
 
@@ -44,6 +44,7 @@ class Problem(ctypes.Structure):
         ("m2_over_k2", ctypes.c_double), ("m2_shift", ctypes.c_double), ("lam", ctypes.c_double),
         ("T", ctypes.c_double), ("p_min", ctypes.c_double), ("p_max", ctypes.c_double),
         ("qmax_over_k", ctypes.c_double), ("prefactor", ctypes.c_double),
+        ("n_va", ctypes.c_int), ("n_vb", ctypes.c_int),
     ]
 
 
@@ -163,7 +164,8 @@ def to_problem(pb) -> Problem:
     """Build the C struct from any object with the problem's attribute names."""
     c = Problem()
     for name, _ in Problem._fields_:
-        setattr(c, name, getattr(pb, name, 0) if name == "statistics" else getattr(pb, name))
+        default = {"statistics": 0, "n_va": 1, "n_vb": 1}
+        setattr(c, name, getattr(pb, name, default[name]) if name in default else getattr(pb, name))
     return c
 
 

@@ -122,7 +122,8 @@ int host_gauss_chebyshev2(int n, double *x, double *w) {
 static int tables_needed(int model) {
   switch (model) {
   case FFRG_MODEL_D3: return 1;
-  case FFRG_MODEL_D4_VERTEX: return 3;
+  case FFRG_MODEL_D4_VERTEX:
+  case FFRG_MODEL_D4_FULL: return 3;
   case FFRG_MODEL_FINITE_T: return 2;
   default: return -1;
   }
@@ -147,8 +148,13 @@ int validate_problem(const ffrg_problem *pb, const ffrg_table_desc *td) {
   if (!(pb->qmax_over_k > 0.0) || !isfinite(pb->qmax_over_k)) return FFRG_EINVAL;
   if (!isfinite(pb->m2_over_k2) || !isfinite(pb->m2_shift) || !isfinite(pb->lam) || !isfinite(pb->prefactor))
     return FFRG_EINVAL;
-  if (pb->model == FFRG_MODEL_D4_VERTEX) {
+  if (is_d4(pb->model)) {
     if (pb->n_ang2 < 1 || pb->n_ang2 > 1024 || pb->n_ext_ang < 1 || pb->n_ext_ang > 1024) return FFRG_EINVAL;
+  }
+  if (pb->model == FFRG_MODEL_D4_FULL) {
+    if (pb->n_va < 1 || pb->n_vb < 1 || pb->n_va > 64 || pb->n_vb > 64) return FFRG_EINVAL;
+  } else if (pb->n_va > 1 || pb->n_vb > 1) {
+    return FFRG_EINVAL;
   }
   if (pb->model == FFRG_MODEL_FINITE_T) {
     if (pb->n_ext_ang < 1 || pb->n_ext_ang > 1024 || pb->n_matsubara < 0 || pb->n_matsubara > 4096) return FFRG_EINVAL;
@@ -160,7 +166,11 @@ int validate_problem(const ffrg_problem *pb, const ffrg_table_desc *td) {
   if (td) {
     if (!desc_ok(td)) return FFRG_EINVAL;
     if (td->n_tables < need) return FFRG_EINVAL;
-    if (pb->model != FFRG_MODEL_FINITE_T && td->n_stack != 1) return FFRG_EINVAL;
+    if (pb->model == FFRG_MODEL_D4_FULL) {
+      if (td->n_stack != pb->n_va * pb->n_vb) return FFRG_EINVAL;
+    } else if (pb->model != FFRG_MODEL_FINITE_T && td->n_stack != 1) {
+      return FFRG_EINVAL;
+    }
   }
   if (ffrg_n_ext(pb) < 1) return FFRG_EINVAL;
   return FFRG_OK;
@@ -184,6 +194,7 @@ static void plan_free(ffrg_ctx *ctx, Plan *pl) {
   dev_free(ctx, pl->ext_done, 0);
   dev_free(ctx, pl->kconst, 0);
   dev_free(ctx, pl->radF32, 0);
+  dev_free(ctx, pl->tabc, 0);
   delete pl;
 }
 
@@ -196,7 +207,7 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   pl->model = pb->model;
   pl->nr = pb->n_rad;
   pl->na1 = pb->n_ang1;
-  pl->na2 = pb->model == FFRG_MODEL_D4_VERTEX ? pb->n_ang2 : 1;
+  pl->na2 = is_d4(pb->model) ? pb->n_ang2 : 1;
   pl->n_ext_ang = pb->n_ext_ang;
   pl->n_ext_p = pb->n_ext_p;
   pl->N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
@@ -210,9 +221,15 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   pl->tab_count = td->n_tables * td->n_stack * td->n_pts;
   // FP32 layout: (value, difference) node pairs; finite T: (Z, lambda) node
   // pairs per stack row plus one zero pair (same bytes as single values)
-  pl->tab32_count = pb->model == FFRG_MODEL_FINITE_T ? td->n_stack * td->n_pts + 1 : pl->tab_count;
+  // D4_FULL: compact [Z row 0 | lambda4 row 0 | lambda3 rows] in both precisions
+  pl->n_va = pb->model == FFRG_MODEL_D4_FULL ? pb->n_va : 1;
+  pl->n_vb = pb->model == FFRG_MODEL_D4_FULL ? pb->n_vb : 1;
+  pl->tabc_count = pb->model == FFRG_MODEL_D4_FULL ? (2 + pl->n_va * pl->n_vb) * td->n_pts : 0;
+  pl->tab32_count = pb->model == FFRG_MODEL_FINITE_T ? td->n_stack * td->n_pts + 1
+                    : pl->tabc_count                 ? pl->tabc_count
+                                                     : pl->tab_count;
   int outer_total, rows_per_outer;
-  if (pb->model == FFRG_MODEL_D4_VERTEX) {
+  if (is_d4(pb->model)) {
     pl->jb = pl->na2;
     outer_total = pl->nr;
     rows_per_outer = pl->na1;
@@ -237,7 +254,7 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   // angle rule into blocks of at least 4 nodes until there is a row per
   // resident lane: small FP64 problems are bound by each lane's FP64 chain.
   auto forward = [&](bool fp64, int &fcr, int &fn_chunks, int &fn_items, int &fjb) {
-    if (pb->model == FFRG_MODEL_D4_VERTEX) {
+    if (is_d4(pb->model)) {
       fjb = pl->na2;
       fcr = chunk(8 * 32);
       fn_chunks = (outer_total + fcr - 1) / fcr;
@@ -262,14 +279,16 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
   auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   const size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
-  pl->smem64 = al16((size_t)pl->tab_count * 8) + al16(ang * 8);
+  pl->smem64 = al16((size_t)(pl->tabc_count ? pl->tabc_count : pl->tab_count) * 8) + al16(ang * 8);
   pl->smem32 = al16((size_t)pl->tab32_count * 8) + al16(ang * 4);
 }
 
 int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {
   std::vector<long long> key = {pb->model, pb->n_rad, pb->n_ang1, pb->n_ang2, pb->n_ext_p, pb->n_ext_ang,
                                 pb->n_matsubara, pb->include_p0, td->n_tables, td->n_stack, td->n_pts,
-                                pb->model == FFRG_MODEL_FINITE_T ? pb->statistics : 0};
+                                pb->model == FFRG_MODEL_FINITE_T ? pb->statistics : 0,
+                                pb->model == FFRG_MODEL_D4_FULL ? pb->n_va : 1,
+                                pb->model == FFRG_MODEL_D4_FULL ? pb->n_vb : 1};
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     *out = it->second;
@@ -285,7 +304,7 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   st = st ? st : upload_rule(ctx, x, &pl->rad_x);
   st = st ? st : upload_rule(ctx, w, &pl->rad_w);
   std::vector<double> x1(pl->na1), w1(pl->na1);
-  if (pb->model == FFRG_MODEL_D4_VERTEX) host_gauss_chebyshev2(pl->na1, x1.data(), w1.data());
+  if (is_d4(pb->model)) host_gauss_chebyshev2(pl->na1, x1.data(), w1.data());
   else host_gauss_legendre(pl->na1, -1.0, 1.0, x1.data(), w1.data());
   st = st ? st : upload_rule(ctx, x1, &pl->a1_x);
   st = st ? st : upload_rule(ctx, w1, &pl->a1_w);
@@ -309,6 +328,7 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   if (!st) st = dev_alloc(ctx, (void **)&pl->work_ctr, sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_done, (size_t)pl->n_ext * sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->kconst, kKConstBytes);
+  if (!st && pl->tabc_count) st = dev_alloc(ctx, (void **)&pl->tabc, (size_t)pl->tabc_count * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
   if (!st)
@@ -347,6 +367,10 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.n_items = pl->fn_items;
   a.jb = pl->fjb;
   a.tab32_count = pl->tab32_count;
+  a.tabc_count = pl->tabc_count;
+  a.n_va = pl->n_va;
+  a.n_vb = pl->n_vb;
+  a.tabc = pl->tabc;
   a.k = k;
   a.m2_over_k2 = pb->m2_over_k2;
   a.m2_shift = pb->m2_shift;
@@ -357,7 +381,8 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   const double pi = kPi;
   switch (pb->model) {
   case FFRG_MODEL_D3: a.norm = pb->prefactor * pb->lam * pb->lam / (4.0 * pi * pi); break;
-  case FFRG_MODEL_D4_VERTEX: a.norm = pb->prefactor / (8.0 * pi * pi * pi); break;
+  case FFRG_MODEL_D4_VERTEX:
+  case FFRG_MODEL_D4_FULL: a.norm = pb->prefactor / (8.0 * pi * pi * pi); break;
   default: a.norm = pb->prefactor * pb->lam * pb->lam * pb->T / (4.0 * pi * pi); break;
   }
   double lr = log(td->x_max / td->x_min);
@@ -448,6 +473,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
     cudaFree(pl->ext_done);
     cudaFree(pl->kconst);
     cudaFree(pl->radF32);
+    cudaFree(pl->tabc);
     delete pl;
   }
   ctx->plans.clear();
@@ -519,6 +545,7 @@ int ffrg_n_ext(const ffrg_problem *pb) {
   if (!pb || pb->n_ext_p < 1) return -1;
   switch (pb->model) {
   case FFRG_MODEL_D3: return pb->n_ext_p + (pb->include_p0 ? 1 : 0);
+  case FFRG_MODEL_D4_FULL:
   case FFRG_MODEL_D4_VERTEX:
     if (pb->n_ext_ang < 1) return -1;
     return 2 * pb->n_ext_p + 1 + pb->n_ext_p * pb->n_ext_ang;
@@ -533,7 +560,7 @@ double ffrg_evals(const ffrg_problem *pb) {
   int ne = ffrg_n_ext(pb);
   if (ne < 0) return -1.0;
   double nodes = (double)pb->n_rad * pb->n_ang1;
-  if (pb->model == FFRG_MODEL_D4_VERTEX) nodes *= pb->n_ang2;
+  if (is_d4(pb->model)) nodes *= pb->n_ang2;
   if (pb->model == FFRG_MODEL_FINITE_T)
     nodes *= (2.0 * pb->n_matsubara + 1.0 + (pb->statistics == FFRG_STAT_FERMI ? 1.0 : 0.0));
   return (double)ne * nodes;

@@ -30,6 +30,11 @@ constexpr int kMaxNodes = 65536;
 // ---------------------------------------------------------------------------
 // Kernel argument block (passed by value).
 // ---------------------------------------------------------------------------
+// the two d=4 vertex-expansion models (1-D or 3-D three-point vertex)
+__host__ __device__ inline bool is_d4(int model) {
+  return model == FFRG_MODEL_D4_VERTEX || model == FFRG_MODEL_D4_FULL;
+}
+
 // bytes of the per-RHS constant block (FP32 and FP64 scale constants)
 constexpr int kKConstBytes = 256;
 
@@ -40,6 +45,8 @@ struct RhsArgs {
   int stat, nfreq;  // loop statistics (ffrg_statistics) and frequency rows: 2N+1 (bosonic), 2N+2 (fermionic)
   int n_tables, n_stack, n_pts, tab_count;
   int tab32_count; // float2 entries of the FP32 table layout
+  int tabc_count;  // D4_FULL: doubles of the compact FP64 tables (0 otherwise)
+  int n_va, n_vb;  // D4_FULL: vertex nodes in the shape variables a, b
   int cr;          // rows per work item (d=4: outer rows)
   int n_chunks;    // work items per external point
   int n_items;     // n_ext * n_chunks
@@ -57,6 +64,7 @@ struct RhsArgs {
   double x_min2;               // x_min^2 (lookups below x_min return the first node)
   double sum_w2;               // sum of the second-angle weights (D4)
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
+  double *tabc;                // D4_FULL: compact FP64 tables [Z row | lambda4 row | lambda3 rows] (precompute)
   float2 *tab32;               // FP32 node pairs (T[i], T[i+1] - T[i]; 0 at a row end), precompute kernel
   const double *rad_x, *rad_w; // unit-interval GL rule on [0, 1]
   const double *a1_x, *a1_w;   // first angle rule
@@ -344,6 +352,8 @@ struct Plan {
   int fjb;                        // angle nodes per forward row (D3 / FINITE_T)
   int fcr64, fn_chunks64, fn_items64, fjb64;  // the same for the FP64 forward kernels
   int tab32_count;                // float2 entries of the FP32 table layout
+  int tabc_count, n_va, n_vb;     // D4_FULL: compact FP64 table doubles, vertex nodes
+  double *tabc;
   int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
   size_t smem64, smem32;    // dynamic shared memory bytes
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;

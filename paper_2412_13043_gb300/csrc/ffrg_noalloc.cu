@@ -80,7 +80,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   int npsi = std::max(1, pl.n_ext_ang);
   std::vector<double> xp(npsi), wp(npsi);
   host_gauss_legendre(pl.nr, 0.0, 1.0, rx.data(), rw.data());
-  if (pb->model == FFRG_MODEL_D4_VERTEX) host_gauss_chebyshev2(pl.na1, x1.data(), w1.data());
+  if (is_d4(pb->model)) host_gauss_chebyshev2(pl.na1, x1.data(), w1.data());
   else host_gauss_legendre(pl.na1, -1.0, 1.0, x1.data(), w1.data());
   host_gauss_legendre(pl.na2, -1.0, 1.0, x2.data(), w2.data());
   host_gauss_legendre(npsi, -1.0, 1.0, xp.data(), wp.data());
@@ -109,6 +109,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.psi_s = sc.take<double>(npsi);
   pl.partial = sc.take<double>(std::max(pl.fn_items, pl.fn_items64));
   pl.tab32 = sc.take<float2>((size_t)pl.tab32_count);
+  if (pl.tabc_count) pl.tabc = sc.take<double>((size_t)pl.tabc_count);
   if (sc.used > kNoallocScratchBytes) return FFRG_EINVAL;  // problem needs more than the 4 MiB scratch
 
   const size_t smem = precision == FFRG_MIXED ? pl.smem32 : pl.smem64;

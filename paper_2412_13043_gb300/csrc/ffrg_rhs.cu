@@ -49,7 +49,10 @@ __device__ __noinline__ float pole_d3(const RhsArgs *a, int e, int r, int j) {
   return pole_prop(a, a->tab, q * q + p * p + 2.0 * q * p * c, 0.0);
 }
 
-// b < 0: the |q + p1| leg; b >= 0: the |q - p2| leg at second-angle node b
+// b < 0: the |q + p1| leg; b >= 0: the |q - p2| leg at second-angle node b.
+// One copy per d=4 model (M), so that the two kernels do not share an
+// out-of-line callee (sharing it cost the vertex-model kernel registers).
+template <int M>
 __device__ __noinline__ float pole_d4(const RhsArgs *a, int e, int r, int ia, int b) {
   const int np_ = a->n_ext_p, npsi = a->n_ext_ang;
   int ip, jp = 0;
@@ -99,6 +102,7 @@ template <typename T>
 struct KConst {
   T k2, inv_k2, m2, us, uo, plim, sy, som;
   T uy1, uy2, uy3, uy4, twopiT, sw2;
+  T isy;  // 1/sy
 };
 
 struct KConstPair {
@@ -126,6 +130,7 @@ __device__ __forceinline__ KConst<float> make_kconst<float>(const RhsArgs &a) {
   c.uo = (float)a.uoc1[0];
   c.sy = (float)(1.4426950408889634074 * inv_k2d);
   c.som = c.sy;  // 1/(k^2 ln 2) = log2(e)/k^2
+  c.isy = (float)(0.6931471805599453094 * k2d);
   // coordinates taken in y = sy s^2: shift by -u_scale ln(sy) / (n-1)
   const double lnsy = 0.36651292058166432701 - log(k2d);  // ln(log2 e) - ln k^2
   c.uy1 = (float)(a.uoc1[0] - a.us1 * lnsy);
@@ -148,6 +153,7 @@ __device__ __forceinline__ KConst<double> make_kconst<double>(const RhsArgs &a) 
   c.uo = a.u_off;
   c.sy = 1.0;
   c.som = 1.0;
+  c.isy = 1.0;
   c.uy1 = a.uoc[0];
   c.uy2 = a.uoc[1];
   c.uy3 = a.uoc[2];
@@ -268,7 +274,7 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
       const int r = r0 + i;
       const double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q, x = q2 * inv_k2;
       s_q2[i] = q2;
-      s_wm[i] = w * ((a.model == FFRG_MODEL_D4_VERTEX) ? q2 * q : q2);
+      s_wm[i] = w * (is_d4(a.model) ? q2 * q : q2);
       double rx, rdx;
       reg_r_rdot(a.reg, x, rx, rdx);
       s_kr[i] = k2 * rx;
@@ -317,7 +323,20 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
   // last node, read with weight 0).
   const double kh = k2 * 0.6931471805599453094;
   const int z_count = a.n_stack * a.n_pts;
-  if (a.model == FFRG_MODEL_FINITE_T) {
+  if (a.model == FFRG_MODEL_D4_FULL) {
+    // compact rows [Z row 0 | lambda4 row 0 | lambda3 rows]: FP64 copy and FP32 pairs
+    const int np = a.n_pts, ns = a.n_stack;
+    for (int i = tid0; i < a.tabc_count; i += stride) {
+      const int row = i / np, col = i - row * np;
+      const size_t src = row == 0 ? (size_t)col : row == 1 ? (size_t)2 * ns * np + col : ((size_t)ns + row - 2) * np + col;
+      const double f = row == 0 ? kh : 1.0;
+      const double v = a.tab[src];
+      a.tabc[i] = v;
+      const float v32 = (float)(f * v);
+      const float d = col == np - 1 ? 0.0f : (float)(f * a.tab[src + 1]) - v32;
+      a.tab32[i] = make_float2(v32, d);
+    }
+  } else if (a.model == FFRG_MODEL_FINITE_T) {
     for (int i = tid0; i <= z_count; i += stride)
       a.tab32[i] = i < z_count ? make_float2((float)(kh * a.tab[i]), (float)a.tab[z_count + i]) : make_float2(0.f, 0.f);
   } else {
@@ -332,7 +351,7 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
     for (int i = tid0; i < a.n_ext; i += stride) a.ext_done[i] = 0u;
   // per-external-point constants used by every work item of the main kernels
   for (int i = tid0; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
-  if (a.model == FFRG_MODEL_D4_VERTEX) {
+  if (is_d4(a.model)) {
     for (int j = tid0; j < a.n_ext_ang; j += stride) {
       const double c = a.psi_x[j];
       a.psi_s[j] = sqrt(fmax(0.0, 1.0 - c * c));
@@ -375,7 +394,9 @@ struct SmemLayout {
   P2 *cw2;
   T *c1, *s1, *w1;
   // table entries in shared memory: FP64 values, or the FP32 layout
-  static __device__ int entries(const RhsArgs &a) { return sizeof(T) == 4 ? a.tab32_count : a.tab_count; }
+  static __device__ int entries(const RhsArgs &a) {
+    return sizeof(T) == 4 ? a.tab32_count : (a.tabc_count ? a.tabc_count : a.tab_count);
+  }
   __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
     tab = (Tab *)base;
     size_t off = ((size_t)entries(a) * sizeof(Tab) + 15) & ~(size_t)15;
@@ -389,7 +410,7 @@ struct SmemLayout {
 template <typename T>
 __device__ __forceinline__ const typename TabOf<T>::type *table_src(const RhsArgs &a);
 template <>
-__device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { return a.tab; }
+__device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { return a.tabc ? a.tabc : a.tab; }
 template <>
 __device__ __forceinline__ const float2 *table_src<float>(const RhsArgs &a) { return a.tab32; }
 
@@ -569,14 +590,77 @@ __device__ __forceinline__ RowAcc<T> ft_witem(const RhsArgs &a, const RhsArgs *s
   return acc;
 }
 
+// D4_FULL three-point vertex lambda3(S0, a, b): the tables hold rows
+// (ia, ib) of the log grid in S0 for uniform nodes of a and b on [-1, 1].
+// For a vertex with legs k1, k2, k3 (sum 0; squared magnitudes s1, s2, s3):
+// a = cosine between k1 and k2, b = (s1 - s2)/(s1 + s2), clamped to [-1, 1]
+// with NaN to -1; linear between nodes in ln S0, a and b.  S0 enters through
+// the table coordinate of y3 = (s1 + s2 + s3) sy with offset uy3 (lerp_pos).
+// FP64 kernels take a = (s3 - s1 - s2)/(2 sqrt(s1 s2)) as the oracle does.
+// In FP32 that form cancels when one leg is short (an error u p^2 divided by
+// q p); the FP32 kernels take the cosine from the leg components instead
+// (see d4_witem), which keeps its error near u.
+__device__ __forceinline__ void shape_pos(double v, int m, int &i, double &w) {
+  if (m < 2) {
+    i = 0;
+    w = 0.0;
+    return;
+  }
+  v = v >= -1.0 ? (v <= 1.0 ? v : 1.0) : -1.0;
+  const double u = 0.5 * (v + 1.0) * (m - 1);
+  i = min((int)u, m - 2);
+  w = u - i;
+}
+__device__ __forceinline__ void shape_pos(float v, int m, int &i, float &w) {
+  if (m < 2) {
+    i = 0;
+    w = 0.0f;
+    return;
+  }
+  float u1;  // (v + 1)/2 saturated to [0, 1], NaN to 0
+  asm("fma.rn.sat.f32 %0, %1, 0f3F000000, 0f3F000000;" : "=f"(u1) : "f"(v));
+  const float u = u1 * (float)(m - 1);
+  i = min((int)u, m - 2);
+  w = u - (float)i;
+}
+__device__ __forceinline__ double shape_a(double s1, double s2, double s3) {
+  return (s3 - s1 - s2) / (2.0 * sqrt(s1 * s2));
+}
+__device__ __forceinline__ double shape_b(double s1, double s2) { return (s1 - s2) / (s1 + s2); }
+__device__ __forceinline__ float shape_b(float s1, float s2) { return (s1 - s2) * hw_rcp(s1 + s2); }
+// cosine between q and -(q + p) at |q+p|^2 = A2: (s3-s1-s2)/(2 sqrt(s1 s2)) in
+// FP64; -(q + p c1)/|q + p| in FP32 (q.(q+p) = q (q + p c1), no cancellation)
+__device__ __forceinline__ double va_shape_a(double, double, double, double q2, double A2, double p2) {
+  return shape_a(q2, A2, p2);
+}
+__device__ __forceinline__ float va_shape_a(float q, float p, float c1, float, float A2, float) {
+  return -fmaf(p, c1, q) * rsqrtf(A2);
+}
+
+template <typename T, typename Tab>
+__device__ __forceinline__ T lam3_full(const RhsArgs &a, const Tab *L3, T y3, T us, T uy3, T va, T vb) {
+  const int np = a.n_pts, na = a.n_va, nb = a.n_vb;
+  int i0, ia, ib;
+  T w, wa, wb;
+  lerp_pos(y3, us, uy3, np, i0, w);
+  shape_pos(va, na, ia, wa);
+  shape_pos(vb, nb, ib, wb);
+  const Tab *r00 = L3 + (size_t)(ia * nb + ib) * np;
+  const int db = nb > 1 ? np : 0, da = na > 1 ? nb * np : 0;
+  const T v00 = lerp_at(r00, i0, w), v01 = lerp_at(r00 + db, i0, w);
+  const T v10 = lerp_at(r00 + da, i0, w), v11 = lerp_at(r00 + da + db, i0, w);
+  return ((T)1 - wa) * (((T)1 - wb) * v00 + wb * v01) + wa * (((T)1 - wb) * v10 + wb * v11);
+}
+
 // d=4 vertex expansion: row = (radial node r, first-angle node ia), inner loop
-// over the second-angle nodes for the three-point block
-template <typename T, bool POLE>
+// over the second-angle nodes for the three-point block.  FULL: the D4_FULL
+// model (lambda3 on (S0, a, b); compact tables Z | lambda4 | lambda3 rows).
+template <typename T, bool POLE, bool FULL = false>
 __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
                                            const KConst<T> &kc, int e, int c, int lane) {
   const T us = kc.us, sy = kc.sy;
   const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang, na1 = a.na1;
-  const auto *Zt = S.tab, *L3 = S.tab + np, *L4 = S.tab + 2 * np;
+  const auto *Zt = S.tab, *L3 = S.tab + (FULL ? 2 : 1) * np, *L4 = S.tab + (FULL ? 1 : 2) * np;
   int block, ip, jp = 0;
   if (e <= np_) {
     block = 0;
@@ -603,19 +687,30 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
     const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
     const T Ay = A2 * sy;
     const T ZA = lerp(Zt, Ay, us, kc.uy1, np);
-    auto pole_a = [&]() { return pole_d4(sa, e, r, ia, -1); };
+    auto pole_a = [&]() { return pole_d4<FULL ? FFRG_MODEL_D4_FULL : FFRG_MODEL_D4_VERTEX>(sa, e, r, ia, -1); };
     const T GA = inv_prop<POLE>(a, ZA, Ay, (T)0, kc, pole_a);
     T v;
     if (block == 0) {
       const T l4 = lerp(L4, (q2 + p2) * sy, us, kc.uy2, np);
-      const T l3 = lerp(L3, (q2 + A2 + p2) * sy, us, kc.uy3, np);
+      T l3;
+      if constexpr (FULL) l3 = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, kc.uy3, va_shape_a(q, p, c1, q2, A2, p2),
+                                         shape_b(q2, A2));   // legs q, -(q+p), p
+      else l3 = lerp(L3, (q2 + A2 + p2) * sy, us, kc.uy3, np);
       v = kc.sw2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
     } else if (block == 2) {
       const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * sy, us, kc.uy4, np);
       v = kc.sw2 * GA * l4 * l4;
     } else {
       const T uy1 = kc.uy1, uy3 = kc.uy3;
-      const T la = lerp(L3, (q2 + A2 + p2) * sy, us, uy3, np);
+      T la;
+      if constexpr (FULL)
+        la = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, uy3, va_shape_a(q, p, c1, q2, A2, p2),
+                       shape_b(q2, A2));   // legs q, -(q+p1), p1
+      else la = lerp(L3, (q2 + A2 + p2) * sy, us, uy3, np);
+      // components (e1 along p1, e2 in the p1-p2 plane): q = q (c1, s1 c2, s1 s2'),
+      // p1 = p (1, 0, 0), p2 = p (cpsi, spsi, 0)
+      [[maybe_unused]] const T qs1 = q * S.s1[ia], x1 = q * c1 + p, x2 = q * c1 - p * cpsi, psp = p * spsi;
+      [[maybe_unused]] const T hc = p * cpsi * c1, hs = p * spsi * S.s1[ia];   // q^.p2 = hc + hs c2
       const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
       const T by = base * sy, b0 = (base - t1) * sy, t2y = t2 * sy, sy_ab = (A2 + C2) * sy;
       T rs = 0;
@@ -623,10 +718,27 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
         const auto cw = S.cw2[b];
         const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
         const T ZB = lerp(Zt, By, us, uy1, np);
-        auto pole_b = [&]() { return pole_d4(sa, e, r, ia, b); };
+        auto pole_b = [&]() { return pole_d4<FULL ? FFRG_MODEL_D4_FULL : FFRG_MODEL_D4_VERTEX>(sa, e, r, ia, b); };
         const T GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
-        const T lb = lerp(L3, by + By, us, uy3, np);
-        const T lc = lerp(L3, sy_ab + By, us, uy3, np);
+        T lb, lc;
+        if constexpr (FULL) {
+          T a_b, a_c;
+          if constexpr (sizeof(T) == 8) {   // FP64: the oracle's form
+            const T B2 = By;                  // sy = 1
+            a_b = shape_a(q2, B2, p2);
+            a_c = shape_a(A2, B2, C2);
+          } else {                          // FP32: from the leg components
+            const T B2 = By * kc.isy, rB = rsqrtf(B2);
+            a_b = (fmaf(hs, cw.x, hc) - q) * rB;                     // cos(q, -(q - p2))
+            const T y1 = qs1 * cw.x, y2 = y1 - psp, z2 = qs1 * qs1 * fmaf(-cw.x, cw.x, (T)1);
+            a_c = -fmaf(x1, x2, fmaf(y1, y2, z2)) * rsqrtf(A2) * rB;  // cos(q + p1, -(q - p2))
+          }
+          lb = lam3_full(a, L3, by + By, us, uy3, a_b, shape_b(q2 * sy, By));   // legs q, -(q-p2), p2
+          lc = lam3_full(a, L3, sy_ab + By, us, uy3, a_c, shape_b(Ay, By));     // legs q+p1, -(q-p2), -(p1+p2)
+        } else {
+          lb = lerp(L3, by + By, us, uy3, np);
+          lc = lerp(L3, sy_ab + By, us, uy3, np);
+        }
         rs += cw.y * GB * lb * lc;
       }
       v = GA * la * rs;
@@ -647,6 +759,7 @@ __device__ __forceinline__ RowAcc<T> witem(const RhsArgs &a, const RhsArgs *sa, 
                                         const KConst<T> &kc, int e, int c, int lane) {
   if constexpr (MODEL == FFRG_MODEL_D3) return d3_witem<T, POLE>(a, sa, S, kc, e, c, lane);
   else if constexpr (MODEL == FFRG_MODEL_D4_VERTEX) return d4_witem<T, POLE>(a, sa, S, kc, e, c, lane);
+  else if constexpr (MODEL == FFRG_MODEL_D4_FULL) return d4_witem<T, POLE, true>(a, sa, S, kc, e, c, lane);
   else return ft_witem<T, POLE>(a, sa, S, kc, e, c, lane);
 }
 
@@ -662,7 +775,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename T>
 __device__ __forceinline__ bool pole_possible(const RhsArgs &a, const SmemLayout<T> &S, const KConst<T> &kc) {
   int neg = 0;
-  const int nz = a.n_stack * a.n_pts;
+  const int nz = (a.model == FFRG_MODEL_D4_FULL ? 1 : a.n_stack) * a.n_pts;
   for (int i = threadIdx.x; i < nz; i += blockDim.x) neg |= table_value(S.tab[i]) < (T)0;
   return __syncthreads_or(neg) || kc.m2 < (T)0;
 }
@@ -672,7 +785,7 @@ __device__ __forceinline__ bool pole_possible(const RhsArgs &a, const SmemLayout
 // normalisation, and the non-finite check into the status word.
 __device__ __forceinline__ void write_output(const RhsArgs &a, int e, double s) {
   double coef = 1.0;
-  if (a.model == FFRG_MODEL_D4_VERTEX) {
+  if (is_d4(a.model)) {
     const int np_ = a.n_ext_p;
     if (e > np_ && e < np_ + 1 + np_ * a.n_ext_ang) coef = 3.0;
     else if (e >= np_ + 1 + np_ * a.n_ext_ang) coef = 1.5;
@@ -699,7 +812,7 @@ template <int MODEL, typename T, bool POLE>
 __device__ __forceinline__ void item_loop(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
                                           const KConst<T> &kc) {
   const int lane = threadIdx.x & 31;
-  const int rot = MODEL == FFRG_MODEL_D4_VERTEX ? a.n_ext_p + 1 : 0;
+  const int rot = is_d4(MODEL) ? a.n_ext_p + 1 : 0;
   for (;;) {
     int d = 0;
     if (lane == 0) d = (int)atomicAdd(a.work_ctr, 1u);
@@ -790,6 +903,9 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
   case FFRG_MODEL_D3: kern = mixed ? rhs_main<FFRG_MODEL_D3, float> : rhs_main<FFRG_MODEL_D3, double>; break;
   case FFRG_MODEL_D4_VERTEX:
     kern = mixed ? rhs_main<FFRG_MODEL_D4_VERTEX, float> : rhs_main<FFRG_MODEL_D4_VERTEX, double>;
+    break;
+  case FFRG_MODEL_D4_FULL:
+    kern = mixed ? rhs_main<FFRG_MODEL_D4_FULL, float> : rhs_main<FFRG_MODEL_D4_FULL, double>;
     break;
   default: kern = mixed ? rhs_main<FFRG_MODEL_FINITE_T, float> : rhs_main<FFRG_MODEL_FINITE_T, double>; break;
   }

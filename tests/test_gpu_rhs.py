@@ -141,6 +141,87 @@ def test_d4_litim_closed_forms_on_gpu(ctx):
     assert np.max(np.abs(blk4 - 1.5 * 1.3 ** 2 * ex3)) / ex3 < 1e-13
 
 
+# ----------------------------------------------------------------------------- d=4, full vertex
+def test_d4_full_small_ragged(ctx):
+    """lambda3 on (S0, a, b) (trilinear), compact tables staged per CTA."""
+    for seed, na, nb in ((41, 3, 4), (42, 1, 5), (43, 4, 1)):
+        wl = fi.make_d4_full(seed=seed, n_pts=12, n_va=na, n_vb=nb, n_ext_ang=3, n_rad=9, n_ang1=5, n_ang2=4)
+        for k in (1.3, 0.4):
+            _check(ctx, wl, k)
+
+
+def test_d4_full_full_size_sampled(ctx):
+    wl = fi.make_d4_full()           # 96-pt log grid x 8 x 7 vertex grid, 1281 ext x (128 x 64 x 16)
+    ne = wl.problem.n_ext()
+    sel = [0, 96, 97, 97 + 8 * 40 + 3, ne - 97, ne - 1]
+    _check(ctx, wl, 1.0, sel=sel)
+
+
+def _termwise_scale(ctx, wl, k, ref):
+    """Per output, the sum of the magnitudes of the parts that can cancel: in
+    the Z block of the d=4 models D2 = int dR G^2 [-lam4/2 + lam3^2 G], two
+    single-signed terms (FP64 runs with lam4 = 0 and with lam3 = 0); the
+    lambda3 and lambda4 blocks are single-signed, |ref| is their scale."""
+    import paper_2412_13043_gb300 as ffrg
+    n = wl.problem.n_ext_p + 1
+    parts = []
+    for zero in (2, 1):
+        t = wl.tables.copy()
+        t[zero] = 0.0
+        parts.append(np.abs(_run(ctx, fi.Workload(wl.problem, t, None), k, ffrg.FP64)[:n]))
+    scale = np.abs(ref).copy()
+    scale[:n] = parts[0] + parts[1]
+    return scale
+
+
+def test_d4_full_mixed_bound_on_every_output(ctx):
+    """All 961 outputs of the 96 x 8 x 7 workload: mixed within MIXED_TOL of
+    the FP64 path (itself checked against the oracle above) relative to the
+    magnitude of the cancelling parts (the Z block crosses zero near
+    p = 1.75 on this workload).  Short legs (q << p) make the FP32 shape
+    variable ill-conditioned in its magnitude form; the kernel takes it from
+    the leg components."""
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d4_full(n_rad=64, n_ang1=32, n_ang2=8)
+    for k in (1.0, 0.1):
+        g64 = _run(ctx, wl, k, ffrg.FP64)
+        g32 = _run(ctx, wl, k, ffrg.MIXED)
+        e = np.abs(g32 - g64) / _termwise_scale(ctx, wl, k, g64)
+        assert np.max(e) < MIXED_TOL, (k, np.max(e), int(np.argmax(e)))
+
+
+def test_d4_full_reduces_to_d4_vertex_on_gpu(ctx):
+    import dataclasses
+
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d4(seed=44, n_pts=16, n_ext_ang=3, n_rad=11, n_ang1=7, n_ang2=5)
+    na, nb = 3, 2
+    pf = dataclasses.replace(wl.problem, model=fi.MODEL_D4_FULL, n_stack=na * nb, n_va=na, n_vb=nb)
+    tf = np.zeros((3, na * nb, pf.n_pts))
+    tf[0, 0], tf[2, 0] = wl.tables[0, 0], wl.tables[2, 0]
+    tf[1, :] = wl.tables[1, 0]
+    wf = fi.Workload(pf, tf, None)
+    for prec, tol in ((ffrg.FP64, 1e-13), (ffrg.MIXED, 1e-6)):
+        a = _run(ctx, wl, 0.9, prec)
+        b = _run(ctx, wf, 0.9, prec)
+        assert np.max(np.abs(a - b) / np.abs(a)) < tol, prec
+
+
+def test_d4_full_rejects_adjoint_and_feedback(ctx):
+    import torch
+
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_d4_full(seed=45, n_pts=8, n_va=2, n_vb=2, n_ext_ang=2, n_rad=4, n_ang1=3, n_ang2=2)
+    tabs = ctx.tables(wl.problem, wl.tables)
+    g = torch.ones(wl.problem.n_ext(), dtype=torch.float64, device="cuda")
+    with pytest.raises(ffrg.FfrgError):
+        ctx.rhs_adjoint(wl.problem, tabs, 1.0, g)
+    y = torch.ones(3 * wl.problem.n_pts, dtype=torch.float64, device="cuda")
+    with pytest.raises(ffrg.FfrgError):
+        ctx.flow(wl.problem, tabs, y, 10.0, 1.0, feedback=1)
+    tabs.free()
+
+
 # ----------------------------------------------------------------------------- finite T
 def test_finite_t_small_ragged(ctx):
     wl = fi.make_finite_t(seed=51, N=3, T=0.05, n_pts=16, n_ext_p=7, n_ext_m=4, n_rad=13, n_ang=9)
