@@ -195,6 +195,7 @@ static void plan_free(ffrg_ctx *ctx, Plan *pl) {
   dev_free(ctx, pl->kconst, 0);
   dev_free(ctx, pl->radF32, 0);
   dev_free(ctx, pl->tabc, 0);
+  dev_free(ctx, pl->kbuf, 0);
   delete pl;
 }
 
@@ -253,11 +254,22 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   // exactly what the single-flow kernels do).  The FP64 kernels split the
   // angle rule into blocks of at least 4 nodes until there is a row per
   // resident lane: small FP64 problems are bound by each lane's FP64 chain.
+  const long long kTargetItems = 8LL * 152 * 32;
   auto forward = [&](bool fp64, int &fcr, int &fn_chunks, int &fn_items, int &fjb) {
     if (is_d4(pb->model)) {
       fjb = pl->na2;
       fcr = chunk(8 * 32);
       fn_chunks = (outer_total + fcr - 1) / fcr;
+      fn_items = pl->n_ext * fn_chunks;
+    } else if (pb->model == FFRG_MODEL_FINITE_T) {
+      // rows of K: (stack row j, |p|) x radial node, the whole angle rule per row
+      fjb = pl->na1;
+      const long long n_outer = (long long)(pl->N + pl->n_ext_ang) * pl->n_ext_p;
+      long long rpi = (n_outer * pl->nr + kTargetItems - 1) / kTargetItems;
+      rpi = std::min<long long>(std::max<long long>((rpi + 31) / 32 * 32, 32), 256);
+      fcr = (int)std::min<long long>(rpi, pl->nr);
+      fn_chunks = (pl->nr + fcr - 1) / fcr;
+      fn_items = (int)(n_outer * fn_chunks);
     } else {
       const long long total_outer = (long long)pl->n_ext * outer_total;
       const long long kRowsWanted = 152LL * 2048;
@@ -266,14 +278,15 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
       fjb = (int)((pl->na1 + nblk - 1) / nblk);
       nblk = (pl->na1 + fjb - 1) / fjb;
       const int rows_ext = outer_total * (int)nblk;
-      const long long kTargetItems = 8LL * 152 * 32;
       long long rpi = ((long long)pl->n_ext * rows_ext + kTargetItems - 1) / kTargetItems;
       rpi = std::min<long long>(std::max<long long>((rpi + 31) / 32 * 32, 32), 256);
       fcr = (int)std::min<long long>(rpi, rows_ext);
       fn_chunks = (rows_ext + fcr - 1) / fcr;
+      fn_items = pl->n_ext * fn_chunks;
     }
-    fn_items = pl->n_ext * fn_chunks;
   };
+  pl->kbuf_count = pb->model == FFRG_MODEL_FINITE_T
+                       ? (size_t)(pl->N + pl->n_ext_ang) * pl->n_ext_p * pl->nr : 0;
   forward(false, pl->fcr, pl->fn_chunks, pl->fn_items, pl->fjb);
   forward(true, pl->fcr64, pl->fn_chunks64, pl->fn_items64, pl->fjb64);
   // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
@@ -329,6 +342,7 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_done, (size_t)pl->n_ext * sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->kconst, kKConstBytes);
   if (!st && pl->tabc_count) st = dev_alloc(ctx, (void **)&pl->tabc, (size_t)pl->tabc_count * sizeof(double));
+  if (!st && pl->kbuf_count) st = dev_alloc(ctx, (void **)&pl->kbuf, pl->kbuf_count * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_pd, (size_t)pl->n_ext_p * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
   if (!st)
@@ -371,6 +385,7 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.n_va = pl->n_va;
   a.n_vb = pl->n_vb;
   a.tabc = pl->tabc;
+  a.kbuf = pl->kbuf;
   a.k = k;
   a.m2_over_k2 = pb->m2_over_k2;
   a.m2_shift = pb->m2_shift;
@@ -474,6 +489,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
     cudaFree(pl->kconst);
     cudaFree(pl->radF32);
     cudaFree(pl->tabc);
+    cudaFree(pl->kbuf);
     delete pl;
   }
   ctx->plans.clear();

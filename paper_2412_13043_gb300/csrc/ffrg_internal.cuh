@@ -65,6 +65,7 @@ struct RhsArgs {
   double sum_w2;               // sum of the second-angle weights (D4)
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
   double *tabc;                // D4_FULL: compact FP64 tables [Z row | lambda4 row | lambda3 rows] (precompute)
+  void *kbuf;                  // FINITE_T: K[j][ip][r], j < N + n_ext_ang, in the kernel precision (main kernel)
   float2 *tab32;               // FP32 node pairs (T[i], T[i+1] - T[i]; 0 at a row end), precompute kernel
   const double *rad_x, *rad_w; // unit-interval GL rule on [0, 1]
   const double *a1_x, *a1_w;   // first angle rule
@@ -354,6 +355,8 @@ struct Plan {
   int tab32_count;                // float2 entries of the FP32 table layout
   int tabc_count, n_va, n_vb;     // D4_FULL: compact FP64 table doubles, vertex nodes
   double *tabc;
+  size_t kbuf_count;              // FINITE_T: entries of K (N + n_ext_ang) x n_ext_p x n_rad
+  double *kbuf;
   int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
   size_t smem64, smem32;    // dynamic shared memory bytes
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;

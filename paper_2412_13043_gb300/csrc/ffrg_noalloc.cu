@@ -110,6 +110,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.partial = sc.take<double>(std::max(pl.fn_items, pl.fn_items64));
   pl.tab32 = sc.take<float2>((size_t)pl.tab32_count);
   if (pl.tabc_count) pl.tabc = sc.take<double>((size_t)pl.tabc_count);
+  if (pl.kbuf_count) pl.kbuf = sc.take<double>(pl.kbuf_count);
   if (sc.used > kNoallocScratchBytes) return FFRG_EINVAL;  // problem needs more than the 4 MiB scratch
 
   const size_t smem = precision == FFRG_MIXED ? pl.smem32 : pl.smem64;

@@ -79,11 +79,11 @@ __device__ __noinline__ float pole_d4(const RhsArgs *a, int e, int r, int ia, in
 // stack row of loop frequency index n: |n| (bosonic), n or -n-1 (fermionic)
 __device__ __forceinline__ int stack_index(int stat, int n) { return stat ? (n >= 0 ? n : -n - 1) : abs(n); }
 
-__device__ __noinline__ float pole_ft(const RhsArgs *a, int e, int n, int r, int j) {
-  const int nm = a->n_ext_ang, ip = e / nm, m = e - ip * nm;
+// K row of stack row jk (finite T): frequency of row jk, table row min(jk, n_stack-1)
+__device__ __noinline__ float pole_ftk(const RhsArgs *a, int ip, int jk, int r, int j) {
   const double p = ext_momentum(*a, ip), q = a->radq[r], c = a->a1_x[j];
-  const int srow = min(stack_index(a->stat, n + m), a->n_stack - 1);
-  const double om = kPi * a->T * (2.0 * (double)(n + m) + (a->stat ? 1.0 : 0.0));
+  const int srow = min(jk, a->n_stack - 1);
+  const double om = kPi * a->T * (2.0 * (double)jk + (a->stat ? 1.0 : 0.0));
   return pole_prop(a, a->tab + (size_t)srow * a->n_pts, q * q + p * p + 2.0 * q * p * c, om * om);
 }
 
@@ -554,40 +554,60 @@ __device__ __forceinline__ void zl_lookup(const float2 *tab, const RhsArgs &a, i
   L = fmaf(w, v1.y - v0.y, v0.y);
 }
 
-// finite T: row = ((Matsubara n, radial node r), block of jb angle nodes);
-// sum_j v_j lam(n+m, s) G(n+m, s), s = |q+p|
+// finite T, factorised through the angle-integrated kernel K(p, q): the
+// angular sum of a loop row depends on the shifted frequency index
+// n' = n + m only through its stack row j (|n'| bosonic; n' or -n'-1
+// fermionic) and that row's frequency^2, so
+//   K[j][ip][r] = sum_c v_c lam(j, |q_r + p_ip|) G(j, |q_r + p_ip|)
+// is evaluated once per (j, p, r), j = 0 .. N+M-1, and
+//   I(m, p) = sum_n sum_r F(n, r) K[j(n + m)][p][r]
+// is a contraction over loop frequencies and radial nodes (ft_contract).
+// The same discrete sum as the direct loop over (m, n, r, c), with (N+M)
+// instead of (2N+1) M angular sums per (p, r).
 template <typename T, bool POLE>
-__device__ __forceinline__ RowAcc<T> ft_witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
-                                           const KConst<T> &kc, int e, int c, int lane) {
+__device__ __forceinline__ void ftk_rows(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
+                                         const KConst<T> &kc, int outer, int c, int lane) {
   const T us = kc.us, uy1 = kc.uy1, sy = kc.sy;
-  const int np = a.n_pts, nm = a.n_ext_ang, na1 = a.na1, nr = a.nr, jb = a.jb, nblk = (na1 + jb - 1) / jb;
-  const int outer_total = a.nfreq * nr;
-  const int ip = e / nm, m = e - ip * nm;
-  const T half = (T)(a.stat ? 0.5 : 0.0);  // fermionic loop: nu = 2 pi T (n + 1/2)
-  const T p = (T)a.ext_pd[ip], p2 = p * p;
-  const int r0 = c * a.cr, r1 = min(r0 + a.cr, outer_total * nblk);
-  RowAcc<T> acc;
-  for (int rr = r0 + lane; rr < r1; rr += 32) {
-    const int o = rr / nblk, j0 = (rr - o * nblk) * jb, j1 = min(j0 + jb, na1);
-    const int nn = o / nr, r = o - nn * nr, n = nn - a.N - a.stat;
-    const int srow = min(stack_index(a.stat, n + m), a.n_stack - 1);
-    const T om = kc.twopiT * ((T)(n + m) + half);
-    const T om2s = om * om * kc.som;
+  const int np = a.n_pts, na1 = a.na1, nr = a.nr;
+  const int jk = outer / a.n_ext_p, ip = outer - jk * a.n_ext_p;
+  const int srow = min(jk, a.n_stack - 1);
+  const T om = kc.twopiT * ((T)jk + (T)(a.stat ? 0.5 : 0.0));   // omega_j or nu_j
+  const T om2s = om * om * kc.som;
+  const T p = (T)a.ext_pd[ip];
+  T *K = (T *)a.kbuf + ((size_t)jk * a.n_ext_p + ip) * nr;
+  const int r0 = c * a.cr, r1 = min(r0 + a.cr, nr);
+  for (int r = r0 + lane; r < r1; r += 32) {
     const T q = radial_q<T>(a, r);
-    const T by = (q * q + p2) * sy, ty = (T)2 * q * p * sy;
+    const T by = (q * q + p * p) * sy, ty = (T)2 * q * p * sy;
     T rs = 0;
-    for (int j = j0; j < j1; ++j) {
+    for (int j = 0; j < na1; ++j) {
       const T y = by + ty * S.c1[j];
       int i0;
       T w, Z, Lv;
       lerp_pos(y, us, uy1, np, i0, w);
       zl_lookup(S.tab, a, srow, i0, w, Z, Lv);
-      auto pole = [&]() { return pole_ft(sa, e, n, r, j); };
+      auto pole = [&]() { return pole_ftk(sa, ip, jk, r, j); };
       rs += S.w1[j] * Lv * inv_prop<POLE>(a, Z, y, om2s, kc, pole);
     }
-    acc.add(radial_F<T>(a, o), rs);
+    K[r] = rs;
   }
-  return acc;
+}
+
+// I(m, p) of external point e = (ip, m) from K and the radial factors, in a
+// fixed order: lane l takes radial nodes l, l+32, ... for every loop index n,
+// accumulating in the precision's RowAcc, then the warp tree (lane 0).
+template <typename T>
+__device__ __forceinline__ double ft_contract(const RhsArgs &a, int e, int lane) {
+  const int nm = a.n_ext_ang, ip = e / nm, m = e - ip * nm, nr = a.nr;
+  const int n_lo = -a.N - a.stat;
+  const T *K = (const T *)a.kbuf;
+  RowAcc<T> acc;
+  for (int n = n_lo; n <= a.N; ++n) {
+    const T *Kr = K + ((size_t)stack_index(a.stat, n + m) * a.n_ext_p + ip) * nr;
+    const int row = (n - n_lo) * nr;
+    for (int r = lane; r < nr; r += 32) acc.add(radial_F<T>(a, row + r), Kr[r]);
+  }
+  return acc.item_sum();
 }
 
 // D4_FULL three-point vertex lambda3(S0, a, b): the tables hold rows
@@ -760,7 +780,7 @@ __device__ __forceinline__ RowAcc<T> witem(const RhsArgs &a, const RhsArgs *sa, 
   if constexpr (MODEL == FFRG_MODEL_D3) return d3_witem<T, POLE>(a, sa, S, kc, e, c, lane);
   else if constexpr (MODEL == FFRG_MODEL_D4_VERTEX) return d4_witem<T, POLE>(a, sa, S, kc, e, c, lane);
   else if constexpr (MODEL == FFRG_MODEL_D4_FULL) return d4_witem<T, POLE, true>(a, sa, S, kc, e, c, lane);
-  else return ft_witem<T, POLE>(a, sa, S, kc, e, c, lane);
+  else static_assert(MODEL != FFRG_MODEL_FINITE_T, "finite T runs through ftk_rows");
 }
 
 // warp sum in a fixed order (valid in lane 0)
@@ -845,8 +865,33 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) rhs_main(RhsArg
   SmemLayout<T> S(smem, a);
   if (!main_prologue<T>(a, S, &bar)) return;
   const KConst<T> kc = load_kconst<T>(a);
-  if (pole_possible<T>(a, S, kc)) item_loop<MODEL, T, true>(a, &sa, S, kc);
-  else item_loop<MODEL, T, false>(a, &sa, S, kc);
+  const bool pole = pole_possible<T>(a, S, kc);
+  if constexpr (MODEL == FFRG_MODEL_FINITE_T) {
+    // K rows: items (stack row, |p|) x chunk of radial nodes from the counter
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+      int d = 0;
+      if (lane == 0) d = (int)atomicAdd(a.work_ctr, 1u);
+      d = __shfl_sync(0xffffffffu, d, 0);
+      if (d >= a.n_items) break;
+      const int outer = d / a.n_chunks, c = d - outer * a.n_chunks;
+      if (pole) ftk_rows<T, true>(a, &sa, S, kc, outer, c, lane);
+      else ftk_rows<T, false>(a, &sa, S, kc, outer, c, lane);
+    }
+  } else {
+    if (pole) item_loop<MODEL, T, true>(a, &sa, S, kc);
+    else item_loop<MODEL, T, false>(a, &sa, S, kc);
+  }
+}
+
+// finite T: outputs from K and the radial factors, one warp per external point
+template <typename T>
+__global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
+  if (skipped(a)) return;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (e >= a.n_ext) return;
+  const double t = ft_contract<T>(a, e, lane);
+  if (lane == 0) write_output(a, e, t);
 }
 
 
@@ -909,7 +954,7 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
     break;
   default: kern = mixed ? rhs_main<FFRG_MODEL_FINITE_T, float> : rhs_main<FFRG_MODEL_FINITE_T, double>; break;
   }
-  if (!a.work_ctr || !a.radq32 || !a.ext_done || !a.kconst) {
+  if (!a.work_ctr || !a.radq32 || !a.ext_done || !a.kconst || (a.model == FFRG_MODEL_FINITE_T && !a.kbuf)) {
     ctx->last_error = "plan without work counters, FP32 radial nodes or constant block";
     return FFRG_EINVAL;
   }
@@ -928,7 +973,13 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;
   }
-  // the main kernel writes the outputs (last warp per external point)
+  // d=3, d=4: the main kernel writes the outputs (last warp per external
+  // point); finite T: the contraction of K with the radial factors
+  if (a.model == FFRG_MODEL_FINITE_T) {
+    const int blocks = (a.n_ext + kThreads / 32 - 1) / (kThreads / 32);
+    if (mixed) ft_contract_kernel<float><<<blocks, kThreads, 0, s>>>(a);
+    else ft_contract_kernel<double><<<blocks, kThreads, 0, s>>>(a);
+  }
   return set_cuda_error(ctx, cudaGetLastError(), "rhs launch");
 }
 
@@ -952,7 +1003,7 @@ __global__ void batched_finalize_kernel(const RhsArgs *descs) {
   if (skipped(a)) return;
   const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (e >= a.n_ext) return;
-  const double t = sum_partials(a, e, lane);
+  const double t = a.model == FFRG_MODEL_FINITE_T ? ft_contract<float>(a, e, lane) : sum_partials(a, e, lane);
   if (lane == 0) write_output(a, e, t);
 }
 
@@ -1003,9 +1054,14 @@ __global__ void __launch_bounds__(kThreads, 4)
     for (int g = lo + warp; g < hi; g += nw) {
       const int item = g - start[f];
       const int e = item / sa.n_chunks, c = item - e * sa.n_chunks;
-      const double acc = pole ? witem<MODEL, float, true>(sa, &sa, S, kc, e, c, lane).item_sum()
-                              : witem<MODEL, float, false>(sa, &sa, S, kc, e, c, lane).item_sum();
-      if (lane == 0) sa.partial[item] = acc;
+      if constexpr (MODEL == FFRG_MODEL_FINITE_T) {   // K rows (e: stack row x |p|)
+        if (pole) ftk_rows<float, true>(sa, &sa, S, kc, e, c, lane);
+        else ftk_rows<float, false>(sa, &sa, S, kc, e, c, lane);
+      } else {
+        const double acc = pole ? witem<MODEL, float, true>(sa, &sa, S, kc, e, c, lane).item_sum()
+                                : witem<MODEL, float, false>(sa, &sa, S, kc, e, c, lane).item_sum();
+        if (lane == 0) sa.partial[item] = acc;
+      }
     }
   }
 }

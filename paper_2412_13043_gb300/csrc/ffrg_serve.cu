@@ -56,6 +56,7 @@ struct SlotLayout {
   int ny, npsi;
   size_t bytes;
   size_t o_tab, o_tab32, o_y, o_ys, o_K, o_raw, o_radF, o_radF32, o_radq, o_radq32, o_kc, o_extp, o_psis, o_part;
+  size_t o_kbuf;
   size_t o_rx, o_rw, o_a1x, o_a1w, o_a2x, o_a2w, o_psx, o_psw;
 };
 
@@ -85,6 +86,7 @@ static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotL
   L.o_radq32 = seg(u, (size_t)pl.nr * sizeof(float));
   L.o_radF32 = seg(u, (size_t)pl.nr * pl.nfreq * sizeof(float));
   L.o_kc = seg(u, kKConstBytes);
+  L.o_kbuf = seg(u, pl.kbuf_count * sizeof(float));   // finite T: K in FP32 (serving is mixed)
   L.o_extp = seg(u, (size_t)pl.n_ext_p * d);
   L.o_psis = seg(u, (size_t)L.npsi * d);
   L.o_part = seg(u, (size_t)pl.fn_items * d);
@@ -170,6 +172,7 @@ static int slot_setup(Server &S, int si) {
   pl.radq32 = (float *)(b + L.o_radq32);
   pl.radF32 = (float *)(b + L.o_radF32);
   pl.kconst = b + L.o_kc;
+  pl.kbuf = pl.kbuf_count ? (double *)(b + L.o_kbuf) : nullptr;
   pl.ext_pd = (double *)(b + L.o_extp);
   pl.psi_s = (double *)(b + L.o_psis);
   pl.partial = (double *)(b + L.o_part);
