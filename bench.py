@@ -311,7 +311,12 @@ def model_bench(ctx, steps: int = 5):
     for name, wl in cases:
         pb = wl.problem
         tabs = ctx.tables(pb, wl.tables)
-        row = {"workload": name, "evals_per_rhs": pb.evals()}
+        # finite T evaluates the angular sums once per (stack row, |p|, radial node)
+        # through K(p, q): the terms of the discrete sum (evals_per_rhs, the metric's
+        # unit) are computed from (N + M) instead of (2N + 1) M angular sums
+        computed = (pb.n_matsubara + pb.n_ext_ang) * pb.n_ext_p * pb.n_rad * pb.n_ang1 \
+            if pb.model == fi.MODEL_FINITE_T else pb.evals()
+        row = {"workload": name, "evals_per_rhs": pb.evals(), "integrands_computed_per_rhs": computed}
         outs = {}
         for pname, prec in (("mixed", ffrg.MIXED), ("fp64", ffrg.FP64)):
             out = torch.empty(pb.n_ext(), dtype=torch.float64, device="cuda")
@@ -329,7 +334,8 @@ def model_bench(ctx, steps: int = 5):
             ctx.set_profiling(False)
             step_ms = e0.elapsed_time(e1) / steps
             row[pname] = {"step_ms": step_ms, "kernel_ms": kms / max(cnt, 1),
-                          "evals_per_s": pb.evals() / (step_ms * 1e-3)}
+                          "evals_per_s": pb.evals() / (step_ms * 1e-3),
+                          "integrands_computed_per_s": computed / (step_ms * 1e-3)}
             outs[pname] = out.cpu().numpy()
         row["mixed_vs_fp64_max_rel_err"] = float(np.max(np.abs(outs["mixed"] - outs["fp64"]) / np.abs(outs["fp64"])))
         # d=4 models: the Z block (D2 = int dR G^2 [-lam4/2 + lam3^2 G]) can cross
