@@ -593,21 +593,30 @@ __device__ __forceinline__ void ftk_rows(const RhsArgs &a, const RhsArgs *sa, co
   }
 }
 
-// I(m, p) of external point e = (ip, m) from K and the radial factors, in a
-// fixed order: lane l takes radial nodes l, l+32, ... for every loop index n,
-// accumulating in the precision's RowAcc, then the warp tree (lane 0).
+// I(m, p) of external point e = (ip, m) from K and the radial factors, by a
+// whole block in a fixed order: thread t takes the terms (n, r) = t,
+// t + blockDim, ... of the nfreq x n_rad terms (n major), accumulating in the
+// precision's RowAcc; each warp reduces with its tree, thread 0 adds the warp
+// sums in order (valid in thread 0).  Every thread of the block must call it.
 template <typename T>
-__device__ __forceinline__ double ft_contract(const RhsArgs &a, int e, int lane) {
+__device__ __forceinline__ double ft_contract(const RhsArgs &a, int e, double *red) {
   const int nm = a.n_ext_ang, ip = e / nm, m = e - ip * nm, nr = a.nr;
-  const int n_lo = -a.N - a.stat;
+  const int n_lo = -a.N - a.stat, total = a.nfreq * nr;
   const T *K = (const T *)a.kbuf;
   RowAcc<T> acc;
-  for (int n = n_lo; n <= a.N; ++n) {
-    const T *Kr = K + ((size_t)stack_index(a.stat, n + m) * a.n_ext_p + ip) * nr;
-    const int row = (n - n_lo) * nr;
-    for (int r = lane; r < nr; r += 32) acc.add(radial_F<T>(a, row + r), Kr[r]);
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int row = i / nr, r = i - row * nr;   // radF index row * nr + r = i
+    const T *Kr = K + ((size_t)stack_index(a.stat, row + n_lo + m) * a.n_ext_p + ip) * nr;
+    acc.add(radial_F<T>(a, i), Kr[r]);
   }
-  return acc.item_sum();
+  const double w = acc.item_sum();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[j];
+  __syncthreads();
+  return t;
 }
 
 // D4_FULL three-point vertex lambda3(S0, a, b): the tables hold rows
@@ -884,14 +893,13 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) rhs_main(RhsArg
   }
 }
 
-// finite T: outputs from K and the radial factors, one warp per external point
+// finite T: outputs from K and the radial factors, one block per external point
 template <typename T>
 __global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
+  __shared__ double red[kThreads / 32];
   if (skipped(a)) return;
-  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (e >= a.n_ext) return;
-  const double t = ft_contract<T>(a, e, lane);
-  if (lane == 0) write_output(a, e, t);
+  const double t = ft_contract<T>(a, blockIdx.x, red);
+  if (threadIdx.x == 0) write_output(a, blockIdx.x, t);
 }
 
 
@@ -976,9 +984,8 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
   // d=3, d=4: the main kernel writes the outputs (last warp per external
   // point); finite T: the contraction of K with the radial factors
   if (a.model == FFRG_MODEL_FINITE_T) {
-    const int blocks = (a.n_ext + kThreads / 32 - 1) / (kThreads / 32);
-    if (mixed) ft_contract_kernel<float><<<blocks, kThreads, 0, s>>>(a);
-    else ft_contract_kernel<double><<<blocks, kThreads, 0, s>>>(a);
+    if (mixed) ft_contract_kernel<float><<<a.n_ext, kThreads, 0, s>>>(a);
+    else ft_contract_kernel<double><<<a.n_ext, kThreads, 0, s>>>(a);
   }
   return set_cuda_error(ctx, cudaGetLastError(), "rhs launch");
 }
@@ -997,14 +1004,21 @@ __global__ void __launch_bounds__(kThreads) batched_precompute_kernel(const RhsA
   precompute_body(a);
 }
 
-// one warp per external point of flow blockIdx.y
-__global__ void batched_finalize_kernel(const RhsArgs *descs) {
+// one block per external point blockIdx.x of flow blockIdx.y: finite T
+// contracts K (the same function as the single-flow kernel), d=3 sums the
+// item partials in warp 0
+__global__ void __launch_bounds__(kThreads) batched_finalize_kernel(const RhsArgs *descs) {
+  __shared__ double red[kThreads / 32];
   const RhsArgs &a = descs[blockIdx.y];
-  if (skipped(a)) return;
-  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (e >= a.n_ext) return;
-  const double t = a.model == FFRG_MODEL_FINITE_T ? ft_contract<float>(a, e, lane) : sum_partials(a, e, lane);
-  if (lane == 0) write_output(a, e, t);
+  const int e = blockIdx.x;
+  if (skipped(a) || e >= a.n_ext) return;   // uniform over the block
+  if (a.model == FFRG_MODEL_FINITE_T) {
+    const double t = ft_contract<float>(a, e, red);
+    if (threadIdx.x == 0) write_output(a, e, t);
+  } else if (threadIdx.x < 32) {
+    const double t = sum_partials(a, e, threadIdx.x);
+    if (threadIdx.x == 0) write_output(a, e, t);
+  }
 }
 
 // Each CTA takes a contiguous range of the combined item list holding an
@@ -1105,8 +1119,7 @@ int launch_rhs_batched(ffrg_ctx *ctx, const BatchList &bl, cudaStream_t s) {
                                   : launch_batched_main<FFRG_MODEL_FINITE_T>(ctx, bl.descs, G, s);
   }
   if (st) return st;
-  const int fin_blocks = (bl.max_ext + kThreads / 32 - 1) / (kThreads / 32);
-  batched_finalize_kernel<<<dim3(fin_blocks, bl.n_flows), kThreads, 0, s>>>(bl.descs);
+  batched_finalize_kernel<<<dim3(std::max(1, bl.max_ext), bl.n_flows), kThreads, 0, s>>>(bl.descs);
   return set_cuda_error(ctx, cudaGetLastError(), "batched rhs launch");
 }
 
