@@ -34,14 +34,18 @@ sys.path.insert(0, ROOT)
 METRIC = "integrand evals/s & flows/s vs plain FP64 GPU at 1e-8 endpoint err; p50/p99 latency"
 WORKLOAD = "d4 vertex-expansion RHS: 3 tables x 128 pts, 1281 ext x (128 rad x 64 GC-II x 16 GL) nodes"
 
-# Special-function evaluations per integrand term of the mixed d=4 kernel
-# (from the integrand's formula, not from the compiled code): inner term of the
-# three-point diagram: 3 table coordinates (log) + 1 regulator exp + 2
-# reciprocals (regulator shape, propagator); per (radial, c1) row: 2 logs +
-# 1 exp + 2 reciprocals for the |q+p1| leg (all three diagram classes).
-SFU_INNER = 6
-SFU_ROW = 5
-SFU_PER_CLK_SM = 16      # MUFU results per clock per SM
+# Special-function work per integrand term of the mixed d=4 kernel, from the
+# integrand's formula (not from the compiled code), in units of one log2 or
+# reciprocal (16 results per clock per SM); the exponential runs at twice that
+# rate on this GPU (a throughput loop measured 15.1 lg2, 15.1 rcp and 29.9 ex2
+# results per SM per clock), so it counts one half.  Inner term of the
+# three-point diagram: 3 table coordinates (log) + 1 regulator exponential +
+# 1 reciprocal (propagator N / (Z k^2 x + m^2 N)).  Per (radial, c1) row: the
+# |q+p1| leg (1 log + 1 exponential + 1 reciprocal) and the row's vertex
+# lookups (Z block 2, three-point block 1, lambda4 block 1 log).
+SFU_INNER = 4.5
+SFU_LEG = 2.5
+SFU_PER_CLK_SM = 16      # log2 / reciprocal results per clock per SM
 FP32_PER_CLK_SM = 128    # FP32 FMA lanes per SM
 
 
@@ -67,13 +71,12 @@ def dist_env():
 
 
 def sfu_ops_per_launch(pb):
-    """Algorithmic special-function evaluations of one d=4 RHS launch."""
+    """Algorithmic special-function work of one d=4 RHS launch (log2 units)."""
     n_p, n_psi = pb.n_ext_p, pb.n_ext_ang
     rows = pb.n_rad * pb.n_ang1
     inner = n_p * n_psi * rows * pb.n_ang2               # three-point diagram terms
-    row_ops = (2 * n_p + 1 + n_p * n_psi) * rows * SFU_ROW
-    extra_rows = (n_p + 1) * rows * 2                    # two vertex lookups per row (Z and lambda4 blocks)
-    return inner * SFU_INNER + row_ops + extra_rows
+    row_units = rows * ((n_p + 1) * (SFU_LEG + 2) + n_p * n_psi * (SFU_LEG + 1) + n_p * (SFU_LEG + 1))
+    return inner * SFU_INNER + row_units
 
 
 class ClockSampler:
@@ -511,7 +514,8 @@ def main():
     kern_s = (main_ms / 1e3) / max(1, launches)
     sfu_ops = sfu_ops_per_launch(pb)
     achieved = sfu_ops / kern_s
-    roofline = {"bound": "alu", "pipe": "MUFU (special-function unit)", "achieved": achieved / 1e12,
+    roofline = {"bound": "alu", "pipe": "MUFU (special-function unit, log2-equivalent results)",
+                "achieved": achieved / 1e12,
                 "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": achieved / sfu_peak, "traffic": None,
                 "peak_source": f"{SFU_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock of measured)",
                 "kernel": "rhs_main<2, float>", "kernel_ms": kern_s * 1e3, "ops_per_launch": sfu_ops,

@@ -292,8 +292,9 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
   auto al16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
   const size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
+  const size_t ang32 = ang + (size_t)4 * ((pl->na2 + 1) / 2);   // + second-angle node pairs
   pl->smem64 = al16((size_t)(pl->tabc_count ? pl->tabc_count : pl->tab_count) * 8) + al16(ang * 8);
-  pl->smem32 = al16((size_t)pl->tab32_count * 8) + al16(ang * 4);
+  pl->smem32 = al16((size_t)pl->tab32_count * 8) + al16(ang32 * 4);
 }
 
 int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {

@@ -66,7 +66,7 @@ struct RhsArgs {
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
   double *tabc;                // D4_FULL: compact FP64 tables [Z row | lambda4 row | lambda3 rows] (precompute)
   void *kbuf;                  // FINITE_T: K[j][ip][r], j < N + n_ext_ang, in the kernel precision (main kernel)
-  float2 *tab32;               // FP32 node pairs (T[i], T[i+1] - T[i]; 0 at a row end), precompute kernel
+  float2 *tab32;               // FP32 tables (rows in line form, or finite-T (Z, lambda) pairs), precompute kernel
   const double *rad_x, *rad_w; // unit-interval GL rule on [0, 1]
   const double *a1_x, *a1_w;   // first angle rule
   const double *a2_x, *a2_w;   // second angle rule (D4)
@@ -191,6 +191,40 @@ __device__ __forceinline__ float lerp(const float2 *tab, float s2, float u_scale
   return lerp_at(tab, i0, w);
 }
 
+// FP32 table rows in line form (d=3, d=4): node i of a row of n nodes holds
+// (x, y) = (T_i - i d_i, (n-1) d_i), d_i = T_{i+1} - T_i (0 at the last node),
+// so that on [i, i+1] the linear interpolant is x + u1 y at the normalised
+// coordinate u1 = u/(n-1): one FMA, no interpolation weight.  A row is
+// addressed by its shared-memory byte address minus 8 x 0x4B400000 (mod 2^32,
+// Row32): the bit pattern of the floor value t = 1.5 2^23 + i (lerp_pos)
+// times 8 then added to it is the address of node i.
+struct Row32 {
+  unsigned b;
+};
+struct Pos32 {
+  unsigned ib;  // bit pattern of t, times 8
+  float u1;
+};
+__device__ __forceinline__ Row32 row32(const float2 *row) {
+  return {(unsigned)__cvta_generic_to_shared(row) - 0x5A000000u};
+}
+__device__ __forceinline__ Row32 row32_at(Row32 r, int entries) { return {r.b + 8u * (unsigned)entries}; }
+__device__ __forceinline__ Pos32 line_pos(float s2, float u_scale1, float u_off1, float nm1) {
+  float u1;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u1) : "f"(u_scale1), "f"(hw_lg2(s2)), "f"(u_off1));
+  const float t = __fmaf_rd(u1, nm1, 12582912.0f);
+  return {__float_as_uint(t) << 3, u1};
+}
+__device__ __forceinline__ float line_at(Row32 r, Pos32 p) {
+  float x, y;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(r.b + p.ib));
+  return fmaf(p.u1, y, x);
+}
+// table lookup at s2 in the kernel precision: FP64 values, or an FP32 line row
+__device__ __forceinline__ float look(Row32 r, float s2, float u_scale1, float u_off1, int n) {
+  return line_at(r, line_pos(s2, u_scale1, u_off1, (float)(n - 1)));
+}
+
 template <typename T>
 __device__ __forceinline__ T lerp_at(const T *tab, int i0, T w) {
   T a = tab[i0], b = tab[i0 + 1];
@@ -203,6 +237,9 @@ __device__ __forceinline__ T lerp(const T *tab, T s2, T u_scale, T u_off, int n)
   T w;
   lerp_pos(s2, u_scale, u_off, n, i0, w);
   return lerp_at(tab, i0, w);
+}
+__device__ __forceinline__ double look(const double *row, double s2, double u_scale, double u_off, int n) {
+  return lerp(row, s2, u_scale, u_off, n);
 }
 
 // Propagator denominator Z (omega^2 + s^2 + k^2 r(s^2/k^2)) + m^2, FP64.

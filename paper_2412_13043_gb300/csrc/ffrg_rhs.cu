@@ -317,10 +317,11 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
     }
   }
   // FP32 tables; the Z table (table 0, every stack row) carries the factor
-  // k^2 ln 2 of the FP32 propagator form.  d=3, d=4: (value, difference to
-  // the next node; 0 at a row end) pairs.  Finite T: (Z, lambda) pairs per
-  // node of each stack row, then one zero pair (the upper neighbour of the
-  // last node, read with weight 0).
+  // k^2 ln 2 of the FP32 propagator form.  d=3, d=4: rows in line form
+  // (T_i - i d_i, (n-1) d_i), d_i the difference to the next node (0 at a
+  // row end), from FP64 values.  Finite T: (Z, lambda) pairs per node of each
+  // stack row, then one zero pair (the upper neighbour of the last node, read
+  // with weight 0).
   const double kh = k2 * 0.6931471805599453094;
   const int z_count = a.n_stack * a.n_pts;
   if (a.model == FFRG_MODEL_D4_FULL) {
@@ -332,19 +333,19 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
       const double f = row == 0 ? kh : 1.0;
       const double v = a.tab[src];
       a.tabc[i] = v;
-      const float v32 = (float)(f * v);
-      const float d = col == np - 1 ? 0.0f : (float)(f * a.tab[src + 1]) - v32;
-      a.tab32[i] = make_float2(v32, d);
+      const double d = col == np - 1 ? 0.0 : f * (a.tab[src + 1] - v);
+      a.tab32[i] = make_float2((float)(f * v - col * d), (float)((np - 1) * d));
     }
   } else if (a.model == FFRG_MODEL_FINITE_T) {
     for (int i = tid0; i <= z_count; i += stride)
       a.tab32[i] = i < z_count ? make_float2((float)(kh * a.tab[i]), (float)a.tab[z_count + i]) : make_float2(0.f, 0.f);
   } else {
+    const int np = a.n_pts;
     for (int i = tid0; i < a.tab_count; i += stride) {
       const double f = i < z_count ? kh : 1.0;
-      const float v = (float)(f * a.tab[i]);
-      const float d = (i % a.n_pts == a.n_pts - 1) ? 0.0f : (float)(f * a.tab[i + 1]) - v;
-      a.tab32[i] = make_float2(v, d);
+      const int col = i % np;
+      const double d = col == np - 1 ? 0.0 : f * (a.tab[i + 1] - a.tab[i]);
+      a.tab32[i] = make_float2((float)(f * a.tab[i] - col * d), (float)((np - 1) * d));
     }
   }
   if (a.ext_done)
@@ -391,6 +392,7 @@ struct SmemLayout {
   using Tab = typename TabOf<T>::type;
   using P2 = typename Pair2<T>::type;
   Tab *tab;
+  float4 *cw4;  // FP32 kernels: second-angle nodes in pairs (x_2j, x_2j+1, w_2j, w_2j+1)
   P2 *cw2;
   T *c1, *s1, *w1;
   // table entries in shared memory: FP64 values, or the FP32 layout
@@ -400,6 +402,8 @@ struct SmemLayout {
   __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
     tab = (Tab *)base;
     size_t off = ((size_t)entries(a) * sizeof(Tab) + 15) & ~(size_t)15;
+    cw4 = (float4 *)(base + off);
+    if (sizeof(T) == 4) off += (size_t)((a.na2 + 1) / 2) * sizeof(float4);
     cw2 = (P2 *)(base + off);
     c1 = (T *)(cw2 + a.na2);
     s1 = c1 + a.na1;
@@ -417,6 +421,11 @@ __device__ __forceinline__ const float2 *table_src<float>(const RhsArgs &a) { re
 __device__ __forceinline__ double table_value(double v) { return v; }
 __device__ __forceinline__ float table_value(float2 v) { return v.x; }
 
+// handle of the table row that starts `off` entries into the staged tables:
+// an FP64 pointer, or an FP32 line row (Row32)
+__device__ __forceinline__ const double *tab_row(const SmemLayout<double> &S, int off) { return S.tab + off; }
+__device__ __forceinline__ Row32 tab_row(const SmemLayout<float> &S, int off) { return row32(S.tab + off); }
+
 // angle rules into shared memory in the kernel precision
 template <typename T>
 __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S) {
@@ -429,6 +438,14 @@ __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S)
   for (int i = threadIdx.x; i < a.na2; i += blockDim.x) {
     S.cw2[i].x = (T)a.a2_x[i];
     S.cw2[i].y = (T)a.a2_w[i];
+  }
+  if (sizeof(T) == 4) {
+    // an odd last node is paired with itself at weight 0
+    for (int j = threadIdx.x; j < (a.na2 + 1) / 2; j += blockDim.x) {
+      const int i0 = 2 * j, i1 = min(2 * j + 1, a.na2 - 1);
+      S.cw4[j] = make_float4((float)a.a2_x[i0], (float)a.a2_x[i1], (float)a.a2_w[i0],
+                             i1 > i0 ? (float)a.a2_w[i1] : 0.0f);
+    }
   }
 }
 
@@ -520,6 +537,7 @@ __device__ __forceinline__ RowAcc<T> d3_witem(const RhsArgs &a, const RhsArgs *s
                                            const KConst<T> &kc, int e, int c, int lane) {
   const T us = kc.us, uy1 = kc.uy1, sy = kc.sy;
   const int np = a.n_pts, na1 = a.na1, jb = a.jb, nblk = (na1 + jb - 1) / jb;
+  const auto Zt = tab_row(S, 0);
   const T p = (T)((e < a.n_ext_p) ? a.ext_pd[e] : 0.0);
   const int r0 = c * a.cr, r1 = min(r0 + a.cr, a.nr * nblk);
   RowAcc<T> acc;
@@ -530,7 +548,7 @@ __device__ __forceinline__ RowAcc<T> d3_witem(const RhsArgs &a, const RhsArgs *s
     T rs = 0;
     for (int j = j0; j < j1; ++j) {
       const T y = by + ty * S.c1[j];   // sy |q+p|^2, >= 0 up to rounding; lookups clamp
-      const T Z = lerp(S.tab, y, us, uy1, np);
+      const T Z = look(Zt, y, us, uy1, np);
       auto pole = [&]() { return pole_d3(sa, e, o, j); };
       rs += S.w1[j] * inv_prop<POLE>(a, Z, y, (T)0, kc, pole);
     }
@@ -666,6 +684,20 @@ __device__ __forceinline__ float va_shape_a(float q, float p, float c1, float, f
   return -fmaf(p, c1, q) * rsqrtf(A2);
 }
 
+__device__ __forceinline__ float lam3_full(const RhsArgs &a, Row32 L3, float y3, float us, float uy3, float va,
+                                          float vb) {
+  const int np = a.n_pts, na = a.n_va, nb = a.n_vb;
+  int ia, ib;
+  float wa, wb;
+  const Pos32 ps = line_pos(y3, us, uy3, (float)(np - 1));
+  shape_pos(va, na, ia, wa);
+  shape_pos(vb, nb, ib, wb);
+  const Row32 r00 = row32_at(L3, (ia * nb + ib) * np);
+  const int db = nb > 1 ? np : 0, da = na > 1 ? nb * np : 0;
+  const float v00 = line_at(r00, ps), v01 = line_at(row32_at(r00, db), ps);
+  const float v10 = line_at(row32_at(r00, da), ps), v11 = line_at(row32_at(r00, da + db), ps);
+  return (1.0f - wa) * ((1.0f - wb) * v00 + wb * v01) + wa * ((1.0f - wb) * v10 + wb * v11);
+}
 template <typename T, typename Tab>
 __device__ __forceinline__ T lam3_full(const RhsArgs &a, const Tab *L3, T y3, T us, T uy3, T va, T vb) {
   const int np = a.n_pts, na = a.n_va, nb = a.n_vb;
@@ -681,6 +713,68 @@ __device__ __forceinline__ T lam3_full(const RhsArgs &a, const Tab *L3, T y3, T 
   return ((T)1 - wa) * (((T)1 - wb) * v00 + wb * v01) + wa * (((T)1 - wb) * v10 + wb * v11);
 }
 
+// Two second-angle nodes per step in packed FP32 arithmetic (FFMA2, FMUL2,
+// FADD2: two lanes of FP32 in one instruction on sm_100 and later); the
+// special functions, the saturating coordinate FMA and the table loads stay
+// scalar.  Lookup of an FP32 line row at two arguments:
+__device__ __forceinline__ float2 look2(Row32 r, float2 s2, float us, float uo, float2 nm1) {
+  float2 u;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u.x) : "f"(us), "f"(hw_lg2(s2.x)), "f"(uo));
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u.y) : "f"(us), "f"(hw_lg2(s2.y)), "f"(uo));
+  const float2 t = __ffma2_rd(u, nm1, make_float2(12582912.0f, 12582912.0f));
+  return make_float2(line_at(r, {__float_as_uint(t.x) << 3, u.x}), line_at(r, {__float_as_uint(t.y) << 3, u.y}));
+}
+
+// Propagator of two lines as G = N R, R = 1/(Zs D + m^2 N), with the regulator
+// form of reg_g: (N, D) = (1 - 2^{-y}, y) for y >= log2(e), (1, series g(y))
+// below.  One reciprocal instead of two (reg_g's and the propagator's);
+// branch-free (setp / selp).  Only for m^2 >= 0 and Z >= 0 (no near-pole
+// test), where Zs D + m^2 N >= 0.
+__device__ __forceinline__ void prop2(float2 y, float2 Zs, float m2, float2 &N, float2 &R) {
+  const float2 E = make_float2(hw_ex2(-y.x), hw_ex2(-y.y));
+  const float2 Nd = __ffma2_rn(E, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  const float2 y2 = __fmul2_rn(y, y);
+  float2 t = __ffma2_rn(y2, make_float2(-6.3553057516916001e-8f, -6.3553057516916001e-8f),
+                        make_float2(5.2910945025509696e-6f, 5.2910945025509696e-6f));
+  t = __ffma2_rn(y2, t, make_float2(-4.6253423887351317e-4f, -4.6253423887351317e-4f));
+  t = __ffma2_rn(y2, t, make_float2(5.7762265046662109e-2f, 5.7762265046662109e-2f));
+  const float2 gs = __ffma2_rn(y2, t, __ffma2_rn(y, make_float2(0.5f, 0.5f),
+                                                 make_float2(1.4426950408889634f, 1.4426950408889634f)));
+  float2 D;
+  asm("{\n .reg .pred p, q;\n"
+      " setp.lt.f32 p, %4, 0f3FB8AA3B;\n setp.lt.f32 q, %5, 0f3FB8AA3B;\n"
+      " selp.f32 %0, 0f3F800000, %6, p;\n selp.f32 %1, 0f3F800000, %7, q;\n"
+      " selp.f32 %2, %8, %4, p;\n selp.f32 %3, %9, %5, q;\n}"
+      : "=f"(N.x), "=f"(N.y), "=f"(D.x), "=f"(D.y)
+      : "f"(y.x), "f"(y.y), "f"(Nd.x), "f"(Nd.y), "f"(gs.x), "f"(gs.y));
+  const float2 den = __ffma2_rn(Zs, D, __fmul2_rn(make_float2(m2, m2), N));
+  R = make_float2(hw_rcp(den.x), hw_rcp(den.y));
+}
+
+// sum_b w_b G(|q - p2|) lam3(.., b) lam3(.., c) of one (radial, first-angle)
+// row of the three-point block in FP32 (arguments as in d4_witem); the even
+// and odd nodes are summed separately and added at the end.
+__device__ __forceinline__ float tp_sum_x2(const RhsArgs &a, const SmemLayout<float> &S, const KConst<float> &kc,
+                                           Row32 Zt, Row32 L3, float b0, float t2y, float by, float sy_ab) {
+  const float us = kc.us, uy1 = kc.uy1, uy3 = kc.uy3, nm1 = (float)(a.n_pts - 1);
+  const float2 nm1v = make_float2(nm1, nm1), b0v = make_float2(b0, b0), nt2 = make_float2(-t2y, -t2y);
+  const float2 byv = make_float2(by, by), sabv = make_float2(sy_ab, sy_ab);
+  float2 rs = make_float2(0.0f, 0.0f);
+  const int npair = (a.na2 + 1) >> 1;
+  for (int j = 0; j < npair; ++j) {
+    const float4 cw = S.cw4[j];
+    const float2 By = __ffma2_rn(nt2, make_float2(cw.x, cw.y), b0v);   // sy |q - p2|^2
+    const float2 ZB = look2(Zt, By, us, uy1, nm1v);
+    float2 N, R;
+    prop2(By, ZB, kc.m2, N, R);
+    const float2 lb = look2(L3, __fadd2_rn(byv, By), us, uy3, nm1v);
+    const float2 lc = look2(L3, __fadd2_rn(sabv, By), us, uy3, nm1v);
+    const float2 P = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(cw.z, cw.w), N), R), lb);
+    rs = __ffma2_rn(P, lc, rs);
+  }
+  return rs.x + rs.y;
+}
+
 // d=4 vertex expansion: row = (radial node r, first-angle node ia), inner loop
 // over the second-angle nodes for the three-point block.  FULL: the D4_FULL
 // model (lambda3 on (S0, a, b); compact tables Z | lambda4 | lambda3 rows).
@@ -689,7 +783,7 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
                                            const KConst<T> &kc, int e, int c, int lane) {
   const T us = kc.us, sy = kc.sy;
   const int np = a.n_pts, np_ = a.n_ext_p, npsi = a.n_ext_ang, na1 = a.na1;
-  const auto *Zt = S.tab, *L3 = S.tab + (FULL ? 2 : 1) * np, *L4 = S.tab + (FULL ? 1 : 2) * np;
+  const auto Zt = tab_row(S, 0), L3 = tab_row(S, (FULL ? 2 : 1) * np), L4 = tab_row(S, (FULL ? 1 : 2) * np);
   int block, ip, jp = 0;
   if (e <= np_) {
     block = 0;
@@ -715,19 +809,19 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
     const T q = radial_q<T>(a, r), q2 = q * q, qp = q * p, c1 = S.c1[ia];
     const T A2 = q2 + p2 + (T)2 * qp * c1;   // >= 0 up to rounding; lookups clamp
     const T Ay = A2 * sy;
-    const T ZA = lerp(Zt, Ay, us, kc.uy1, np);
+    const T ZA = look(Zt, Ay, us, kc.uy1, np);
     auto pole_a = [&]() { return pole_d4<FULL ? FFRG_MODEL_D4_FULL : FFRG_MODEL_D4_VERTEX>(sa, e, r, ia, -1); };
     const T GA = inv_prop<POLE>(a, ZA, Ay, (T)0, kc, pole_a);
     T v;
     if (block == 0) {
-      const T l4 = lerp(L4, (q2 + p2) * sy, us, kc.uy2, np);
+      const T l4 = look(L4, (q2 + p2) * sy, us, kc.uy2, np);
       T l3;
       if constexpr (FULL) l3 = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, kc.uy3, va_shape_a(q, p, c1, q2, A2, p2),
                                          shape_b(q2, A2));   // legs q, -(q+p), p
-      else l3 = lerp(L3, (q2 + A2 + p2) * sy, us, kc.uy3, np);
+      else l3 = look(L3, (q2 + A2 + p2) * sy, us, kc.uy3, np);
       v = kc.sw2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
     } else if (block == 2) {
-      const T l4 = lerp(L4, (q2 + A2 + (T)2 * p2) * sy, us, kc.uy4, np);
+      const T l4 = look(L4, (q2 + A2 + (T)2 * p2) * sy, us, kc.uy4, np);
       v = kc.sw2 * GA * l4 * l4;
     } else {
       const T uy1 = kc.uy1, uy3 = kc.uy3;
@@ -735,7 +829,7 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
       if constexpr (FULL)
         la = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, uy3, va_shape_a(q, p, c1, q2, A2, p2),
                        shape_b(q2, A2));   // legs q, -(q+p1), p1
-      else la = lerp(L3, (q2 + A2 + p2) * sy, us, uy3, np);
+      else la = look(L3, (q2 + A2 + p2) * sy, us, uy3, np);
       // components (e1 along p1, e2 in the p1-p2 plane): q = q (c1, s1 c2, s1 s2'),
       // p1 = p (1, 0, 0), p2 = p (cpsi, spsi, 0)
       [[maybe_unused]] const T qs1 = q * S.s1[ia], x1 = q * c1 + p, x2 = q * c1 - p * cpsi, psp = p * spsi;
@@ -743,10 +837,11 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
       const T base = q2 + p2, t1 = (T)2 * qp * cpsi * c1, t2 = (T)2 * qp * spsi * S.s1[ia];
       const T by = base * sy, b0 = (base - t1) * sy, t2y = t2 * sy, sy_ab = (A2 + C2) * sy;
       T rs = 0;
-      for (int b = 0; b < a.na2; ++b) {
+      if constexpr (sizeof(T) == 4 && !FULL && !POLE) rs = tp_sum_x2(a, S, kc, Zt, L3, b0, t2y, by, sy_ab);
+      else for (int b = 0; b < a.na2; ++b) {
         const auto cw = S.cw2[b];
         const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
-        const T ZB = lerp(Zt, By, us, uy1, np);
+        const T ZB = look(Zt, By, us, uy1, np);
         auto pole_b = [&]() { return pole_d4<FULL ? FFRG_MODEL_D4_FULL : FFRG_MODEL_D4_VERTEX>(sa, e, r, ia, b); };
         const T GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
         T lb, lc;
@@ -765,8 +860,8 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
           lb = lam3_full(a, L3, by + By, us, uy3, a_b, shape_b(q2 * sy, By));   // legs q, -(q-p2), p2
           lc = lam3_full(a, L3, sy_ab + By, us, uy3, a_c, shape_b(Ay, By));     // legs q+p1, -(q-p2), -(p1+p2)
         } else {
-          lb = lerp(L3, by + By, us, uy3, np);
-          lc = lerp(L3, sy_ab + By, us, uy3, np);
+          lb = look(L3, by + By, us, uy3, np);
+          lc = look(L3, sy_ab + By, us, uy3, np);
         }
         rs += cw.y * GB * lb * lc;
       }
@@ -801,11 +896,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // The near-pole test can only fire with m^2 < 0 or a negative Z node (table
 // 0, every stack row).  Block-wide: every thread of the CTA must call it.
+// FP32 line rows do not hold node values, so the FP32 d=3 / d=4 kernels take
+// the signs from the FP64 tables, where the Z rows come first (the FP32 value
+// is the FP64 one times k^2 ln 2 > 0, rounded: the same sign).
 template <typename T>
 __device__ __forceinline__ bool pole_possible(const RhsArgs &a, const SmemLayout<T> &S, const KConst<T> &kc) {
   int neg = 0;
   const int nz = (a.model == FFRG_MODEL_D4_FULL ? 1 : a.n_stack) * a.n_pts;
-  for (int i = threadIdx.x; i < nz; i += blockDim.x) neg |= table_value(S.tab[i]) < (T)0;
+  if (sizeof(T) == 4 && a.model != FFRG_MODEL_FINITE_T)
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) neg |= a.tab[i] < 0.0;
+  else
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) neg |= table_value(S.tab[i]) < (T)0;
   return __syncthreads_or(neg) || kc.m2 < (T)0;
 }
 
