@@ -46,6 +46,10 @@ WORKLOAD = "d4 vertex-expansion RHS: 3 tables x 128 pts, 1281 ext x (128 rad x 6
 SFU_INNER = 4.5
 SFU_LEG = 2.5
 SFU_PER_CLK_SM = 16      # log2 / reciprocal results per clock per SM
+# DRAM bytes (read + write) of one rhs_main<2, float> launch on the default
+# d=4 workload, from an ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum: 78.8 KB + 0 B)
+D4_MAIN_DRAM_BYTES = 78848
 FP32_PER_CLK_SM = 128    # FP32 FMA lanes per SM
 
 
@@ -516,7 +520,7 @@ def main():
     achieved = sfu_ops / kern_s
     roofline = {"bound": "alu", "pipe": "MUFU (special-function unit, log2-equivalent results)",
                 "achieved": achieved / 1e12,
-                "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": achieved / sfu_peak, "traffic": None,
+                "peak": sfu_peak / 1e12, "unit": "Tops/s", "frac": achieved / sfu_peak, "traffic": D4_MAIN_DRAM_BYTES,
                 "peak_source": f"{SFU_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz (max SM clock of measured)",
                 "kernel": "rhs_main<2, float>", "kernel_ms": kern_s * 1e3, "ops_per_launch": sfu_ops,
                 "kernel_share_of_step": (main_ms / max(1, launches)) / (sum(step_ms) / K)}

@@ -319,6 +319,59 @@ __device__ bool stage_to_smem(T *sdst, const T *gsrc, int count, uint64_t *bar, 
   return bad == 0;
 }
 
+// The same staging, repeated: a CTA that stages several inputs in turn (the
+// serving kernel, one per flow segment) initialises `bar` once
+// (mbar_init_once) and passes the parity of each staging (0, 1, 0, ...).
+// Every thread calls it after a block barrier that ends all reads of the
+// previous contents of sdst; the async-proxy fence orders those reads before
+// the bulk copy's writes.
+__device__ __forceinline__ void mbar_init_once(uint64_t *bar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+template <typename T>
+__device__ bool stage_to_smem_phase(T *sdst, const T *gsrc, int count, uint64_t *bar, unsigned parity,
+                                    unsigned *status) {
+  size_t bytes = (size_t)count * sizeof(T);
+  uint32_t bulk = 0;
+  if ((((uintptr_t)gsrc) & 15u) == 0 && (((uintptr_t)sdst) & 15u) == 0 && bytes < (1u << 20))
+    bulk = (uint32_t)(bytes & ~(size_t)15);
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (bulk) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bulk)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(sdst)),
+          "l"(gsrc), "r"(bulk), "r"(smem_u32(bar))
+          : "memory");
+    } else {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    }
+  }
+  for (int i = (int)(bulk / sizeof(T)) + threadIdx.x; i < count; i += blockDim.x) sdst[i] = gsrc[i];
+  bool ok = true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok) {
+    raise_status(status, kStatusTimeout);
+    long long t1 = clock64();
+    while (!mbar_try_wait(bar, parity) && clock64() - t1 < kWaitCycles) {
+    }
+  }
+  int bad = __syncthreads_or(ok ? 0 : 1);
+  return bad == 0;
+}
+
 // ---------------------------------------------------------------------------
 // Shared helpers
 // ---------------------------------------------------------------------------

@@ -108,7 +108,8 @@ struct Slot {
   SlotLayout L;
   RhsArgs ra;
   FlowArgs fa;
-  bool fresh = false;  // admitted, first derivative not yet taken
+  bool fresh = false;    // admitted, first derivative not yet taken
+  bool cooling = false;  // retired while a tick that still lists it is in flight
 };
 
 // Compact device copies of the descriptors of one launch set.
@@ -119,6 +120,11 @@ struct LaunchSet {
   BatchList bl{};
   int n = 0, max_ny = 0;
 };
+
+// Ticks in flight at most: while the GPU runs one tick, the next is queued
+// behind it and the host reads the control blocks of the one before, retires,
+// admits and rebuilds the launch set for the tick after.
+constexpr int kTickDepth = 2;
 
 struct Server {
   ffrg_ctx lc;  // launch context of the scheduler thread (no allocations behind it)
@@ -132,11 +138,16 @@ struct Server {
   unsigned long long next_id = 1;
   std::vector<Slot> slots;
   size_t hbm_used = 0;
-  cudaStream_t st = nullptr;
-  FlowCtl *ctl_dev = nullptr, *ctl_host = nullptr;
+  cudaStream_t st = nullptr;  // ticks: batched steps and first derivatives
+  cudaStream_t io = nullptr;  // request uploads and result copies
+  FlowCtl *ctl_dev = nullptr;
+  FlowCtl *ctl_host = nullptr;        // pinned, kTickDepth snapshots of the control blocks
+  cudaEvent_t tick_ev[kTickDepth] = {};  // end of the tick whose snapshot is in buffer b
   unsigned *status_dev = nullptr;
   LaunchSet step_set, init_set;
-  unsigned char *stage_host = nullptr;  // pinned staging of descriptor uploads
+  unsigned char *stage_host = nullptr;  // pinned staging of descriptor uploads, two buffers
+  cudaEvent_t stage_ev[2] = {};         // end of the last upload from staging buffer 0 / 1
+  int stage_i = 0;
   size_t stage_bytes = 0;
   ffrg_serve_stats stats{};
   int fatal = FFRG_OK;
@@ -184,7 +195,7 @@ static int slot_setup(Server &S, int si) {
       {pl.a2_x, &x2, d},                              {pl.a2_w, &w2, d},
       {pl.psi_x, xp.data(), xp.size() * d},           {pl.psi_w, wp.data(), wp.size() * d}};
   for (auto &u : ups) {
-    cudaError_t e = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, S.st);
+    cudaError_t e = cudaMemcpyAsync(u.dst, u.src, u.n, cudaMemcpyHostToDevice, S.io);
     if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve upload");
   }
   FlowCtl hc;
@@ -202,10 +213,13 @@ static int slot_setup(Server &S, int si) {
   hc.Lambda = r->Lambda;
   hc.max_steps = o.max_steps;
   FlowCtl *ctl = S.ctl_dev + si;
-  cudaError_t e = cudaMemcpyAsync(ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, S.st);
+  cudaError_t e = cudaMemcpyAsync(ctl, &hc, sizeof(hc), cudaMemcpyHostToDevice, S.io);
   if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve ctl upload");
-  // the host copies above come from pageable memory and the stack: wait for them
-  e = cudaStreamSynchronize(S.st);
+  // The host copies above come from pageable memory and the stack: wait for
+  // them.  The slot is listed in no launch set of a tick in flight (slots
+  // cool down until those ticks end), and the flow's first launch on the
+  // tick stream is issued after this wait.
+  e = cudaStreamSynchronize(S.io);
   if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve upload sync");
   fill_args(&pl, &r->pb, &r->td, (const double *)(b + L.o_tab), r->Lambda, sl.ra);
   sl.ra.out = (double *)(b + L.o_raw);
@@ -251,10 +265,14 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
   BatchList &bl = ls.bl;
   bl = BatchList();
   if (n == 0) return FFRG_OK;
-  // host staging: descs | fa | lists | costs
-  RhsArgs *hd = (RhsArgs *)S.stage_host;
-  FlowArgs *hf = (FlowArgs *)(S.stage_host + sizeof(RhsArgs) * cap);
-  int *hl = (int *)(S.stage_host + (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap);
+  // host staging: descs | fa | lists | costs, in the staging buffer whose
+  // previous upload has ended (two buffers used in turn)
+  unsigned char *stage = S.stage_host + (size_t)S.stage_i * S.stage_bytes;
+  cudaError_t e = cudaEventSynchronize(S.stage_ev[S.stage_i]);
+  if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve staging wait");
+  RhsArgs *hd = (RhsArgs *)stage;
+  FlowArgs *hf = (FlowArgs *)(stage + sizeof(RhsArgs) * cap);
+  int *hl = (int *)(stage + (sizeof(RhsArgs) + sizeof(FlowArgs)) * cap);
   long long *hc = (long long *)(hl + list_ints(cap));
   int gn[kMaxBatchGroups] = {}, gitems[kMaxBatchGroups] = {};
   size_t gsmem[kMaxBatchGroups] = {};
@@ -285,9 +303,11 @@ static int build_set(Server &S, const std::vector<int> &ids, LaunchSet &ls) {
     gcost(g)[k + 1] = gcost(g)[k] + cost;
     gsmem[g] = std::max(gsmem[g], smem);
   }
-  cudaError_t e = cudaMemcpyAsync(ls.descs, S.stage_host, set_bytes_of(cap), cudaMemcpyHostToDevice, S.st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);  // the staging buffer is reused
+  // stream order on the tick stream: after every tick that reads the old set
+  e = cudaMemcpyAsync(ls.descs, stage, set_bytes_of(cap), cudaMemcpyHostToDevice, S.st);
+  if (e == cudaSuccess) e = cudaEventRecord(S.stage_ev[S.stage_i], S.st);
   if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve descriptor upload");
+  S.stage_i ^= 1;
   int *dl = ls.lists;
   const long long *dc = (const long long *)(dl + list_ints(cap));
   bl.descs = ls.descs;
@@ -318,14 +338,17 @@ static void finish_req(Server &S, ServeReq *r, int status) {
   else S.stats.completed++;
 }
 
-// Retire slot si: copy the state back (unless cancelled) and free the slot.
-static int retire(Server &S, int si, int status) {
+// Retire slot si after the tick whose control blocks are c: copy the state
+// back (unless cancelled) and let the slot cool down.  A finished flow's state
+// no longer changes (its later launches return at once), so the copy may run
+// beside the tick in flight.
+static int retire(Server &S, int si, const FlowCtl &c, int status) {
   Slot &sl = S.slots[si];
   ServeReq *r = sl.req;
-  const FlowCtl &c = S.ctl_host[si];
   if (status != FFRG_ECANCELED) {
     r->result.resize(sl.L.ny);
-    cudaError_t e = cudaMemcpy(r->result.data(), sl.fa.y, sl.L.ny * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(r->result.data(), sl.fa.y, sl.L.ny * sizeof(double), cudaMemcpyDeviceToHost, S.io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S.io);
     if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve result copy");
     r->stats.steps = c.steps;
     r->stats.rejects = c.rejects;
@@ -337,6 +360,7 @@ static int retire(Server &S, int si, int status) {
   finish_req(S, r, status);
   sl.req = nullptr;
   sl.fresh = false;
+  sl.cooling = true;
   return FFRG_OK;
 }
 
@@ -356,11 +380,11 @@ static int admit(Server &S) {
       if (S.queue.empty()) return FFRG_OK;
       r = S.queue.front();
       for (int i = 0; i < (int)S.slots.size() && si < 0; ++i)
-        if (!S.slots[i].req) si = i;
+        if (!S.slots[i].req && !S.slots[i].cooling) si = i;
       if (si < 0) return FFRG_OK;
       // a free slot whose buffer is large enough avoids a new allocation
       for (int i = 0; i < (int)S.slots.size(); ++i)
-        if (!S.slots[i].req && S.slots[i].cap >= r->need) {
+        if (!S.slots[i].req && !S.slots[i].cooling && S.slots[i].cap >= r->need) {
           si = i;
           break;
         }
@@ -369,7 +393,7 @@ static int admit(Server &S) {
       if (S.hbm_used + grow > S.opts.hbm_budget_bytes) {
         // release idle buffers before giving up
         for (auto &o : S.slots)
-          if (!o.req && o.buf && &o != &sl) {
+          if (!o.req && !o.cooling && o.buf && &o != &sl) {
             cudaFree(o.buf);
             S.hbm_used -= o.cap;
             o.buf = nullptr;
@@ -402,80 +426,121 @@ static int admit(Server &S) {
   }
 }
 
+struct Tick {
+  long long id;
+  std::vector<int> live;  // slots in this tick's launch set
+};
+
 static void scheduler(Server *Sp) {
   Server &S = *Sp;
   cudaSetDevice(S.lc.device);
   bool changed = true;
+  std::deque<Tick> inflight;
+  std::vector<std::pair<int, long long>> cooling;  // (slot, last tick that lists it)
+  long long launched = 0;                           // ids of issued ticks: 1, 2, ...
+  int st = FFRG_OK;
   while (true) {
     {
       std::unique_lock<std::mutex> lock(S.mu);
       if (S.stop) break;
     }
-    int st = admit(S);
-    // new flows: first derivative and first step size
-    std::vector<int> fresh, live;
+    std::vector<int> live;
+    for (int i = 0; i < (int)S.slots.size(); ++i)
+      if (S.slots[i].req) live.push_back(i);
+    // the oldest tick, once the pipeline is full or nothing is left to issue
+    if (!inflight.empty() && ((int)inflight.size() >= kTickDepth || live.empty())) {
+      Tick T = std::move(inflight.front());
+      inflight.pop_front();
+      const int b = (int)(T.id % kTickDepth);
+      cudaError_t e = cudaEventSynchronize(S.tick_ev[b]);
+      if (e != cudaSuccess) {
+        st = set_cuda_error(&S.lc, e, "serve tick");
+        break;
+      }
+      {
+        std::lock_guard<std::mutex> lock(S.mu);
+        S.stats.ticks++;
+        S.stats.resident = (int)T.live.size();
+        S.stats.peak_resident = std::max(S.stats.peak_resident, (int)T.live.size());
+        S.stats.hbm_in_use = S.hbm_used;
+      }
+      const FlowCtl *ctl = S.ctl_host + (size_t)b * S.slots.size();
+      for (int i : T.live) {
+        Slot &sl = S.slots[i];
+        if (!sl.req) continue;  // retired after an earlier tick
+        bool cancel;
+        {
+          std::lock_guard<std::mutex> lock(S.mu);
+          cancel = sl.req->cancel;
+        }
+        if (ctl[i].done || cancel) {
+          st = retire(S, i, ctl[i], cancel ? FFRG_ECANCELED : ctl[i].status);
+          if (st) break;
+          cooling.push_back({i, launched});
+          changed = true;
+        }
+      }
+      if (st) break;
+      for (size_t k = 0; k < cooling.size();)
+        if (cooling[k].second <= T.id) {
+          S.slots[cooling[k].first].cooling = false;
+          cooling[k] = cooling.back();
+          cooling.pop_back();
+        } else {
+          ++k;
+        }
+      S.cv.notify_all();
+      continue;  // re-read the slots before admitting
+    }
+    st = admit(S);
+    if (st) break;
+    // new flows: first derivative and first step size, queued before the next tick
+    std::vector<int> fresh;
+    live.clear();
     for (int i = 0; i < (int)S.slots.size(); ++i) {
       if (!S.slots[i].req) continue;
       live.push_back(i);
       if (S.slots[i].fresh) fresh.push_back(i);
     }
-    if (!st && !fresh.empty()) {
+    if (!fresh.empty()) {
       st = build_set(S, fresh, S.init_set);
       if (!st) st = launch_flow_batched_init(&S.lc, S.init_set.fa, S.init_set.n, S.init_set.max_ny, S.init_set.bl,
                                             S.st);
+      if (st) break;
       for (int i : fresh) S.slots[i].fresh = false;
       changed = true;
     }
-    if (st) {
-      S.fatal = st;
-      break;
-    }
     if (live.empty()) {
+      if (!inflight.empty()) continue;
       std::unique_lock<std::mutex> lock(S.mu);
       S.cv.wait_for(lock, std::chrono::milliseconds(2), [&] { return S.stop || !S.queue.empty(); });
       continue;
     }
     if (changed) {
       st = build_set(S, live, S.step_set);
+      if (st) break;
       changed = false;
     }
-    if (!st) st = launch_flow_batched_step(&S.lc, S.step_set.fa, S.step_set.n, S.step_set.max_ny, S.step_set.bl,
-                                           S.st);
-    cudaError_t e = cudaSuccess;
-    if (!st) e = cudaMemcpyAsync(S.ctl_host, S.ctl_dev, sizeof(FlowCtl) * S.slots.size(), cudaMemcpyDeviceToHost, S.st);
-    if (!st && e == cudaSuccess) e = cudaStreamSynchronize(S.st);
-    if (!st && e != cudaSuccess) st = set_cuda_error(&S.lc, e, "serve tick");
-    if (st) {
-      S.fatal = st;
+    // one tick: a batched step of every flow in the set, then a snapshot of
+    // the control blocks into this tick's host buffer
+    const long long id = ++launched;
+    const int b = (int)(id % kTickDepth);
+    st = launch_flow_batched_step(&S.lc, S.step_set.fa, S.step_set.n, S.step_set.max_ny, S.step_set.bl, S.st);
+    if (st) break;
+    cudaError_t e = cudaMemcpyAsync(S.ctl_host + (size_t)b * S.slots.size(), S.ctl_dev,
+                                    sizeof(FlowCtl) * S.slots.size(), cudaMemcpyDeviceToHost, S.st);
+    if (e == cudaSuccess) e = cudaEventRecord(S.tick_ev[b], S.st);
+    if (e != cudaSuccess) {
+      st = set_cuda_error(&S.lc, e, "serve tick");
       break;
     }
-    {
-      std::lock_guard<std::mutex> lock(S.mu);
-      S.stats.ticks++;
-      S.stats.resident = (int)live.size();
-      S.stats.peak_resident = std::max(S.stats.peak_resident, (int)live.size());
-      S.stats.hbm_in_use = S.hbm_used;
-    }
-    for (int i : live) {
-      const FlowCtl &c = S.ctl_host[i];
-      bool cancel;
-      {
-        std::lock_guard<std::mutex> lock(S.mu);
-        cancel = S.slots[i].req->cancel;
-      }
-      if (c.done || cancel) {
-        st = retire(S, i, cancel ? FFRG_ECANCELED : c.status);
-        changed = true;
-        if (st) break;
-      }
-    }
-    if (st) {
-      S.fatal = st;
-      break;
-    }
-    S.cv.notify_all();
+    inflight.push_back({id, std::move(live)});
   }
-  // drain: everything still queued or resident is cancelled
+  // drain: nothing of this server stays in flight; everything still queued or
+  // resident is cancelled (or failed with the fatal status)
+  if (st) S.fatal = st;
+  cudaStreamSynchronize(S.st);
+  cudaStreamSynchronize(S.io);
   std::lock_guard<std::mutex> lock(S.mu);
   for (auto &sl : S.slots)
     if (sl.req) {
@@ -518,12 +583,18 @@ extern "C" int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts) {
   const size_t set_bytes = set_bytes_of(cap);
   S->stage_bytes = set_bytes;
   cudaError_t e = cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->io, cudaStreamNonBlocking);
+  for (int b = 0; b < kTickDepth; ++b)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->tick_ev[b], cudaEventDisableTiming);
+  for (int b = 0; b < 2; ++b)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->stage_ev[b], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc((void **)&S->ctl_dev, sizeof(FlowCtl) * cap);
   if (e == cudaSuccess) e = cudaMemset(S->ctl_dev, 0, sizeof(FlowCtl) * cap);
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&S->ctl_host, sizeof(FlowCtl) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&S->ctl_host, sizeof(FlowCtl) * cap * kTickDepth);
   if (e == cudaSuccess) e = cudaMalloc((void **)&S->status_dev, 16);
   if (e == cudaSuccess) e = cudaMemset(S->status_dev, 0, 16);
-  if (e == cudaSuccess) e = cudaMallocHost((void **)&S->stage_host, set_bytes);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&S->stage_host, set_bytes * 2);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the memsets above ran on the legacy stream
   for (LaunchSet *ls : {&S->step_set, &S->init_set}) {
     unsigned char *blk = nullptr;
     if (e == cudaSuccess) e = cudaMalloc((void **)&blk, set_bytes);
@@ -539,6 +610,11 @@ extern "C" int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts) {
     cudaFreeHost(S->stage_host);
     cudaFree(S->step_set.descs);
     cudaFree(S->init_set.descs);
+    for (int b = 0; b < kTickDepth; ++b)
+      if (S->tick_ev[b]) cudaEventDestroy(S->tick_ev[b]);
+    for (int b = 0; b < 2; ++b)
+      if (S->stage_ev[b]) cudaEventDestroy(S->stage_ev[b]);
+    if (S->io) cudaStreamDestroy(S->io);
     if (S->st) cudaStreamDestroy(S->st);
     delete S;
     return st;
@@ -646,6 +722,7 @@ extern "C" int ffrg_serve_stop(ffrg_ctx *ctx) {
   if (S->th.joinable()) S->th.join();
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(S->st);
+  cudaStreamSynchronize(S->io);
   for (auto &sl : S->slots) cudaFree(sl.buf);
   for (auto &kv : S->reqs) delete kv.second;
   cudaFree(S->ctl_dev);
@@ -654,6 +731,9 @@ extern "C" int ffrg_serve_stop(ffrg_ctx *ctx) {
   cudaFreeHost(S->stage_host);
   cudaFree(S->step_set.descs);
   cudaFree(S->init_set.descs);
+  for (int b = 0; b < kTickDepth; ++b) cudaEventDestroy(S->tick_ev[b]);
+  for (int b = 0; b < 2; ++b) cudaEventDestroy(S->stage_ev[b]);
+  cudaStreamDestroy(S->io);
   cudaStreamDestroy(S->st);
   const int fatal = S->fatal;
   if (fatal) ctx->last_error = S->lc.last_error;
