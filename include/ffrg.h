@@ -305,7 +305,7 @@ typedef struct {
 
 typedef struct {
   long long submitted, admitted, completed, cancelled, rejected;
-  long long ticks;          /* batched steps launched */
+  long long ticks;          /* batched steps completed */
   int resident, queued, peak_resident, reserved0;
   size_t hbm_in_use;        /* bytes held by resident slots */
 } ffrg_serve_stats;

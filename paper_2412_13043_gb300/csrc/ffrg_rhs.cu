@@ -754,6 +754,22 @@ __device__ __forceinline__ void prop2(float2 y, float2 Zs, float m2, float2 &N, 
   R = make_float2(hw_rcp(den.x), hw_rcp(den.y));
 }
 
+// The same propagator for one line: G = N / (Zs D + m^2 N), one reciprocal.
+__device__ __forceinline__ float prop1(float y, float Zs, float m2) {
+  const float Nd = 1.0f - hw_ex2(-y);
+  const float y2 = y * y;
+  float t = fmaf(y2, -6.3553057516916001e-8f, 5.2910945025509696e-6f);
+  t = fmaf(y2, t, -4.6253423887351317e-4f);
+  t = fmaf(y2, t, 5.7762265046662109e-2f);
+  const float gs = fmaf(y2, t, fmaf(y, 0.5f, 1.4426950408889634f));
+  float N, D;
+  asm("{\n .reg .pred p;\n setp.lt.f32 p, %2, 0f3FB8AA3B;\n"
+      " selp.f32 %0, 0f3F800000, %3, p;\n selp.f32 %1, %4, %2, p;\n}"
+      : "=f"(N), "=f"(D)
+      : "f"(y), "f"(Nd), "f"(gs));
+  return N * hw_rcp(fmaf(Zs, D, m2 * N));
+}
+
 // sum_b w_b G(|q - p2|) lam3(.., b) lam3(.., c) of one (radial, first-angle)
 // row of the three-point block in FP32 (arguments as in d4_witem); the even
 // and odd nodes are summed separately and added at the end.
@@ -847,22 +863,30 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
         const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
         const T ZB = look(Zt, By, us, uy1, np);
         auto pole_b = [&]() { return pole_d4<FULL ? FFRG_MODEL_D4_FULL : FFRG_MODEL_D4_VERTEX>(sa, e, r, ia, b); };
-        const T GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
+        T GB;
+        if constexpr (sizeof(T) == 4 && !POLE) GB = prop1(By, ZB, kc.m2);   // one reciprocal
+        else GB = inv_prop<POLE>(a, ZB, By, (T)0, kc, pole_b);
         T lb, lc;
         if constexpr (FULL) {
-          T a_b, a_c;
+          T a_b, a_c, b_b, b_c;
           if constexpr (sizeof(T) == 8) {   // FP64: the oracle's form
             const T B2 = By;                  // sy = 1
             a_b = shape_a(q2, B2, p2);
             a_c = shape_a(A2, B2, C2);
+            b_b = shape_b(q2, By);
+            b_c = shape_b(Ay, By);
           } else {                          // FP32: from the leg components
             const T B2 = By * kc.isy, rB = rsqrtf(B2);
             a_b = (fmaf(hs, cw.x, hc) - q) * rB;                     // cos(q, -(q - p2))
             const T y1 = qs1 * cw.x, y2 = y1 - psp, z2 = qs1 * qs1 * fmaf(-cw.x, cw.x, (T)1);
             a_c = -fmaf(x1, x2, fmaf(y1, y2, z2)) * rsqrtf(A2) * rB;  // cos(q + p1, -(q - p2))
+            // both b = (s1 - s2)/(s1 + s2) from one reciprocal of the product of the denominators
+            const T qy = q2 * sy, db = qy + By, dc = Ay + By, rbc = hw_rcp(db * dc);
+            b_b = (qy - By) * dc * rbc;
+            b_c = (Ay - By) * db * rbc;
           }
-          lb = lam3_full(a, L3, by + By, us, uy3, a_b, shape_b(q2 * sy, By));   // legs q, -(q-p2), p2
-          lc = lam3_full(a, L3, sy_ab + By, us, uy3, a_c, shape_b(Ay, By));     // legs q+p1, -(q-p2), -(p1+p2)
+          lb = lam3_full(a, L3, by + By, us, uy3, a_b, b_b);   // legs q, -(q-p2), p2
+          lc = lam3_full(a, L3, sy_ab + By, us, uy3, a_c, b_c);     // legs q+p1, -(q-p2), -(p1+p2)
         } else {
           lb = look(L3, by + By, us, uy3, np);
           lc = look(L3, sy_ab + By, us, uy3, np);

@@ -122,6 +122,28 @@ def test_d4_full_size_sampled(ctx):
         _check(ctx, wl, k, sel=sel)
 
 
+@pytest.mark.parametrize("full", [False, True])
+def test_d4_near_pole_mixed_uses_fp64_propagator(ctx, full):
+    """m^2 = -0.999 k^2 with Z = 1: every propagator denominator Z k^2 h(x) + m^2
+    cancels to ~1e-3 k^2 at small momenta, so the mixed d=4 kernels run their
+    near-pole variant (scalar second-angle loop, FP64 recompute)."""
+    if full:
+        wl = fi.make_d4_full(seed=13, n_pts=16, n_va=3, n_vb=2, n_ext_ang=2, n_rad=12, n_ang1=6, n_ang2=5)
+    else:
+        wl = fi.make_d4(seed=12, n_pts=24, n_ext_ang=3, n_rad=16, n_ang1=8, n_ang2=5)
+    import paper_2412_13043_gb300 as ffrg
+    wl.tables[0][:] = 1.0
+    wl.problem.m2_over_k2 = -0.999
+    wl.problem.m2_shift = 0.0
+    for k in (1.0, 0.05):
+        ref = oracle.rhs(wl.problem, wl.tables, k)
+        scale = _termwise_scale(ctx, wl, k, ref)   # the Z block can cross zero
+        g64 = _run(ctx, wl, k, ffrg.FP64)
+        g32 = _run(ctx, wl, k, ffrg.MIXED)
+        assert np.max(np.abs(g64 - ref) / scale) < FP64_TOL
+        assert np.max(np.abs(g32 - ref) / scale) < MIXED_TOL, (k, np.max(np.abs(g32 - ref) / scale))
+
+
 def test_d4_litim_closed_forms_on_gpu(ctx):
     import paper_2412_13043_gb300 as ffrg
     k, M2 = 2.0, 1.0

@@ -148,6 +148,43 @@ def test_cancel_and_unknown_ticket():
     ctx.close()
 
 
+def test_cancel_resident_flow_and_reuse_its_slot():
+    """A flow cancelled while resident (ticks in flight behind it) finishes
+    with FFRG_ECANCELED; its slot cools down and then serves the next requests,
+    whose results equal their results alone, bitwise."""
+    import paper_2412_13043_gb300 as ffrg
+    reqs = _stream(4, seed=41)
+    alone = []
+    for rq in reqs:
+        ctx = gpu_context()
+        ctx.serve_start(max_slots=1)
+        tk = _submit(ctx, rq.workload)
+        alone.append(_wait(ctx, [tk], [rq.workload.problem.n_ext()])[tk])
+        assert ctx.serve_stop() == ffrg.OK
+        ctx.close()
+    long_wl = fi.make_d3(seed=5, n_pts=32, n_ext_p=16, n_rad=24, n_ang=12)
+    ctx = gpu_context()
+    ctx.serve_start(max_slots=1)
+    long_tk = _submit(ctx, long_wl, rtol=1e-12, atol=1e-15)
+    t0 = time.time()
+    while ctx.serve_stats()["ticks"] < 2:   # admitted and stepping
+        assert time.time() - t0 < 60.0
+        time.sleep(0.0005)
+    assert ctx.serve_cancel(long_tk) == ffrg.OK
+    tks = [_submit(ctx, rq.workload) for rq in reqs]
+    out = _wait(ctx, [long_tk] + tks, [long_wl.problem.n_ext()] + [rq.workload.problem.n_ext() for rq in reqs])
+    stats = ctx.serve_stats()
+    assert ctx.serve_stop() == ffrg.OK
+    ctx.close()
+    assert out[long_tk][0] == ffrg.ECANCELED
+    for a, tk in zip(alone, tks):
+        st, y, fs, _ = out[tk]
+        assert st == ffrg.OK and a[0] == ffrg.OK
+        assert np.array_equal(y, a[1])
+        assert fs["steps"] == a[2]["steps"]
+    assert stats["cancelled"] == 1 and stats["completed"] == len(reqs)
+
+
 def test_served_fermionic_flows_match_oracle():
     """Finite-T flows with a fermionic loop through the server."""
     import paper_2412_13043_gb300 as ffrg
