@@ -74,6 +74,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x of all ranks (x itself without a process group): every
+    timed region is charged at its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, t_max: float) -> float:
+    """Units of all ranks per second of the slowest rank (replicas: every rank
+    processes units_per_rank)."""
+    return world * units_per_rank / t_max
+
+
 def sfu_ops_per_launch(pb):
     """Algorithmic special-function work of one d=4 RHS launch (log2 units)."""
     n_p, n_psi = pb.n_ext_p, pb.n_ext_ang
@@ -467,13 +484,8 @@ def main():
     main_ms, launches = ctx.profile_read()
     ctx.set_profiling(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, stops)]
-    t_tot = sum(step_ms) / 1e3
-    t_max = t_tot
-    if dist is not None:
-        tt = torch.tensor([t_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * evals * K / t_max
+    t_max = max_over_ranks(sum(step_ms) / 1e3, dist, "cuda")
+    value = whole_job_rate(world, evals * K, t_max)
     assert ctx.status_read() == ffrg.OK
 
     # ---------------- FP64 path on the same workload ----------------
@@ -507,8 +519,8 @@ def main():
         host_out.copy_(out, non_blocking=True)
         ee[i].record(stream)
     barrier()
-    e2e_t = sum(s.elapsed_time(e) for s, e in zip(es, ee)) / 1e3
-    e2e_val = world * evals * K / e2e_t
+    e2e_t = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(es, ee)) / 1e3, dist, "cuda")
+    e2e_val = whole_job_rate(world, evals * K, e2e_t)
 
     # ---------------- roofline of the dominant kernel ----------------
     peaks = measured_peaks()
@@ -579,9 +591,9 @@ def main():
             "mixed_vs_fp64_max_rel_err": mixed_err,
             "e2e": {"value": e2e_val, "unit": "integrand evals/s",
                     "h2d_bytes_per_step": int(wl.tables.size * 8), "d2h_bytes_per_step": int(pb.n_ext() * 8)},
-            # per timed step: precompute_kernel and rhs_main (the d=4 main kernel writes
-            # the outputs itself); the L2 flush between steps is torch's fill kernel
-            "gpu_launches": 2 * K,
+            # per timed step and rank: precompute_kernel and rhs_main (the d=4 main
+            # kernel writes the outputs itself); the L2 flush is torch's fill kernel
+            "gpu_launches": 2 * K * world,
             "roofline": roofline,
             "clocks": clocks,
             "flows": flows,
