@@ -214,9 +214,10 @@ __device__ __forceinline__ double inv_prop(const RhsArgs &a, double Z, double y,
 template <bool POLE = true, typename Pole>
 __device__ __forceinline__ float inv_prop(const RhsArgs &a, float Zs, float y, float om2s, const KConst<float> &kc,
                                           Pole &&pole) {
-  // the denominator is one explicit FMA in both variants, so that kernels with
+  // the denominator is one explicit FMA in both variants and the sum an
+  // explicit add (no contraction with reg_g's product), so that kernels with
   // and without the test (serving, single flow) round it identically
-  const float t = reg_g(a.reg, y) + om2s;
+  const float t = __fadd_rn(reg_g(a.reg, y), om2s);
   if (POLE && Zs * t < kc.plim) return pole();
   return hw_rcp(fmaf(Zs, t, kc.m2));
 }
@@ -533,6 +534,129 @@ __device__ __forceinline__ double radial_q<double>(const RhsArgs &a, int r) { re
 template <>
 __device__ __forceinline__ float radial_q<float>(const RhsArgs &a, int r) { return a.radq32[r]; }
 
+// Two second-angle nodes per step in packed FP32 arithmetic (FFMA2, FMUL2,
+// FADD2: two lanes of FP32 in one instruction on sm_100 and later); the
+// special functions, the saturating coordinate FMA and the table loads stay
+// scalar.  Lookup of an FP32 line row at two arguments:
+__device__ __forceinline__ float2 look2(Row32 r, float2 s2, float us, float uo, float2 nm1) {
+  float2 u;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u.x) : "f"(us), "f"(hw_lg2(s2.x)), "f"(uo));
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u.y) : "f"(us), "f"(hw_lg2(s2.y)), "f"(uo));
+  const float2 t = __ffma2_rd(u, nm1, make_float2(12582912.0f, 12582912.0f));
+  return make_float2(line_at(r, {__float_as_uint(t.x) << 3, u.x}), line_at(r, {__float_as_uint(t.y) << 3, u.y}));
+}
+
+// Propagator of two lines as G = N R, R = 1/(Zs D + m2e N), with the regulator
+// form of reg_g: (N, D) = (1 - 2^{-y}, y) for y >= log2(e), (1, series g(y))
+// below, and m2e = m^2 (finite T: m^2 + Zs om2s, the frequency part).  One
+// reciprocal instead of two (reg_g's and the propagator's); branch-free
+// (setp / selp).  Only for m^2 >= 0 and Z >= 0 (no near-pole test), where the
+// denominator is >= 0.
+__device__ __forceinline__ void prop2(float2 y, float2 Zs, float2 m2e, float2 &N, float2 &R) {
+  const float2 E = make_float2(hw_ex2(-y.x), hw_ex2(-y.y));
+  const float2 Nd = __ffma2_rn(E, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  const float2 y2 = __fmul2_rn(y, y);
+  float2 t = __ffma2_rn(y2, make_float2(-6.3553057516916001e-8f, -6.3553057516916001e-8f),
+                        make_float2(5.2910945025509696e-6f, 5.2910945025509696e-6f));
+  t = __ffma2_rn(y2, t, make_float2(-4.6253423887351317e-4f, -4.6253423887351317e-4f));
+  t = __ffma2_rn(y2, t, make_float2(5.7762265046662109e-2f, 5.7762265046662109e-2f));
+  const float2 gs = __ffma2_rn(y2, t, __ffma2_rn(y, make_float2(0.5f, 0.5f),
+                                                 make_float2(1.4426950408889634f, 1.4426950408889634f)));
+  float2 D;
+  asm("{\n .reg .pred p, q;\n"
+      " setp.lt.f32 p, %4, 0f3FB8AA3B;\n setp.lt.f32 q, %5, 0f3FB8AA3B;\n"
+      " selp.f32 %0, 0f3F800000, %6, p;\n selp.f32 %1, 0f3F800000, %7, q;\n"
+      " selp.f32 %2, %8, %4, p;\n selp.f32 %3, %9, %5, q;\n}"
+      : "=f"(N.x), "=f"(N.y), "=f"(D.x), "=f"(D.y)
+      : "f"(y.x), "f"(y.y), "f"(Nd.x), "f"(Nd.y), "f"(gs.x), "f"(gs.y));
+  const float2 den = __ffma2_rn(Zs, D, __fmul2_rn(m2e, N));
+  R = make_float2(hw_rcp(den.x), hw_rcp(den.y));
+}
+
+// The same propagator for one line: G = N / (Zs D + m2e N), one reciprocal.
+__device__ __forceinline__ float prop1(float y, float Zs, float m2e) {
+  const float Nd = 1.0f - hw_ex2(-y);
+  const float y2 = y * y;
+  float t = fmaf(y2, -6.3553057516916001e-8f, 5.2910945025509696e-6f);
+  t = fmaf(y2, t, -4.6253423887351317e-4f);
+  t = fmaf(y2, t, 5.7762265046662109e-2f);
+  const float gs = fmaf(y2, t, fmaf(y, 0.5f, 1.4426950408889634f));
+  float N, D;
+  asm("{\n .reg .pred p;\n setp.lt.f32 p, %2, 0f3FB8AA3B;\n"
+      " selp.f32 %0, 0f3F800000, %3, p;\n selp.f32 %1, %4, %2, p;\n}"
+      : "=f"(N), "=f"(D)
+      : "f"(y), "f"(Nd), "f"(gs));
+  return N * hw_rcp(fmaf(Zs, D, m2e * N));
+}
+
+// One FP32 row of angle nodes j0 .. j1-1 without the near-pole test: pairs
+// of nodes in packed FP32 with the one-reciprocal propagator, an odd last
+// node alone.  d=3: sum_j v_j G(|q+p|) at y_j = by + ty c_j.
+__device__ __forceinline__ float d3_row_x2(const SmemLayout<float> &S, const KConst<float> &kc, Row32 Zt, int np,
+                                           float by, float ty, int j0, int j1) {
+  const float nm1 = (float)(np - 1);
+  const float2 nm1v = make_float2(nm1, nm1), byv = make_float2(by, by), tyv = make_float2(ty, ty);
+  const float2 m2v = make_float2(kc.m2, kc.m2);
+  float2 rs = make_float2(0.0f, 0.0f);
+  int j = j0;
+  for (; j + 1 < j1; j += 2) {
+    const float2 y = __ffma2_rn(tyv, make_float2(S.c1[j], S.c1[j + 1]), byv);
+    const float2 Z = look2(Zt, y, kc.us, kc.uy1, nm1v);
+    float2 N, R;
+    prop2(y, Z, m2v, N, R);
+    rs = __ffma2_rn(__fmul2_rn(make_float2(S.w1[j], S.w1[j + 1]), N), R, rs);
+  }
+  float t = rs.x + rs.y;
+  if (j < j1) {
+    const float y = fmaf(ty, S.c1[j], by);
+    t = fmaf(S.w1[j], prop1(y, look(Zt, y, kc.us, kc.uy1, np), kc.m2), t);
+  }
+  return t;
+}
+
+// Finite T: sum_j v_j lam(j, s) G(j, s) of one K row from the (Z, lambda)
+// node pairs of its stack row (interpolation weight form), om2s the row's
+// scaled frequency^2 (mass term m^2 + Zs om2s per line).
+__device__ __forceinline__ void zl_pos(float y, float us, float uo, float nm1, int &i0, float &w) {
+  float u1;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u1) : "f"(us), "f"(hw_lg2(y)), "f"(uo));
+  const float t = __fmaf_rd(u1, nm1, 12582912.0f);
+  i0 = __float_as_int(t) - 0x4B400000;
+  w = fmaf(u1, nm1, 12582912.0f - t);
+}
+__device__ __forceinline__ float ftk_row_x2(const SmemLayout<float> &S, const KConst<float> &kc, const float2 *zl,
+                                            int np, int na1, float om2s, float by, float ty) {
+  const float nm1 = (float)(np - 1);
+  const float2 byv = make_float2(by, by), tyv = make_float2(ty, ty), omv = make_float2(om2s, om2s);
+  const float2 m2v = make_float2(kc.m2, kc.m2);
+  float2 rs = make_float2(0.0f, 0.0f);
+  int j = 0;
+  for (; j + 1 < na1; j += 2) {
+    const float2 y = __ffma2_rn(tyv, make_float2(S.c1[j], S.c1[j + 1]), byv);
+    int i0, i1;
+    float w0, w1;
+    zl_pos(y.x, kc.us, kc.uy1, nm1, i0, w0);
+    zl_pos(y.y, kc.us, kc.uy1, nm1, i1, w1);
+    const float2 a0 = zl[i0], b0 = zl[i0 + 1], a1 = zl[i1], b1 = zl[i1 + 1];
+    const float2 Z = make_float2(fmaf(w0, b0.x - a0.x, a0.x), fmaf(w1, b1.x - a1.x, a1.x));
+    const float2 L = make_float2(fmaf(w0, b0.y - a0.y, a0.y), fmaf(w1, b1.y - a1.y, a1.y));
+    float2 N, R;
+    prop2(y, Z, __ffma2_rn(Z, omv, m2v), N, R);
+    rs = __ffma2_rn(__fmul2_rn(__fmul2_rn(make_float2(S.w1[j], S.w1[j + 1]), L), N), R, rs);
+  }
+  float t = rs.x + rs.y;
+  if (j < na1) {
+    const float y = fmaf(ty, S.c1[j], by);
+    int i0;
+    float w0;
+    zl_pos(y, kc.us, kc.uy1, nm1, i0, w0);
+    const float2 a0 = zl[i0], b0 = zl[i0 + 1];
+    const float Z = fmaf(w0, b0.x - a0.x, a0.x), L = fmaf(w0, b0.y - a0.y, a0.y);
+    t = fmaf(S.w1[j] * L, prop1(y, Z, fmaf(Z, om2s, kc.m2)), t);
+  }
+  return t;
+}
+
 // d=3, T=0: row = (radial node o, block of jb angle nodes);
 // sum_j v_j G(|q+p|)
 template <typename T, bool POLE>
@@ -547,13 +671,15 @@ __device__ __forceinline__ RowAcc<T> d3_witem(const RhsArgs &a, const RhsArgs *s
   for (int rr = r0 + lane; rr < r1; rr += 32) {
     const int o = rr / nblk, j0 = (rr - o * nblk) * jb, j1 = min(j0 + jb, na1);
     const T q = radial_q<T>(a, o);
-    const T by = (q * q + p * p) * sy, ty = (T)2 * q * p * sy;
+    // explicit FMAs: the single-flow and serving kernels must round alike
+    const T by = fma(q, q, p * p) * sy, ty = (T)2 * q * p * sy;
     T rs = 0;
-    for (int j = j0; j < j1; ++j) {
-      const T y = by + ty * S.c1[j];   // sy |q+p|^2, >= 0 up to rounding; lookups clamp
+    if constexpr (sizeof(T) == 4 && !POLE) rs = d3_row_x2(S, kc, Zt, np, by, ty, j0, j1);
+    else for (int j = j0; j < j1; ++j) {
+      const T y = fma(ty, S.c1[j], by);   // sy |q+p|^2, >= 0 up to rounding; lookups clamp
       const T Z = look(Zt, y, us, uy1, np);
       auto pole = [&]() { return pole_d3(sa, e, o, j); };
-      rs += S.w1[j] * inv_prop<POLE>(a, Z, y, (T)0, kc, pole);
+      rs = fma(S.w1[j], inv_prop<POLE>(a, Z, y, (T)0, kc, pole), rs);
     }
     acc.add(radial_F<T>(a, o), rs);
   }
@@ -599,16 +725,17 @@ __device__ __forceinline__ void ftk_rows(const RhsArgs &a, const RhsArgs *sa, co
   const int r0 = c * a.cr, r1 = min(r0 + a.cr, nr);
   for (int r = r0 + lane; r < r1; r += 32) {
     const T q = radial_q<T>(a, r);
-    const T by = (q * q + p * p) * sy, ty = (T)2 * q * p * sy;
+    const T by = fma(q, q, p * p) * sy, ty = (T)2 * q * p * sy;   // explicit FMAs, as in d3_witem
     T rs = 0;
-    for (int j = 0; j < na1; ++j) {
-      const T y = by + ty * S.c1[j];
+    if constexpr (sizeof(T) == 4 && !POLE) rs = ftk_row_x2(S, kc, S.tab + (size_t)srow * np, np, na1, om2s, by, ty);
+    else for (int j = 0; j < na1; ++j) {
+      const T y = fma(ty, S.c1[j], by);
       int i0;
       T w, Z, Lv;
       lerp_pos(y, us, uy1, np, i0, w);
       zl_lookup(S.tab, a, srow, i0, w, Z, Lv);
       auto pole = [&]() { return pole_ftk(sa, ip, jk, r, j); };
-      rs += S.w1[j] * Lv * inv_prop<POLE>(a, Z, y, om2s, kc, pole);
+      rs = fma(S.w1[j] * Lv, inv_prop<POLE>(a, Z, y, om2s, kc, pole), rs);
     }
     K[r] = rs;
   }
@@ -716,60 +843,6 @@ __device__ __forceinline__ T lam3_full(const RhsArgs &a, const Tab *L3, T y3, T 
   return ((T)1 - wa) * (((T)1 - wb) * v00 + wb * v01) + wa * (((T)1 - wb) * v10 + wb * v11);
 }
 
-// Two second-angle nodes per step in packed FP32 arithmetic (FFMA2, FMUL2,
-// FADD2: two lanes of FP32 in one instruction on sm_100 and later); the
-// special functions, the saturating coordinate FMA and the table loads stay
-// scalar.  Lookup of an FP32 line row at two arguments:
-__device__ __forceinline__ float2 look2(Row32 r, float2 s2, float us, float uo, float2 nm1) {
-  float2 u;
-  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u.x) : "f"(us), "f"(hw_lg2(s2.x)), "f"(uo));
-  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u.y) : "f"(us), "f"(hw_lg2(s2.y)), "f"(uo));
-  const float2 t = __ffma2_rd(u, nm1, make_float2(12582912.0f, 12582912.0f));
-  return make_float2(line_at(r, {__float_as_uint(t.x) << 3, u.x}), line_at(r, {__float_as_uint(t.y) << 3, u.y}));
-}
-
-// Propagator of two lines as G = N R, R = 1/(Zs D + m^2 N), with the regulator
-// form of reg_g: (N, D) = (1 - 2^{-y}, y) for y >= log2(e), (1, series g(y))
-// below.  One reciprocal instead of two (reg_g's and the propagator's);
-// branch-free (setp / selp).  Only for m^2 >= 0 and Z >= 0 (no near-pole
-// test), where Zs D + m^2 N >= 0.
-__device__ __forceinline__ void prop2(float2 y, float2 Zs, float m2, float2 &N, float2 &R) {
-  const float2 E = make_float2(hw_ex2(-y.x), hw_ex2(-y.y));
-  const float2 Nd = __ffma2_rn(E, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
-  const float2 y2 = __fmul2_rn(y, y);
-  float2 t = __ffma2_rn(y2, make_float2(-6.3553057516916001e-8f, -6.3553057516916001e-8f),
-                        make_float2(5.2910945025509696e-6f, 5.2910945025509696e-6f));
-  t = __ffma2_rn(y2, t, make_float2(-4.6253423887351317e-4f, -4.6253423887351317e-4f));
-  t = __ffma2_rn(y2, t, make_float2(5.7762265046662109e-2f, 5.7762265046662109e-2f));
-  const float2 gs = __ffma2_rn(y2, t, __ffma2_rn(y, make_float2(0.5f, 0.5f),
-                                                 make_float2(1.4426950408889634f, 1.4426950408889634f)));
-  float2 D;
-  asm("{\n .reg .pred p, q;\n"
-      " setp.lt.f32 p, %4, 0f3FB8AA3B;\n setp.lt.f32 q, %5, 0f3FB8AA3B;\n"
-      " selp.f32 %0, 0f3F800000, %6, p;\n selp.f32 %1, 0f3F800000, %7, q;\n"
-      " selp.f32 %2, %8, %4, p;\n selp.f32 %3, %9, %5, q;\n}"
-      : "=f"(N.x), "=f"(N.y), "=f"(D.x), "=f"(D.y)
-      : "f"(y.x), "f"(y.y), "f"(Nd.x), "f"(Nd.y), "f"(gs.x), "f"(gs.y));
-  const float2 den = __ffma2_rn(Zs, D, __fmul2_rn(make_float2(m2, m2), N));
-  R = make_float2(hw_rcp(den.x), hw_rcp(den.y));
-}
-
-// The same propagator for one line: G = N / (Zs D + m^2 N), one reciprocal.
-__device__ __forceinline__ float prop1(float y, float Zs, float m2) {
-  const float Nd = 1.0f - hw_ex2(-y);
-  const float y2 = y * y;
-  float t = fmaf(y2, -6.3553057516916001e-8f, 5.2910945025509696e-6f);
-  t = fmaf(y2, t, -4.6253423887351317e-4f);
-  t = fmaf(y2, t, 5.7762265046662109e-2f);
-  const float gs = fmaf(y2, t, fmaf(y, 0.5f, 1.4426950408889634f));
-  float N, D;
-  asm("{\n .reg .pred p;\n setp.lt.f32 p, %2, 0f3FB8AA3B;\n"
-      " selp.f32 %0, 0f3F800000, %3, p;\n selp.f32 %1, %4, %2, p;\n}"
-      : "=f"(N), "=f"(D)
-      : "f"(y), "f"(Nd), "f"(gs));
-  return N * hw_rcp(fmaf(Zs, D, m2 * N));
-}
-
 // sum_b w_b G(|q - p2|) lam3(.., b) lam3(.., c) of one (radial, first-angle)
 // row of the three-point block in FP32 (arguments as in d4_witem); the even
 // and odd nodes are summed separately and added at the end.
@@ -777,7 +850,7 @@ __device__ __forceinline__ float tp_sum_x2(const RhsArgs &a, const SmemLayout<fl
                                            Row32 Zt, Row32 L3, float b0, float t2y, float by, float sy_ab) {
   const float us = kc.us, uy1 = kc.uy1, uy3 = kc.uy3, nm1 = (float)(a.n_pts - 1);
   const float2 nm1v = make_float2(nm1, nm1), b0v = make_float2(b0, b0), nt2 = make_float2(-t2y, -t2y);
-  const float2 byv = make_float2(by, by), sabv = make_float2(sy_ab, sy_ab);
+  const float2 byv = make_float2(by, by), sabv = make_float2(sy_ab, sy_ab), m2v = make_float2(kc.m2, kc.m2);
   float2 rs = make_float2(0.0f, 0.0f);
   const int npair = (a.na2 + 1) >> 1;
 #pragma unroll 8   // independent pairs in flight: 8 % faster than no unrolling, 2 % than 4
@@ -786,7 +859,7 @@ __device__ __forceinline__ float tp_sum_x2(const RhsArgs &a, const SmemLayout<fl
     const float2 By = __ffma2_rn(nt2, make_float2(cw.x, cw.y), b0v);   // sy |q - p2|^2
     const float2 ZB = look2(Zt, By, us, uy1, nm1v);
     float2 N, R;
-    prop2(By, ZB, kc.m2, N, R);
+    prop2(By, ZB, m2v, N, R);
     const float2 lb = look2(L3, __fadd2_rn(byv, By), us, uy3, nm1v);
     const float2 lc = look2(L3, __fadd2_rn(sabv, By), us, uy3, nm1v);
     const float2 P = __fmul2_rn(__fmul2_rn(__fmul2_rn(make_float2(cw.z, cw.w), N), R), lb);
