@@ -167,7 +167,8 @@ __device__ __forceinline__ void lerp_pos(double s2, double u_scale, double u_off
 // NaN, both saturated to 0 (the first node, as for s < x_min).  floor(u) comes
 // from u1 (n-1) + 1.5*2^23 rounded towards -inf: the low mantissa bits of the
 // sum hold floor(u), so no float<->int conversion is needed.  At u = n-1 this
-// gives i0 = n-1, w = 0; the FP32 node pairs carry a zero difference there.
+// gives i0 = n-1, w = 0: the caller's table needs a readable entry after the
+// last node (read with weight 0).  Line-form rows (below) use u1 itself.
 __device__ __forceinline__ void lerp_pos(float s2, float u_scale1, float u_off1, int n, int &i0, float &w) {
   const float nm1 = (float)(n - 1);
   float u1;
@@ -176,19 +177,6 @@ __device__ __forceinline__ void lerp_pos(float s2, float u_scale1, float u_off1,
   const float t = __fmaf_rd(u1, nm1, magic);
   i0 = __float_as_int(t) - 0x4B400000;
   w = fmaf(u1, nm1, magic - t);
-}
-
-// FP32 lookup on node pairs: one 8-byte shared load and one FMA
-__device__ __forceinline__ float lerp_at(const float2 *tab, int i0, float w) {
-  const float2 v = tab[i0];
-  return fmaf(w, v.y, v.x);
-}
-
-__device__ __forceinline__ float lerp(const float2 *tab, float s2, float u_scale1, float u_off1, int n) {
-  int i0;
-  float w;
-  lerp_pos(s2, u_scale1, u_off1, n, i0, w);
-  return lerp_at(tab, i0, w);
 }
 
 // FP32 table rows in line form (d=3, d=4): node i of a row of n nodes holds

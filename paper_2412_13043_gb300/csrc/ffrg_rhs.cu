@@ -617,16 +617,8 @@ __device__ __forceinline__ float d3_row_x2(const SmemLayout<float> &S, const KCo
 // Finite T: sum_j v_j lam(j, s) G(j, s) of one K row from the (Z, lambda)
 // node pairs of its stack row (interpolation weight form), om2s the row's
 // scaled frequency^2 (mass term m^2 + Zs om2s per line).
-__device__ __forceinline__ void zl_pos(float y, float us, float uo, float nm1, int &i0, float &w) {
-  float u1;
-  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u1) : "f"(us), "f"(hw_lg2(y)), "f"(uo));
-  const float t = __fmaf_rd(u1, nm1, 12582912.0f);
-  i0 = __float_as_int(t) - 0x4B400000;
-  w = fmaf(u1, nm1, 12582912.0f - t);
-}
 __device__ __forceinline__ float ftk_row_x2(const SmemLayout<float> &S, const KConst<float> &kc, const float2 *zl,
                                             int np, int na1, float om2s, float by, float ty) {
-  const float nm1 = (float)(np - 1);
   const float2 byv = make_float2(by, by), tyv = make_float2(ty, ty), omv = make_float2(om2s, om2s);
   const float2 m2v = make_float2(kc.m2, kc.m2);
   float2 rs = make_float2(0.0f, 0.0f);
@@ -635,8 +627,8 @@ __device__ __forceinline__ float ftk_row_x2(const SmemLayout<float> &S, const KC
     const float2 y = __ffma2_rn(tyv, make_float2(S.c1[j], S.c1[j + 1]), byv);
     int i0, i1;
     float w0, w1;
-    zl_pos(y.x, kc.us, kc.uy1, nm1, i0, w0);
-    zl_pos(y.y, kc.us, kc.uy1, nm1, i1, w1);
+    lerp_pos(y.x, kc.us, kc.uy1, np, i0, w0);
+    lerp_pos(y.y, kc.us, kc.uy1, np, i1, w1);
     const float2 a0 = zl[i0], b0 = zl[i0 + 1], a1 = zl[i1], b1 = zl[i1 + 1];
     const float2 Z = make_float2(fmaf(w0, b0.x - a0.x, a0.x), fmaf(w1, b1.x - a1.x, a1.x));
     const float2 L = make_float2(fmaf(w0, b0.y - a0.y, a0.y), fmaf(w1, b1.y - a1.y, a1.y));
@@ -649,7 +641,7 @@ __device__ __forceinline__ float ftk_row_x2(const SmemLayout<float> &S, const KC
     const float y = fmaf(ty, S.c1[j], by);
     int i0;
     float w0;
-    zl_pos(y, kc.us, kc.uy1, nm1, i0, w0);
+    lerp_pos(y, kc.us, kc.uy1, np, i0, w0);
     const float2 a0 = zl[i0], b0 = zl[i0 + 1];
     const float Z = fmaf(w0, b0.x - a0.x, a0.x), L = fmaf(w0, b0.y - a0.y, a0.y);
     t = fmaf(S.w1[j] * L, prop1(y, Z, fmaf(Z, om2s, kc.m2)), t);
