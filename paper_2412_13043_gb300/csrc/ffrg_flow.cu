@@ -3,8 +3,8 @@
 // (Sec. 5.2.2, Eqs. assVar / flowVar) and the explicit-stepper parameters dt,
 // minimal_dt, maximal_dt, abs_tol, rel_tol (Sec. 5.2.1 RK45, App. C).
 //
-// One step = six stages of [stage state -> RHS (precompute / main / finalize)
-// -> derivative map], then one single-CTA control kernel that forms the FP64
+// One step = six stages of [stage state -> RHS (precompute / main, finite T
+// also the contraction) -> derivative map], then one single-CTA control kernel that forms the FP64
 // error norm, accepts or rejects, updates the step size and decides the next
 // step (or that the flow is done).  All of it reads its scalars (t, h, k, m^2,
 // done) from a device control block, so one step is captured once into a CUDA

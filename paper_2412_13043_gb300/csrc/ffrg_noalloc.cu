@@ -1,6 +1,6 @@
 // ffrg_rhs_noalloc: the RHS of ffrg_rhs for callers that cannot allocate
-// device memory.  It runs the same kernels (precompute, main, finalize) as
-// ffrg_rhs, but all of its scratch -- quadrature rules, per-radial factors,
+// device memory.  It runs the same kernels (precompute, main, finite-T
+// contraction) as ffrg_rhs, but all of its scratch -- quadrature rules, per-radial factors,
 // partial sums, the FP32 table mirror and a status word -- lives in one
 // file-scope device array of fixed size instead of cudaMalloc'd buffers.  No
 // context, no cudaMalloc/cudaFree, no allocating library routine.

@@ -8,17 +8,22 @@
 //   1. precompute: per radial node (and Matsubara index) the p-independent
 //      factor F = w q^{d-1} dR(q) G(q)^2 [lam(n,q)] in FP64 (the paper's
 //      generated kernels hoist repeated regulator/interpolator calls the same
-//      way, Sec. 5.3.2), plus the FP32 mirror of the tables;
-//   2. main: persistent CTAs walk work items (external point x chunk of
-//      radial rows); tables are staged into shared memory by a TMA bulk copy
-//      (cp.async.bulk + mbarrier, bounded wait); threads take angular rows,
-//      accumulate in FP64 (FP64 path) or sum a row in FP32 and add it into an
-//      FP64 accumulator (mixed path); a warp-shuffle + shared-memory tree
-//      writes one partial per item;
-//   3. finalize: fixed-order sum of the partials of each external point, the
-//      overall normalisation, and a non-finite check into the status word.
-// The reduction order depends only on the problem shape, never on the grid
-// size or on other work in flight.
+//      way, Sec. 5.3.2), the FP32 tables (d=3, d=4: line-form rows; finite T:
+//      (Z, lambda) node pairs) and the per-RHS constant block;
+//   2. main (rhs_main): persistent CTAs stage the tables into shared memory
+//      by a TMA bulk copy (cp.async.bulk + mbarrier, bounded wait); warps take
+//      warp-sized work items (external point x chunk of rows) from a device
+//      counter; lanes take rows and run the row's angle loop in the kernel
+//      precision (FP32: pairs of nodes in packed FP32 where no near-pole test
+//      is needed); FP64 accumulation, or Kahan FP32 with an error-free
+//      two-sum warp tree (mixed); the warp that completes an external point
+//      sums its partials in a fixed order and writes the output.  Finite T:
+//      the main kernel fills the angle-integrated kernel K(p, q) instead;
+//   3. finite T only: the contraction of K with the radial factors, one
+//      block per output.
+// Serving runs the same item functions from batched kernels over many flows
+// (bottom of this file).  The reduction order depends only on the problem
+// shape, never on the grid size or on other work in flight.
 #include <math.h>
 
 #include <algorithm>

@@ -8,7 +8,9 @@
 // per stage, one control kernel with a CTA per flow).  Flows retire when
 // their control block says done; queued requests are admitted as soon as a
 // slot and enough of the HBM budget are free, so new flows join while others
-// are mid-flight.  Each flow's reductions and step control depend only on its
+// are mid-flight.  Ticks are pipelined two deep: the next tick is queued
+// before the host reads the previous tick's control blocks, retires, admits
+// and rebuilds.  Each flow's reductions and step control depend only on its
 // own data, so its result does not depend on what it is batched with.
 //
 // Requests: frozen-background flows (d_t y = -Flow, Sec. 5.2.2 Eqs. assVar /
