@@ -306,6 +306,44 @@ def test_fermionic_flag_rejected_outside_finite_t(ctx):
 
 
 # ----------------------------------------------------------------------------- errors
+# ----------------------------------------------------------------------------- maximum sizes
+def test_d3_maximum_table_and_rule_sizes(ctx):
+    """4096-point tables (the largest table), 4096 radial and 1024 angle nodes
+    (the largest rules) in one RHS."""
+    wl = fi.make_d3(seed=21, n_pts=4096, n_ext_p=4, n_rad=4096, n_ang=1024)
+    _check(ctx, wl, 0.7)
+
+
+def test_d4_maximum_angle_rules(ctx):
+    """1024 x 1024 angle nodes per radial node (512 packed pairs in the FP32
+    three-point loop)."""
+    wl = fi.make_d4(seed=22, n_pts=16, n_ext_ang=1, n_rad=2, n_ang1=1024, n_ang2=1024)
+    wl.problem.n_ext_p = 1
+    _check(ctx, wl, 1.1)
+
+
+def test_finite_t_maximum_matsubara_count(ctx):
+    """N = 4096 (8193 loop frequencies, 4097 stack rows) with the smallest tables."""
+    wl = fi.make_finite_t(seed=23, N=4096, T=0.002, n_pts=2, n_ext_p=1, n_ext_m=1, n_rad=2, n_ang=2)
+    _check(ctx, wl, 0.5)
+
+
+def test_tables_beyond_shared_memory_rejected(ctx):
+    """Stacks that do not fit in shared memory (4097 rows x 8 points: 524 KB
+    FP64, 262 KB FP32) are refused before any launch."""
+    import torch
+
+    import paper_2412_13043_gb300 as ffrg
+    wl = fi.make_finite_t(seed=24, N=4096, T=0.002, n_pts=8, n_ext_p=1, n_ext_m=1, n_rad=2, n_ang=2)
+    tabs = ctx.tables(wl.problem, wl.tables)
+    out = torch.empty(wl.problem.n_ext(), dtype=torch.float64, device="cuda")
+    for prec in (ffrg.FP64, ffrg.MIXED):
+        with pytest.raises(ffrg.FfrgError):
+            ctx.rhs(wl.problem, tabs, 0.5, out=out, precision=prec)
+    assert ctx.status_read() == ffrg.OK
+    tabs.free()
+
+
 def test_nonfinite_table_sets_status(ctx):
     import paper_2412_13043_gb300 as ffrg
     wl = fi.make_d3(seed=1, n_pts=16, n_ext_p=8, n_rad=8, n_ang=4)
