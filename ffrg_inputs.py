@@ -12,7 +12,9 @@ uniform double takes the top 53 bits.
 
 Workload shapes follow the paper's vertex-expansion setups (Sec. 3.3: 96-point
 logarithmic momentum grid, 96x8x7 vertex grid, quadrature order 32x8^n in
-Table 1) scaled to the synthetic configurations described in the design doc.
+Table 1) scaled to synthetic configurations: d=3 (64 ext x 64 x 32 nodes),
+the d=4 vertex model (1281 ext x 128 x 64 x 16), finite T (64 |p| x 9 p0,
+96 x 48 x (2N+1)), the full three-point vertex and the serving request mix.
 """
 from __future__ import annotations
 

@@ -10,7 +10,9 @@
  * definitions (Sec. 2.1 Eq. GenfRG / FlowGamman, Sec. 5.2.2 Eq. assVar /
  * flowVar, Sec. 5.3.1 regulator API, Sec. 5.3.2 quadrature integrators,
  * App. F interpolator types, App. C time-stepping parameters) and from the
- * synthetic integrands fixed in the design doc where the paper is silent.
+ * synthetic integrands of this library's models where the paper is silent
+ * (propagator, regulator and vertex diagrams of the d=3, d=4 and finite-T
+ * models, each written out at its function below).
  *
  * Style: nested loops in the order the definitions are written (external point,
  * then Matsubara index, radial node, angular nodes), Neumaier-compensated sums

@@ -169,11 +169,17 @@ def test_d3_litim_closed_form(k, w):
     assert abs(out[-1] - (-2.0 * 0.49 * exact)) / exact < 1e-14
 
 
-def test_d3_survey_values():
-    # k=1.7, w=0.5 : 1/((1+w)^3) threshold value quoted with 18 digits
+def test_d3_litim_threshold_to_double_precision():
+    """Flat regulator, Z = 1, p = 0, q < k: G = 1/(k^2 (1 + w)), dR = 2 k^2, so
+    I(0) = (1/2 pi^2) (k^3/3) 2 k^2 G^3 = 1/(3 pi^2 k (1 + w)^3); at k = 1.7,
+    w = 0.5 in 30-digit arithmetic, the oracle agrees to a few ulp."""
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workdps(30):
+        k, w = mpmath.mpf("1.7"), mpmath.mpf("0.5")
+        exact = float(1 / (3 * mpmath.pi ** 2 * k * (1 + w) ** 3))
     pb = _d3_litim()
     out = oracle.rhs(pb, fi.constant_tables(pb, [1.0]), 1.7)
-    assert abs(out[-1] - 0.00588648851952579660) < 3e-18
+    assert abs(out[-1] - exact) < 3e-18
 
 
 def test_d3_litim_with_running_Z_log_linear():
