@@ -152,8 +152,12 @@ typedef struct {
 } ffrg_flow_stats;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
- * library's own device allocations (0 = no cap).  Owns *out until destroy. */
+ * library's own device allocations (0 = no cap).  Owns *out until destroy.
+ * Errors: FFRG_EINVAL (NULL out, bad device), FFRG_ECUDA. */
 FFRG_API int ffrg_create(ffrg_ctx **out, int device, size_t hbm_budget_bytes);
+/* Release a context: stops its server (requests finish FFRG_ECANCELED),
+ * waits for the device and frees every library-owned buffer, including
+ * tables not yet freed.  ctx is invalid afterwards.  FFRG_EINVAL for NULL. */
 FFRG_API int ffrg_destroy(ffrg_ctx *ctx);
 
 /* Quadrature rule on the host (Sec. 5.3.2 "quadrature rules of arbitrary
@@ -169,9 +173,13 @@ FFRG_API int ffrg_quad_nodes(int rule, int n, double a, double b, double *x, dou
  * Errors: FFRG_EINVAL (shape), FFRG_ENOMEM (budget). */
 FFRG_API int ffrg_tables_upload(ffrg_ctx *ctx, const ffrg_table_desc *desc, const double *values, int values_on_device,
                        ffrg_tables **out, void *stream);
-/* Overwrite the values of existing tables (same shape), stream-ordered. */
+/* Overwrite the values of existing tables (same shape, host or device
+ * source as for upload), stream-ordered on `stream`; a host source must stay
+ * valid until the copy has run (pinned memory: until the stream reaches it).
+ * Errors: FFRG_EINVAL (NULL arguments), FFRG_ECUDA. */
 FFRG_API int ffrg_tables_update(ffrg_ctx *ctx, ffrg_tables *tables, const double *values, int values_on_device,
                        void *stream);
+/* Free tables (after the work that reads them).  FFRG_EINVAL for NULL. */
 FFRG_API int ffrg_tables_free(ffrg_ctx *ctx, ffrg_tables *tables);
 /* Device pointer to the FP64 table values (library-owned, for zero-copy use). */
 FFRG_API int ffrg_tables_device_ptr(const ffrg_tables *tables, double **dev_values);
@@ -186,9 +194,13 @@ FFRG_API double ffrg_evals(const ffrg_problem *pb);
  * loop integrals; the D4 Z-block holds the propagator-diagram sum D2(p), see
  * the layout above).  out_dev: caller-owned device array of ffrg_n_ext()
  * doubles.  precision: FFRG_FP64 (all arithmetic FP64) or FFRG_MIXED (FP32
- * integrand, FP64 per-radial-node factors and cross-node accumulation, FP64
- * propagator near the pole).  Asynchronous; non-finite outputs set
- * FFRG_ENONFINITE in the status word. */
+ * integrand and row sums, compensated FP32 accumulation within a work item
+ * rounded once to FP64, FP64 across work items, FP64 per-radial-node
+ * factors, FP64 propagator near the pole).  Asynchronous; non-finite outputs
+ * set FFRG_ENONFINITE in the status word.  Errors: FFRG_EINVAL for a bad
+ * problem, tables of another shape, or tables and rules that do not fit in
+ * the 227 KB of shared memory of a block (8 bytes per table node in either
+ * precision, plus the angle rules); FFRG_ENOMEM (budget); FFRG_ECUDA. */
 FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_dev,
              int precision, void *stream);
 
@@ -328,6 +340,7 @@ FFRG_API int ffrg_serve_poll(ffrg_ctx *ctx, unsigned long long ticket, double *r
                              double *latency_s);
 /* Cancel a queued or resident request (it finishes with FFRG_ECANCELED). */
 FFRG_API int ffrg_serve_cancel(ffrg_ctx *ctx, unsigned long long ticket);
+/* Counters of the running server (host copy).  FFRG_EINVAL without a server. */
 FFRG_API int ffrg_serve_get_stats(ffrg_ctx *ctx, ffrg_serve_stats *out);
 /* Stop the scheduler: resident and queued requests finish with FFRG_ECANCELED. */
 FFRG_API int ffrg_serve_stop(ffrg_ctx *ctx);
