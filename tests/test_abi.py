@@ -100,3 +100,35 @@ def test_create_without_gpu_fails_cleanly():
         pytest.skip("a GPU is present")
     with pytest.raises(ffrg.FfrgError):
         ffrg.Context(0)
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """Every field of the binding's ctypes structures has the offset and size
+    that the C compiler gives the header's struct (a mismatch would corrupt
+    the arguments of every call silently)."""
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    pairs = [("ffrg_problem", ffrg.Problem), ("ffrg_table_desc", ffrg.TableDesc), ("ffrg_step_opts", ffrg.StepOpts),
+             ("ffrg_flow_stats", ffrg.FlowStats), ("ffrg_serve_opts", ffrg.ServeOpts),
+             ("ffrg_serve_stats", ffrg.ServeStats)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "ffrg.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append(f'  printf("{cname} - %zu %zu\\n", (size_t)0, sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                         f'sizeof((({cname} *)0)->{fname}));')
+    lines += ["  return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines) + "\n")
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    c = {(out[i], out[i + 1]): (int(out[i + 2]), int(out[i + 3])) for i in range(0, len(out), 4)}
+    for cname, cls in pairs:
+        assert c[(cname, "-")][1] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            f = getattr(cls, fname)
+            assert c[(cname, fname)] == (f.offset, f.size), (cname, fname)
