@@ -5,10 +5,12 @@ leg may import this package.  The product library never loads it.  The C
 source ``ffrg_oracle.c`` shares no code with the CUDA path; this wrapper only
 marshals arguments (ctypes) and compiles the C file with gcc on first use.
 
-Functions with no external pin: none at the RHS level (every model reduces to
-a closed form in a special case, see tests/test_oracle_pins.py); the finite-T
-and d=4 synthetic profiles away from those special cases are pinned only by
-convergence, rotational-invariance and Monte-Carlo checks.
+Pins: every model reduces to a closed form in a special case, and with
+non-constant tables away from p = 0 the d=3, finite-T and d=4 two-point
+integrands match an independent quadrature route (tests/test_oracle_pins.py).
+Parity unpinned: the d=4 three-point block with non-constant tables and the
+full-vertex model with (a, b)-dependent tables away from its special cases
+(only convergence, rotational-invariance and reduction checks).
 """
 from __future__ import annotations
 

@@ -773,3 +773,153 @@ def test_d4_full_shape_variables_from_vectors():
         assert abs(a - k1 @ k2 / math.sqrt((k1 @ k1) * (k2 @ k2))) < 1e-12
         assert abs(b - (k1 @ k1 - k2 @ k2) / (k1 @ k1 + k2 @ k2)) < 1e-13
     assert oracle.d4_shape(1.0, 1.0, 9.0)[0] == 1.0 and oracle.d4_shape(1.0, 1.0, -5.0)[0] == -1.0
+
+
+# --------------------------------------------------------------------------
+# Non-constant tables away from p = 0, against an independent route to the
+# same continuum integral.  With s^2 = |q + p|^2 = q^2 + p^2 + 2 q p c the
+# angular integral of a function of |q + p| becomes a 1-D integral in s:
+#   int_{-1}^{1} f(|q+p|) dc = (1/qp) int_{|q-p|}^{q+p} s f(s) ds
+# (d=4, Gauss-Chebyshev-II weight: the same with sqrt(1 - c(s)^2) inside).
+# Nested adaptive quadrature of that form (scipy) against the oracle's
+# Gauss product rule.  Tables linear in ln s, which the log-grid lookup
+# reproduces exactly; smooth exponential regulator.
+# --------------------------------------------------------------------------
+def _exp_r(x):
+    return 1.0 if x < 1e-12 else x / math.expm1(x)
+
+
+def _exp_rdot(x):
+    if x < 1e-12:
+        return 2.0
+    em = math.expm1(-x)
+    return 2.0 * x * x * math.exp(-x) / (em * em)
+
+
+def _loglin(pb, a, b):
+    """lookup of a + b ln(s / x_min), clamped like the table lookup"""
+    def f(s):
+        return a + b * math.log(min(max(s, pb.x_min), pb.x_max) / pb.x_min)
+    return f
+
+
+def _ang(q, p, f, gc2=False):
+    from scipy import integrate
+
+    def g(s):
+        if not gc2:
+            return s * f(s)
+        c = (s * s - q * q - p * p) / (2 * q * p)
+        return s * math.sqrt(max(0.0, 1.0 - c * c)) * f(s)
+    v, _ = integrate.quad(g, abs(q - p), q + p, epsabs=0, epsrel=1e-13, limit=200)
+    return v / (q * p)
+
+
+def _radial(f, qmax):
+    from scipy import integrate
+    v, _ = integrate.quad(f, 0.0, qmax, epsabs=0, epsrel=1e-12, limit=200)
+    return v
+
+
+def test_d3_nonconstant_table_at_finite_p_vs_angle_substitution():
+    pytest.importorskip("scipy")
+    k, w, a, b = 1.0, 0.5, 1.0, 0.04
+    wl = fi.make_d3(seed=5, n_pts=48, n_ext_p=16, n_rad=128, n_ang=128)
+    pb = wl.problem
+    pb.m2_over_k2, pb.m2_shift = w, 0.0
+    xs = fi.log_grid(pb.n_pts, pb.x_min, pb.x_max)
+    ref = oracle.rhs(pb, (a + b * np.log(xs / pb.x_min)).reshape(1, 1, -1), k)
+    Z, m2 = _loglin(pb, a, b), w * k * k
+
+    def G(s):
+        return 1.0 / (Z(s) * (s * s + k * k * _exp_r(s * s / (k * k))) + m2)
+    ps = [pb.p_min * (pb.p_max / pb.p_min) ** (e / (pb.n_ext_p - 1)) for e in range(pb.n_ext_p)]
+    for e in (4, 8, 11, 13):
+        p = ps[e]
+        val = _radial(lambda q: q * q * Z(q) * k * k * _exp_rdot(q * q / (k * k)) * G(q) ** 2 * _ang(q, p, G),
+                      pb.qmax_over_k * k) / (4 * math.pi ** 2)
+        # the lookup clamp at s -> 0 (q = p, c = -1) limits the product rule
+        # to algebraic convergence: 3e-8 at 128 x 128 nodes
+        assert abs(val - ref[e]) / abs(ref[e]) < 2e-7, (e, val, ref[e])
+
+
+@pytest.mark.parametrize("fermionic", [False, True])
+def test_finite_t_row_dependent_tables_at_finite_p_and_m_vs_angle_substitution(fermionic):
+    """Z and lambda linear in ln s with coefficients that depend on the stack
+    row: pins the frequency of every line, the row of n and n + m, and both
+    vertex factors of the finite-T loop."""
+    pytest.importorskip("scipy")
+    k, w, T, N, M = 1.0, 0.5, 0.3, 2, 2
+    wl = fi.make_finite_t(seed=8 if fermionic else 7, N=N, T=T, n_pts=40, n_ext_p=6, n_ext_m=M, n_rad=128,
+                          n_ang=128, fermionic=fermionic)
+    pb = wl.problem
+    pb.m2_over_k2, pb.m2_shift = w, 0.0
+    ns = pb.n_stack
+    za = [1.0 + 0.05 * j for j in range(ns)]
+    zb = [0.03 - 0.004 * j for j in range(ns)]
+    la = [0.9 - 0.03 * j for j in range(ns)]
+    lb = [0.02 + 0.003 * j for j in range(ns)]
+    lg = np.log(fi.log_grid(pb.n_pts, pb.x_min, pb.x_max) / pb.x_min)
+    tab = np.stack([np.stack([za[j] + zb[j] * lg for j in range(ns)]),
+                    np.stack([la[j] + lb[j] * lg for j in range(ns)])])
+    ref = oracle.rhs(pb, tab, k)
+    m2 = w * k * k
+
+    def row(n):          # bosonic omega_n: |n|; fermionic nu_n = (2n+1) pi T: n or -n-1
+        return min(abs(n) if not fermionic else (n if n >= 0 else -n - 1), ns - 1)
+
+    def freq2(n):
+        return ((2 * n + 1) * math.pi * T) ** 2 if fermionic else (2 * math.pi * T * n) ** 2
+
+    def Z(n, s):
+        return _loglin(pb, za[row(n)], zb[row(n)])(s)
+
+    def lam(n, s):
+        return _loglin(pb, la[row(n)], lb[row(n)])(s)
+
+    def G(n, s):
+        return 1.0 / (Z(n, s) * (freq2(n) + s * s + k * k * _exp_r(s * s / (k * k))) + m2)
+    ps = [pb.p_min * (pb.p_max / pb.p_min) ** (e / (pb.n_ext_p - 1)) for e in range(pb.n_ext_p)]
+    loop = range(-N - 1, N + 1) if fermionic else range(-N, N + 1)
+    for ip in (2, 4):
+        for m in range(M):
+            p = ps[ip]
+            tot = sum(_radial(lambda q: q * q * Z(n, q) * k * k * _exp_rdot(q * q / (k * k)) * G(n, q) ** 2
+                              * lam(n, q) * _ang(q, p, lambda s: lam(n + m, s) * G(n + m, s)), pb.qmax_over_k * k)
+                      for n in loop) * T / (4 * math.pi ** 2)
+            e = ip * M + m
+            assert abs(tot - ref[e]) / abs(ref[e]) < 5e-9, (ip, m, tot, ref[e])
+
+
+def test_d4_two_point_blocks_at_finite_p_vs_angle_substitution():
+    """The propagator block D2(p) = int dR G^2 [-lam4/2 + lam3^2 G(|q+p|)] and
+    the four-point block 3/2 int dR G^2 G(|q+p|) lam4^2 with all three tables
+    linear in ln s; the second angle integrates to 2."""
+    pytest.importorskip("scipy")
+    k = 1.0
+    wl = fi.make_d4(seed=9, n_pts=40, n_ext_ang=2, n_rad=128, n_ang1=128, n_ang2=2)
+    pb = wl.problem
+    co = [(1.0, 0.03), (1.1, -0.02), (0.8, 0.025)]
+    lg = np.log(fi.log_grid(pb.n_pts, pb.x_min, pb.x_max) / pb.x_min)
+    ref = oracle.rhs(pb, np.stack([(a + b * lg).reshape(1, -1) for a, b in co]), k)
+    Z, l3, l4 = (_loglin(pb, a, b) for a, b in co)
+    m2 = pb.m2_over_k2 * k * k + pb.m2_shift
+
+    def G(s):
+        return 1.0 / (Z(s) * (s * s + k * k * _exp_r(s * s / (k * k))) + m2)
+
+    def base(q):
+        return q ** 3 * Z(q) * k * k * _exp_rdot(q * q / (k * k)) * G(q) ** 2 * 2.0
+    np_, npsi = pb.n_ext_p, pb.n_ext_ang
+    ps = [pb.p_min * (pb.p_max / pb.p_min) ** (e / (np_ - 1)) for e in range(np_)]
+    norm = 8 * math.pi ** 3
+    for ip in (np_ // 2, (3 * np_) // 4, np_ - 3):
+        p = ps[ip]
+        zb = _radial(lambda q: base(q) * (-0.5 * l4(math.sqrt((q * q + p * p) / 2)) * math.pi / 2
+                                          + _ang(q, p, lambda s: l3(math.sqrt((q * q + s * s + p * p) / 3)) ** 2
+                                                 * G(s), gc2=True)), pb.qmax_over_k * k) / norm
+        f4 = _radial(lambda q: 1.5 * base(q) * _ang(q, p, lambda s: G(s) * l4(math.sqrt((q * q + s * s + 2 * p * p)
+                                                                                      / 4)) ** 2, gc2=True),
+                     pb.qmax_over_k * k) / norm
+        for val, e in ((zb, ip), (f4, np_ + 1 + np_ * npsi + ip)):
+            assert abs(val - ref[e]) / abs(ref[e]) < 2e-9, (ip, e, val, ref[e])
