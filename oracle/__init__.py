@@ -6,11 +6,10 @@ source ``ffrg_oracle.c`` shares no code with the CUDA path; this wrapper only
 marshals arguments (ctypes) and compiles the C file with gcc on first use.
 
 Pins: every model reduces to a closed form in a special case, and with
-non-constant tables away from p = 0 the d=3, finite-T and d=4 two-point
-integrands match an independent quadrature route (tests/test_oracle_pins.py).
-Parity unpinned: the d=4 three-point block with non-constant tables and the
-full-vertex model with (a, b)-dependent tables away from its special cases
-(only convergence, rotational-invariance and reduction checks).
+non-constant tables away from p = 0 every RHS summand matches an independent
+route to the same integral (angle substitution and adaptive quadrature, or
+summands written from the model definitions over explicit 4-vectors; see
+tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

@@ -22,13 +22,13 @@
  * sum keeps its fixed order, so results do not depend on the thread count).
  *
  * Parity pins: see tests/test_oracle_pins.py.  Every function here is pinned
- * by at least one closed form, library routine, invariant or brute-force case;
- * with non-constant tables away from p = 0 the d=3, finite-T and d=4
- * two-point summands are pinned against an independent quadrature route.
- * Parity unpinned: orc_d4_summand_3 (the three-point block) with
- * non-constant tables, and the full-vertex model with (a, b)-dependent
- * tables away from its reduction and exactness cases -- pinned there only
- * through rotational invariance, convergence and those special cases.
+ * by at least one closed form, library routine, invariant or brute-force case.
+ * With non-constant tables away from p = 0 every RHS summand is also pinned
+ * against an independent route to the same integral: the d=3, finite-T and
+ * d=4 two-point integrands through the substitution s = |q + p| and adaptive
+ * quadrature; the d=4 three-point block and the full-vertex blocks through
+ * summands written from the model definitions over explicit 4-vectors (the
+ * full vertex with its shape variables from the leg vectors).
  */
 #include <math.h>
 #include <stdlib.h>

@@ -923,3 +923,154 @@ def test_d4_two_point_blocks_at_finite_p_vs_angle_substitution():
                      pb.qmax_over_k * k) / norm
         for val, e in ((zb, ip), (f4, np_ + 1 + np_ * npsi + ip)):
             assert abs(val - ref[e]) / abs(ref[e]) < 2e-9, (ip, e, val, ref[e])
+
+
+def test_d4_three_point_block_summand_written_from_the_model():
+    """The three-point block 3 int dR G(q)^2 G(|q+p1|) G(|q-p2|) lam3 lam3 lam3,
+    with the three vertices at S0 of their legs (q, q+p1, p1), (q, q-p2, p2),
+    (q+p1, q-p2, p1+p2), written here from the model definition and summed
+    over explicit 4-vectors (three-angle product rule, p1 and p2 under a random
+    O(4) rotation) -- independent of the oracle's summand, its two-angle
+    reduction and its angle variables.  Tables linear in ln s."""
+    wl = fi.make_d4(seed=9, n_pts=32, n_ext_ang=3, n_rad=24, n_ang1=40, n_ang2=40)
+    pb = wl.problem
+    k = 1.0
+    co = [(1.0, 0.015), (1.2, -0.03), (0.8, 0.02)]
+    lg = np.log(fi.log_grid(pb.n_pts, pb.x_min, pb.x_max) / pb.x_min)
+    ref = oracle.rhs(pb, np.stack([(a + b * lg).reshape(1, -1) for a, b in co]), k)
+
+    def look(i, s):
+        a, b = co[i]
+        return a + b * np.log(np.clip(s, pb.x_min, pb.x_max) / pb.x_min)
+
+    def r(x):
+        out = np.ones_like(x)
+        m = x > 1e-12
+        out[m] = x[m] / np.expm1(x[m])
+        return out
+
+    def rdot(x):
+        out = np.full_like(x, 2.0)
+        m = x > 1e-12
+        em = np.expm1(-x[m])
+        out[m] = 2 * x[m] ** 2 * np.exp(-x[m]) / em ** 2
+        return out
+    m2 = pb.m2_over_k2 * k * k + pb.m2_shift
+
+    def G(s2):
+        return 1.0 / (look(0, np.sqrt(np.maximum(s2, 0.0))) * (s2 + k * k * r(s2 / (k * k))) + m2)
+    xr, wr = oracle.gauss_legendre(pb.n_rad, 0.0, pb.qmax_over_k * k)
+    x1, w1 = oracle.gauss_chebyshev2(40)
+    x2, w2 = np.polynomial.legendre.leggauss(40)
+    nphi = 40
+    ph = 2 * np.pi * np.arange(nphi) / nphi
+    cpsi, _ = np.polynomial.legendre.leggauss(pb.n_ext_ang)
+    Q, C1, C2, PH = np.meshgrid(xr, x1, x2, ph, indexing="ij")
+    S1, S2 = np.sqrt(1 - C1 ** 2), np.sqrt(1 - C2 ** 2)
+    qv = np.stack([Q * C1, Q * S1 * C2, Q * S1 * S2 * np.cos(PH), Q * S1 * S2 * np.sin(PH)], -1)
+    W = (wr[:, None, None, None] * w1[None, :, None, None] * w2[None, None, :, None]
+         * (2 * np.pi / nphi) * Q ** 3) / (2 * np.pi) ** 4
+    q2 = Q ** 2
+    base = 3 * look(0, Q) * k * k * rdot(q2 / (k * k)) * G(q2) ** 2
+    rng = np.random.default_rng(7)
+    np_ = pb.n_ext_p
+    for ip, j in [(18, 0), (25, 2), (29, 1)]:
+        p = pb.p_min * (pb.p_max / pb.p_min) ** (ip / (np_ - 1))
+        Rm = _rot4(rng)
+        p1 = Rm @ np.array([p, 0, 0, 0])
+        p2 = Rm @ np.array([p * cpsi[j], p * math.sqrt(1 - cpsi[j] ** 2), 0, 0])
+        A2 = np.sum((qv + p1) ** 2, -1)
+        B2 = np.sum((qv - p2) ** 2, -1)
+        Cc = float(np.sum((p1 + p2) ** 2))
+        f = (base * G(A2) * G(B2) * look(1, np.sqrt((q2 + A2 + p * p) / 3))
+             * look(1, np.sqrt((q2 + B2 + p * p) / 3)) * look(1, np.sqrt((A2 + B2 + Cc) / 3)))
+        val = float(np.sum(W * f))
+        e = np_ + 1 + ip * pb.n_ext_ang + j
+        assert abs(val - ref[e]) / abs(ref[e]) < 2e-8, (ip, j, val, ref[e])
+
+
+def test_d4_full_vertex_blocks_with_shape_variables_from_leg_vectors():
+    """Full vertex: lambda3 multilinear in (ln S0, a, b) (reproduced exactly by
+    the trilinear lookup), its a = cos(k1, k2) and b = (|k1|^2 - |k2|^2) /
+    (|k1|^2 + |k2|^2) taken here from dot products of the explicit leg
+    4-vectors; the propagator block and the three-point block summed over the
+    three-angle product rule with p1, p2 under a random O(4) rotation (and the
+    four-point block, whose table sits at another row offset here).  The
+    difference is the two rules' discretisation (2.9e-7 here, 1.9e-8 with 64^2
+    and 64^2 x 48 nodes); a wrong leg or leg order changes a or b at O(1)."""
+    na, nb = 4, 3
+    wl = fi.make_d4_full(seed=11, n_pts=32, n_va=na, n_vb=nb, n_ext_ang=3, n_rad=24, n_ang1=40, n_ang2=40)
+    pb = wl.problem
+    k = 1.0
+    lg = np.log(fi.log_grid(pb.n_pts, pb.x_min, pb.x_max) / pb.x_min)
+    zc, l4c = (1.0, 0.015), (0.8, 0.02)
+    g = (1.1, -0.02, 0.15, -0.1, 0.05)      # lam3 = g0 + g1 ln(S0/x_min) + g2 a + g3 b + g4 a b
+    av, bv = np.linspace(-1, 1, na), np.linspace(-1, 1, nb)
+    tab = np.zeros((3, na * nb, pb.n_pts))
+    tab[0, 0] = zc[0] + zc[1] * lg
+    tab[2, 0] = l4c[0] + l4c[1] * lg
+    for ia in range(na):
+        for ib in range(nb):
+            tab[1, ia * nb + ib] = g[0] + g[1] * lg + g[2] * av[ia] + g[3] * bv[ib] + g[4] * av[ia] * bv[ib]
+
+    def ell(s):
+        return np.log(np.clip(s, pb.x_min, pb.x_max) / pb.x_min)
+
+    def lam3(k1, k2):     # vertex with legs k1, k2, -(k1 + k2)
+        s1, s2 = np.sum(k1 * k1, -1), np.sum(k2 * k2, -1)
+        s3 = np.sum((k1 + k2) ** 2, -1)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            a = np.sum(k1 * k2, -1) / np.sqrt(s1 * s2)
+            b = (s1 - s2) / (s1 + s2)
+        a = np.nan_to_num(np.clip(a, -1, 1), nan=-1.0)
+        b = np.nan_to_num(np.clip(b, -1, 1), nan=-1.0)
+        return g[0] + g[1] * ell(np.sqrt((s1 + s2 + s3) / 3)) + g[2] * a + g[3] * b + g[4] * a * b
+
+    def r(x):
+        out = np.ones_like(x)
+        m = x > 1e-12
+        out[m] = x[m] / np.expm1(x[m])
+        return out
+
+    def rdot(x):
+        out = np.full_like(x, 2.0)
+        m = x > 1e-12
+        em = np.expm1(-x[m])
+        out[m] = 2 * x[m] ** 2 * np.exp(-x[m]) / em ** 2
+        return out
+    m2 = pb.m2_over_k2 * k * k + pb.m2_shift
+
+    def G(s2):
+        return 1.0 / ((zc[0] + zc[1] * ell(np.sqrt(np.maximum(s2, 0.0)))) * (s2 + k * k * r(s2 / (k * k))) + m2)
+    xr, wr = oracle.gauss_legendre(pb.n_rad, 0.0, pb.qmax_over_k * k)
+    x1, w1 = oracle.gauss_chebyshev2(40)
+    x2, w2 = np.polynomial.legendre.leggauss(40)
+    nphi = 40
+    ph = 2 * np.pi * np.arange(nphi) / nphi
+    cpsi, _ = np.polynomial.legendre.leggauss(pb.n_ext_ang)
+    Q, C1, C2, PH = np.meshgrid(xr, x1, x2, ph, indexing="ij")
+    S1, S2 = np.sqrt(1 - C1 ** 2), np.sqrt(1 - C2 ** 2)
+    qv = np.stack([Q * C1, Q * S1 * C2, Q * S1 * S2 * np.cos(PH), Q * S1 * S2 * np.sin(PH)], -1)
+    W = (wr[:, None, None, None] * w1[None, :, None, None] * w2[None, None, :, None]
+         * (2 * np.pi / nphi) * Q ** 3) / (2 * np.pi) ** 4
+    q2 = Q ** 2
+    base = (zc[0] + zc[1] * ell(Q)) * k * k * rdot(q2 / (k * k)) * G(q2) ** 2
+    rng = np.random.default_rng(5)
+    np_ = pb.n_ext_p
+    sel, vals = [], []
+    for ip, j in [(12, 0), (20, 2), (26, 1)]:
+        p = pb.p_min * (pb.p_max / pb.p_min) ** (ip / (np_ - 1))
+        Rm = _rot4(rng)
+        p1 = Rm @ np.array([p, 0, 0, 0])
+        p2 = Rm @ np.array([p * cpsi[j], p * math.sqrt(1 - cpsi[j] ** 2), 0, 0])
+        A2 = np.sum((qv + p1) ** 2, -1)
+        B2 = np.sum((qv - p2) ** 2, -1)
+        l4 = l4c[0] + l4c[1] * ell(np.sqrt((2 * q2 + 2 * p * p) / 4))
+        zblock = base * (-0.5 * l4 + lam3(qv, -(qv + p1)) ** 2 * G(A2))
+        three = 3 * base * G(A2) * G(B2) * lam3(qv, -(qv + p1)) * lam3(qv, -(qv - p2)) * lam3(qv + p1, -(qv - p2))
+        four = 1.5 * base * G(A2) * (l4c[0] + l4c[1] * ell(np.sqrt((q2 + A2 + 2 * p * p) / 4))) ** 2
+        sel += [ip, np_ + 1 + ip * pb.n_ext_ang + j, np_ + 1 + np_ * pb.n_ext_ang + ip]
+        vals += [float(np.sum(W * zblock)), float(np.sum(W * three)), float(np.sum(W * four))]
+    ref = oracle.rhs_subset(pb, tab, k, sel)
+    for e, v, rf in zip(sel, vals, ref):
+        assert abs(v - rf) / abs(rf) < 1e-6, (e, v, rf)
