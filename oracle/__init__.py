@@ -105,6 +105,7 @@ def _load():
         lib.orc_dp45_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
         lib.orc_ros2_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
         lib.orc_ros2_flow.argtypes = [pp, D, dp, P(_StepOpts), P(_Stats)]
+        lib.orc_d4_state_jacobian.argtypes = [pp, D, D, dp, dp]
         lib.orc_abm_textbook.argtypes = [I, I, D, D, ctypes.c_long, dp, P(ctypes.c_long)]
         lib.orc_lam3_full.argtypes = [pp, dp, D, D, D]
         lib.orc_lam3_full.restype = D
@@ -309,6 +310,15 @@ def abm_flow(pb, tables, y0, Lambda: float, t1: float, n: int, order: int = 4, f
     _check(_load().orc_abm_flow(ctypes.byref(_problem(pb)), _ptr(_f64(tables)), int(feedback), Lambda, _ptr(y),
                                 t0, t1, int(n), int(order), ctypes.byref(st)), "abm_flow")
     return y, dict(steps=st.steps, rhs_evals=st.rhs_evals)
+
+
+def d4_state_jacobian(pb, Lambda: float, t: float, y) -> np.ndarray:
+    """d(d_t y)/dy of the d=4 feedback state (the tables) at RG time t."""
+    yy = _f64(y).copy()
+    J = np.empty((yy.size, yy.size))
+    _check(_load().orc_d4_state_jacobian(ctypes.byref(_problem(pb)), Lambda, t, _ptr(yy), _ptr(J)),
+           "d4_state_jacobian")
+    return J
 
 
 def ros2_flow(pb, y0, Lambda: float, t1: float, dt0: float = 1e-2, dt_min: float = 1e-10, dt_max: float = 0.5,

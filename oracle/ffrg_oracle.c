@@ -28,7 +28,12 @@
  * d=4 two-point integrands through the substitution s = |q + p| and adaptive
  * quadrature; the d=4 three-point block and the full-vertex blocks through
  * summands written from the model definitions over explicit 4-vectors (the
- * full vertex with its shape variables from the leg vectors).
+ * full vertex with its shape variables from the leg vectors).  The feedback
+ * maps of flow_deriv (d=3: m^2 and Z_i; d=4: Z_i, the psi average of lambda3,
+ * lambda4) are pinned by flat-regulator closed forms, by the p -> 0 limit of
+ * their difference quotients (d/d(p^2) of the angle average) and by the same
+ * independent routes at finite p; the d=4 state Jacobian by central
+ * differences of that pinned map (tests/test_oracle_feedback_pins.py).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -1177,6 +1182,20 @@ static int d4_state_jac(void *ctxp, double t, const double *y, double *J, int ny
     }
   }
   free(dt); free(o); free(d);
+  return st;
+}
+
+/* The d=4 feedback state Jacobian at (t, y), row-major ny x ny, exposed so
+ * tests can compare its columns with differences of the flow derivative. */
+int orc_d4_state_jacobian(const orc_problem *pb, double Lambda, double t, const double *y, double *J) {
+  int st = check_problem(pb);
+  if (st) return st;
+  if (pb->model != ORC_D4_VERTEX || !y || !J || !(Lambda > 0.0)) return ORC_EINVAL;
+  int ny = orc_flow_state_size(pb, 1);
+  flow_ctx fc;
+  st = flow_ctx_init(&fc, pb, NULL, 1, Lambda);
+  if (!st) st = d4_state_jac(&fc, t, y, J, ny);
+  flow_ctx_free(&fc);
   return st;
 }
 
