@@ -218,14 +218,19 @@ FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *
  *   doubles; out_dev: caller-owned device array of ffrg_n_ext(pb) doubles;
  *   k, precision, stream: as for ffrg_rhs.  Runs on the current CUDA device.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and sets the kernels' shared-memory limit.  Make that
- * first call before any stream capture.  Each call copies its quadrature
- * rules from host memory into the array, ordered on `stream`.  All calls share the one array, which keeps the last call's contents.  Calls
- * whose work overlaps on the GPU (other streams, other host threads) race on
- * it: serialise them.  Errors: FFRG_EINVAL for bad arguments and for problems
- * whose scratch exceeds 4 MiB (quadrature rules + (2N+1) n_rad factors +
- * n_ext x chunk partials + the FP32 table copy, about 460 000 doubles);
- * FFRG_ECUDA on a CUDA error.  Non-finite results are visible only in out_dev. */
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  A
+ * call whose kernels need more dynamic shared memory than any earlier call's
+ * on that device also raises the kernels' limit (cudaFuncSetAttribute).  Each
+ * call copies its quadrature rules from host memory into the array, ordered
+ * on `stream`.  All calls share the one array, which keeps the last call's
+ * contents.  Calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it: serialise them.  Errors: FFRG_EINVAL for bad arguments
+ * and for problems whose scratch exceeds 4 MiB (quadrature rules + (2N+1)
+ * n_rad factors + n_ext x chunk partials + the FP32 table copy, about 460 000
+ * doubles); FFRG_ECUDA on a CUDA error.  There is no status word to read:
+ * device-side errors show in out_dev.  Non-finite results stay non-finite,
+ * and if a bounded device wait gave up (what ffrg_rhs reports as
+ * FFRG_ETIMEOUT) every entry of out_dev is NaN. */
 FFRG_API int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *desc, const double *tables_dev, double k,
                               double *out_dev, int precision, void *stream);
 

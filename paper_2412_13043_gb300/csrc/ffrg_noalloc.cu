@@ -42,6 +42,15 @@ static cudaError_t noalloc_scratch_for_current_device(int dev, unsigned char **o
   return cudaSuccess;
 }
 
+// The call has no context whose status word a caller could read, so a
+// bounded device wait that gave up (kStatusTimeout) is reported through the
+// outputs: every entry becomes NaN, instead of keeping values that a CTA
+// never wrote (the previous call's, or from stale scratch).
+__global__ void noalloc_poison_on_timeout(const unsigned *status, double *out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && (*(volatile const unsigned *)status & kStatusTimeout)) out[i] = __longlong_as_double(-1ll);
+}
+
 // Bump allocator over the fixed array (256-byte aligned segments).
 struct ScratchCarver {
   unsigned char *base;
@@ -148,5 +157,8 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   fill_args(&pl, pb, td, tables_dev, k, a);
   a.out = out_dev;
   a.status = status;
-  return launch_rhs(&lc, &pl, a, precision, s);
+  int st = launch_rhs(&lc, &pl, a, precision, s);
+  if (st != FFRG_OK) return st;
+  noalloc_poison_on_timeout<<<(pl.n_ext + 255) / 256, 256, 0, s>>>(status, out_dev, pl.n_ext);
+  return cudaGetLastError() == cudaSuccess ? FFRG_OK : FFRG_ECUDA;
 }

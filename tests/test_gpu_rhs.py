@@ -4,8 +4,13 @@ FP64 path: 1e-12 relative per output (Sec. 5.3.2 quadrature, computed by the
 same discrete sums; the two sides differ only in summation order and libm vs
 CUDA rounding).  Mixed path (FP32 integrand, FP64 per-radial factors and
 cross-node accumulation): the stated bound MIXED_TOL per output.
-Small cases span several work items with ragged tails; full-size cases are
-checked on sampled external points that the oracle computes one by one.
+Small cases span several work items with ragged tails; the full-size
+workloads (d=4 1281 x 128 x 64 x 16, the 96 x 8 x 7 full vertex, finite T at
+N = 16/32/64 with both loop statistics) are compared on every output.  The
+d=4 Z block D2 = int dR G^2 [-lam4/2 + lam3^2 G] is a difference of two
+single-signed parts that can cancel; there the error is taken relative to
+the sum of the parts' magnitudes (both computed by the oracle), and the
+condition number |parts| / |D2| is printed beside it.
 """
 import math
 
@@ -40,22 +45,48 @@ def _run(ctx, wl, k, precision, out=None):
     return res
 
 
+def _oracle_scale(wl, k, ref, sel=None):
+    """Per output, the magnitude the error is measured against: |ref|, except
+    in the Z block of the d=4 models, where it is |D2 at lam4 = 0| + |D2 at
+    lam3 = 0| (the two single-signed parts of D2), from the oracle."""
+    pb = wl.problem
+    scale = np.abs(ref).copy()
+    if pb.model not in (fi.MODEL_D4_VERTEX, fi.MODEL_D4_FULL):
+        return scale
+    nz = pb.n_ext_p + 1
+    idx = np.arange(pb.n_ext()) if sel is None else np.asarray(sel)
+    zpos = np.nonzero(idx < nz)[0]
+    if zpos.size == 0:
+        return scale
+    parts = np.zeros(zpos.size)
+    for zero in (2, 1):
+        t = wl.tables.copy()
+        t[zero] = 0.0
+        parts += np.abs(oracle.rhs_subset(pb, t, k, idx[zpos]))
+    scale[zpos] = parts
+    return scale
+
+
 def _check(ctx, wl, k, sel=None, mixed=True):
     import paper_2412_13043_gb300 as ffrg
     if sel is None:
         ref = oracle.rhs(wl.problem, wl.tables, k)
     else:
         ref = oracle.rhs_subset(wl.problem, wl.tables, k, sel)
+    scale = _oracle_scale(wl, k, ref, sel)
+    cond = float(np.max(scale / np.maximum(np.abs(ref), 1e-300)))
     g64 = _run(ctx, wl, k, ffrg.FP64)
     g64 = g64 if sel is None else g64[sel]
-    e64 = rel_err(g64, ref)
+    e64 = np.abs(g64 - ref) / scale
     assert np.max(e64) < FP64_TOL, (np.max(e64), int(np.argmax(e64)))
+    msg = f"model {wl.problem.model} k={k} n={ref.size}: fp64 max {np.max(e64):.2e}"
     if mixed:
         g32 = _run(ctx, wl, k, ffrg.MIXED)
         g32 = g32 if sel is None else g32[sel]
-        e32 = rel_err(g32, ref)
-        print(f"model {wl.problem.model} k={k}: fp64 max rel {np.max(e64):.2e}, mixed max rel {np.max(e32):.2e}")
+        e32 = np.abs(g32 - ref) / scale
+        msg += f", mixed max {np.max(e32):.2e}"
         assert np.max(e32) < MIXED_TOL, (np.max(e32), int(np.argmax(e32)))
+    print(msg + f", max condition {cond:.1f}")
     return e64
 
 
@@ -112,14 +143,12 @@ def test_d4_small_ragged(ctx):
         _check(ctx, wl, k)
 
 
-def test_d4_full_size_sampled(ctx):
-    wl = fi.make_d4(seed=2)       # (128+1+1024+128) ext x (128 x 64 x 16)
-    np_, npsi = wl.problem.n_ext_p, wl.problem.n_ext_ang
-    sel = [0, 37, np_ - 1, np_,                                     # Z block incl. p = 0
-           np_ + 1, np_ + 1 + 50 * npsi + 3, np_ + 1 + np_ * npsi - 1,  # lambda3 block
-           np_ + 1 + np_ * npsi, np_ + 1 + np_ * npsi + 90, 2 * np_ + np_ * npsi]  # lambda4 block
+def test_d4_full_size_every_output(ctx):
+    """The d=4 vertex workload at full size, (128 + 1 + 1024 + 128) external
+    points x (128 x 64 x 16) nodes, every output against the oracle."""
+    wl = fi.make_d4(seed=2)
     for k in (10.0, 0.5):
-        _check(ctx, wl, k, sel=sel)
+        _check(ctx, wl, k)
 
 
 @pytest.mark.parametrize("full", [False, True])
@@ -137,7 +166,7 @@ def test_d4_near_pole_mixed_uses_fp64_propagator(ctx, full):
     wl.problem.m2_shift = 0.0
     for k in (1.0, 0.05):
         ref = oracle.rhs(wl.problem, wl.tables, k)
-        scale = _termwise_scale(ctx, wl, k, ref)   # the Z block can cross zero
+        scale = _oracle_scale(wl, k, ref)   # the Z block can cross zero
         g64 = _run(ctx, wl, k, ffrg.FP64)
         g32 = _run(ctx, wl, k, ffrg.MIXED)
         assert np.max(np.abs(g64 - ref) / scale) < FP64_TOL
@@ -172,44 +201,12 @@ def test_d4_full_small_ragged(ctx):
             _check(ctx, wl, k)
 
 
-def test_d4_full_full_size_sampled(ctx):
-    wl = fi.make_d4_full()           # 96-pt log grid x 8 x 7 vertex grid, 1281 ext x (128 x 64 x 16)
-    ne = wl.problem.n_ext()
-    sel = [0, 96, 97, 97 + 8 * 40 + 3, ne - 97, ne - 1]
-    _check(ctx, wl, 1.0, sel=sel)
-
-
-def _termwise_scale(ctx, wl, k, ref):
-    """Per output, the sum of the magnitudes of the parts that can cancel: in
-    the Z block of the d=4 models D2 = int dR G^2 [-lam4/2 + lam3^2 G], two
-    single-signed terms (FP64 runs with lam4 = 0 and with lam3 = 0); the
-    lambda3 and lambda4 blocks are single-signed, |ref| is their scale."""
-    import paper_2412_13043_gb300 as ffrg
-    n = wl.problem.n_ext_p + 1
-    parts = []
-    for zero in (2, 1):
-        t = wl.tables.copy()
-        t[zero] = 0.0
-        parts.append(np.abs(_run(ctx, fi.Workload(wl.problem, t, None), k, ffrg.FP64)[:n]))
-    scale = np.abs(ref).copy()
-    scale[:n] = parts[0] + parts[1]
-    return scale
-
-
-def test_d4_full_mixed_bound_on_every_output(ctx):
-    """All 961 outputs of the 96 x 8 x 7 workload: mixed within MIXED_TOL of
-    the FP64 path (itself checked against the oracle above) relative to the
-    magnitude of the cancelling parts (the Z block crosses zero near
-    p = 1.75 on this workload).  Short legs (q << p) make the FP32 shape
-    variable ill-conditioned in its magnitude form; the kernel takes it from
-    the leg components."""
-    import paper_2412_13043_gb300 as ffrg
-    wl = fi.make_d4_full(n_rad=64, n_ang1=32, n_ang2=8)
+def test_d4_full_full_size_every_output(ctx):
+    """96-point log grid x 8 x 7 vertex grid, 961 external points x
+    (128 x 64 x 16) nodes, every output against the oracle."""
+    wl = fi.make_d4_full()
     for k in (1.0, 0.1):
-        g64 = _run(ctx, wl, k, ffrg.FP64)
-        g32 = _run(ctx, wl, k, ffrg.MIXED)
-        e = np.abs(g32 - g64) / _termwise_scale(ctx, wl, k, g64)
-        assert np.max(e) < MIXED_TOL, (k, np.max(e), int(np.argmax(e)))
+        _check(ctx, wl, k)
 
 
 def test_d4_full_reduces_to_d4_vertex_on_gpu(ctx):
@@ -252,11 +249,10 @@ def test_finite_t_small_ragged(ctx):
 
 
 @pytest.mark.parametrize("N,T_over_kend", [(16, 0.05), (32, 0.2), (64, 1.0)])
-def test_finite_t_full_size_sampled(ctx, N, T_over_kend):
-    wl = fi.make_finite_t(seed=3, N=N, T=T_over_kend * 0.01)   # 64 |p| x 9 p0, 96 x 48 x (2N+1)
-    ne = wl.problem.n_ext()
-    sel = [0, 8, 9 * 20 + 4, 9 * 40 + 1, ne - 9, ne - 1]
-    _check(ctx, wl, 1.0, sel=sel)
+def test_finite_t_full_size_every_output(ctx, N, T_over_kend):
+    """64 |p| x 9 p0 external points x 96 x 48 x (2N+1) nodes, every output."""
+    wl = fi.make_finite_t(seed=3, N=N, T=T_over_kend * 0.01)
+    _check(ctx, wl, 1.0)
 
 
 # ----------------------------------------------------------------------------- fermionic loop
@@ -269,12 +265,11 @@ def test_finite_t_fermionic_small_ragged(ctx):
             _check(ctx, wl, k)
 
 
-@pytest.mark.parametrize("N,T_over_kend", [(16, 0.05), (64, 1.0)])
-def test_finite_t_fermionic_full_size_sampled(ctx, N, T_over_kend):
-    wl = fi.make_finite_t(seed=4, N=N, T=T_over_kend * 0.01, fermionic=True)   # 96 x 48 x (2N+2)
-    ne = wl.problem.n_ext()
-    sel = [0, 8, 9 * 20 + 4, 9 * 40 + 1, ne - 9, ne - 1]
-    _check(ctx, wl, 1.0, sel=sel)
+@pytest.mark.parametrize("N,T_over_kend", [(16, 0.05), (32, 0.2), (64, 1.0)])
+def test_finite_t_fermionic_full_size_every_output(ctx, N, T_over_kend):
+    """Fermionic loop, 96 x 48 x (2N+2) nodes, every output."""
+    wl = fi.make_finite_t(seed=4, N=N, T=T_over_kend * 0.01, fermionic=True)
+    _check(ctx, wl, 1.0)
 
 
 def test_finite_t_fermionic_litim_closed_form_on_gpu(ctx):
