@@ -184,10 +184,14 @@ def cpu_baseline(wl, stride: int, stride_1t: int = 32):
             "single_thread": {"value": v1, "unit": "integrand evals/s", "cores": 1, "sample": sample1}}
 
 
-def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
-    """Served mixed-precision flows (continuous batching) vs one flow at a time
-    through ffrg_flow in FP64 and mixed precision; p50/p99 latency under
-    Poisson arrivals at 0.8x the measured served capacity."""
+def serving_bench(ctx, n_req: int, seconds_cap: float = 120.0):
+    """Served mixed-precision flows (continuous batching) against the plain
+    path, one flow at a time through ffrg_flow in FP64 and in mixed precision,
+    on the same requests.  The launch plans of every request shape are built
+    before any timing; each one-at-a-time flow is timed from its table upload
+    to its result on the host, like a served request from submit to poll.
+    Every served endpoint is compared with its FP64 counterpart; p50/p99
+    latency under Poisson arrivals at 0.8x the measured served capacity."""
     import numpy as np
     import torch
 
@@ -199,23 +203,30 @@ def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
     def t1_of(wl):
         return math.log(wl.Lambda / wl.k_end)
 
-    # one flow at a time (the plain path), FP64 and mixed, on the first n_fp64 requests
+    for rq in reqs:                       # plans (device scratch, rules, launch geometry) per shape
+        wl = rq.workload
+        tabs = ctx.tables(wl.problem, wl.tables)
+        for prec in (ffrg.FP64, ffrg.MIXED):
+            ctx.rhs(wl.problem, tabs, wl.Lambda, precision=prec)
+        torch.cuda.synchronize()
+        tabs.free()
+
     single = {}
     for name, prec in (("fp64", ffrg.FP64), ("mixed", ffrg.MIXED)):
-        outs, t_tot, ev = [], 0.0, 0.0
-        for rq in reqs[:n_fp64]:
+        outs, times, ev = [], [], 0.0
+        for rq in reqs:
             wl = rq.workload
-            tabs = ctx.tables(wl.problem, wl.tables)
-            y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
             t = time.perf_counter()
+            tabs = ctx.tables(wl.problem, wl.tables)
+            y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
             fs = ctx.flow(wl.problem, tabs, y, wl.Lambda, t1_of(wl), precision=prec, rtol=rtol, atol=atol)
-            torch.cuda.synchronize()
-            t_tot += time.perf_counter() - t
-            ev += fs["integrand_evals"]
             outs.append(y.cpu().numpy())
+            times.append(time.perf_counter() - t)
             tabs.free()
-        single[name] = {"flows_per_s": len(outs) / t_tot, "evals_per_s": ev / t_tot, "outs": outs}
+            ev += fs["integrand_evals"]
+        single[name] = {"flows_per_s": len(outs) / sum(times), "evals_per_s": ev / sum(times), "outs": outs,
+                        "p50_s": sorted(times)[len(times) // 2]}
 
     def run(arrivals):
         ctx.serve_start(max_slots=64, max_queue=len(reqs) + 8, hbm_budget_bytes=8 << 30)
@@ -247,8 +258,37 @@ def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
 
     wall, lat_sat, res, stats, ev_sat = run([0.0] * len(reqs))
     capacity = len(reqs) / wall
-    err = max(float(np.max(np.abs(res[j] - single["fp64"]["outs"][j]) / np.abs(single["fp64"]["outs"][j])))
-              for j in range(n_fp64))
+
+    # Endpoint errors of a flow y(t1) = y0 - int I dt against a reference r:
+    #   norm: max_i |y_i - r_i| / max_i |r_i|  (the endpoint accuracy compared)
+    #   cancel: max_i |y_i - r_i| / (|y0_i| + |r_i - y0_i|), each component
+    #     against the magnitudes of the two parts that can cancel (components
+    #     that end near zero: y0 and the integrated flow nearly equal)
+    #   elem: max_i |y_i - r_i| / |r_i|
+    def endpoint_errs(y, r, y0):
+        d = np.abs(y - r)
+        return (float(np.max(d) / np.max(np.abs(r))), float(np.max(d / (np.abs(y0) + np.abs(r - y0)))),
+                float(np.max(d / np.abs(r))))
+
+    def errs(other):
+        return np.array([endpoint_errs(res[j], single[other]["outs"][j], reqs[j].workload.y0)
+                         for j in range(len(reqs))])
+    e64 = errs("fp64")
+    emx = errs("mixed")
+    # truth (FP64 at rtol 1e-13) on a seeded sample: every path's endpoint error
+    sample = sorted(np.random.default_rng(11).choice(len(reqs), min(64, len(reqs)), replace=False).tolist())
+    vs_truth = {"served": np.zeros(3), "fp64": np.zeros(3), "mixed": np.zeros(3)}
+    for j in sample:
+        wl = reqs[j].workload
+        tabs = ctx.tables(wl.problem, wl.tables)
+        y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+        ctx.flow(wl.problem, tabs, y, wl.Lambda, t1_of(wl), precision=ffrg.FP64, rtol=1e-13, atol=1e-16)
+        tr = y.cpu().numpy()
+        tabs.free()
+        for name, v in (("served", res[j]), ("fp64", single["fp64"]["outs"][j]),
+                        ("mixed", single["mixed"]["outs"][j])):
+            vs_truth[name] = np.maximum(vs_truth[name], endpoint_errs(v, tr, wl.y0))
+    keys = ("norm", "cancel", "elem")
     rate = 0.8 * capacity
     arrivals = [rq.arrival_s * (200.0 / rate) for rq in reqs]   # the stream was drawn at 200 Hz
     wall_p, lat, _, stats_p, _ = run(arrivals)
@@ -256,17 +296,26 @@ def serving_bench(ctx, n_req: int, n_fp64: int = 8, seconds_cap: float = 60.0):
     return {"requests": len(reqs), "families": "T=0 d3 frozen flows and finite-T frozen flows, "
                                               "ext 32-256, radial 32-128, angular 16-64, tables 64-256 pts",
             "served_flows_per_s": capacity, "served_integrand_evals_per_s": ev_sat / wall,
-            "fp64_one_at_a_time_evals_per_s": single["fp64"]["evals_per_s"],
-            "mixed_one_at_a_time_evals_per_s": single["mixed"]["evals_per_s"],
-            "peak_resident": stats["peak_resident"], "ticks": stats["ticks"],
             "fp64_one_at_a_time_flows_per_s": single["fp64"]["flows_per_s"],
             "mixed_one_at_a_time_flows_per_s": single["mixed"]["flows_per_s"],
+            "fp64_one_at_a_time_evals_per_s": single["fp64"]["evals_per_s"],
+            "mixed_one_at_a_time_evals_per_s": single["mixed"]["evals_per_s"],
+            "one_at_a_time_timing": "every request, plans built beforehand, upload + flow + result copy",
             "speedup_served_over_fp64": capacity / single["fp64"]["flows_per_s"],
-            "sample_for_one_at_a_time": n_fp64,
-            "served_vs_fp64_endpoint_max_rel_diff": err, "rtol": rtol,
+            "speedup_served_over_mixed_one_at_a_time": capacity / single["mixed"]["flows_per_s"],
+            "peak_resident": stats["peak_resident"], "ticks": stats["ticks"],
+            "endpoint_error_measures": "norm = max|y - r| / max|r|; cancel = max |y_i - r_i| / (|y0_i| + "
+                                       "|r_i - y0_i|); elem = max |y_i - r_i| / |r_i|",
+            "served_vs_fp64_endpoint_max": dict(zip(keys, e64.max(axis=0).tolist())),
+            "served_vs_fp64_endpoint_p99": dict(zip(keys, np.quantile(e64, 0.99, axis=0).tolist())),
+            "served_vs_mixed_one_at_a_time_max": dict(zip(keys, emx.max(axis=0).tolist())),
+            "endpoint_max_vs_truth": {**{nm: dict(zip(keys, v.tolist())) for nm, v in vs_truth.items()},
+                                      "sample": len(sample), "truth": "FP64 ffrg_flow at rtol 1e-13, atol 1e-16"},
+            "endpoints_compared": len(reqs), "rtol": rtol,
             "poisson_rate_hz": rate, "poisson_flows_per_s": len(reqs) / wall_p,
             "latency_p50_s": lv[len(lv) // 2], "latency_p99_s": lv[min(len(lv) - 1, int(0.99 * len(lv)))],
-            "saturation_latency_p50_s": sorted(lat_sat.values())[len(lat_sat) // 2]}
+            "saturation_latency_p50_s": sorted(lat_sat.values())[len(lat_sat) // 2],
+            "fp64_one_at_a_time_p50_s": single["fp64"]["p50_s"]}
 
 
 def stepper_bench(ctx):
@@ -602,6 +651,19 @@ def main():
             "models": models,
             "cpu_baseline": cpu,
         }
+        # last key of the line, so that a truncated tail of the output still shows it
+        summ = {"fp64_d4_evals_per_s": line["fp64_path"]["value"],
+                "mixed_over_fp64_d4": line["fp64_path"]["speedup_mixed_over_fp64"]}
+        if serving:
+            summ.update({k: serving[k] for k in (
+                "served_flows_per_s", "fp64_one_at_a_time_flows_per_s", "speedup_served_over_fp64",
+                "mixed_one_at_a_time_flows_per_s", "latency_p50_s", "latency_p99_s",
+                "endpoints_compared")})
+            summ["served_vs_fp64_endpoint_norm_max"] = serving["served_vs_fp64_endpoint_max"]["norm"]
+            vt = serving["endpoint_max_vs_truth"]
+            summ["endpoint_vs_truth_norm_max"] = {"served": vt["served"]["norm"], "fp64": vt["fp64"]["norm"]}
+            summ["endpoint_vs_truth_cancel_max"] = {"served": vt["served"]["cancel"], "fp64": vt["fp64"]["cancel"]}
+        line["summary"] = summ
         print(json.dumps(line))
     tabs.free()
     ctx.close()

@@ -197,10 +197,13 @@ FFRG_API double ffrg_evals(const ffrg_problem *pb);
  * integrand and row sums, compensated FP32 accumulation within a work item
  * rounded once to FP64, FP64 across work items, FP64 per-radial-node
  * factors, FP64 propagator near the pole).  Asynchronous; non-finite outputs
- * set FFRG_ENONFINITE in the status word.  Errors: FFRG_EINVAL for a bad
- * problem, tables of another shape, or tables and rules that do not fit in
- * the 227 KB of shared memory of a block (8 bytes per table node in either
- * precision, plus the angle rules); FFRG_ENOMEM (budget); FFRG_ECUDA. */
+ * set FFRG_ENONFINITE in the status word.  The kernels stage the tables and
+ * rules in the 227 KB of shared memory of a block; FP64 tables that do not fit
+ * (8 bytes per value) are read in place from global memory (L2) instead.
+ * Errors: FFRG_EINVAL for a bad problem, tables of another shape, or, in mixed
+ * precision, FP32 tables and rules that do not fit in shared memory (8 bytes
+ * per table node: one FP32 line-form pair, or the (Z, lambda) pair of finite
+ * T, plus the angle rules); FFRG_ENOMEM (budget); FFRG_ECUDA. */
 FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_dev,
              int precision, void *stream);
 
@@ -317,7 +320,9 @@ FFRG_API int ffrg_profile_read(ffrg_ctx *ctx, double *main_ms, long long *launch
 typedef struct {
   int max_slots;            /* resident flows at once, 1..256 */
   int max_queue;            /* queued requests before submit returns FFRG_EBUSY */
-  size_t hbm_budget_bytes;  /* device memory for resident flows (0: 1 GiB) */
+  size_t hbm_budget_bytes;  /* device memory for resident flows (0: 1 GiB), reserved
+                               by ffrg_serve_start; slot buffers are carved from it
+                               on the host, so admission never calls a device allocator */
 } ffrg_serve_opts;
 
 typedef struct {

@@ -295,6 +295,7 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   const size_t ang32 = ang + (size_t)4 * ((pl->na2 + 1) / 2);   // + second-angle node pairs
   pl->smem64 = al16((size_t)(pl->tabc_count ? pl->tabc_count : pl->tab_count) * 8) + al16(ang * 8);
   pl->smem32 = al16((size_t)pl->tab32_count * 8) + al16(ang32 * 4);
+  pl->smem64g = al16(ang * 8);
 }
 
 int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, Plan **out) {
@@ -496,6 +497,10 @@ int ffrg_destroy(ffrg_ctx *ctx) {
   ctx->plans.clear();
   for (void *p : ctx->owned) cudaFree(p);
   for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+  if (ctx->flow_dev) cudaFree(ctx->flow_dev);
+  if (ctx->flow_host) cudaFreeHost(ctx->flow_host);
+  if (ctx->flow_ev) cudaEventDestroy(ctx->flow_ev);
+  if (ctx->flow_stream) cudaStreamDestroy(ctx->flow_stream);
   if (ctx->status_dev) cudaFree(ctx->status_dev);
   if (ctx->status_host) cudaFreeHost(ctx->status_host);
   delete ctx;

@@ -486,23 +486,43 @@ extern "C" int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_ta
   if (st) return st;
   const int n_ext = pl->n_ext;
 
-  // device buffers of this flow
-  FlowCtl *ctl = nullptr;
-  double *ys = nullptr, *K = nullptr, *raw = nullptr, *tabbuf = nullptr;
-  FlowCtl *ctl_host = nullptr;
-  const size_t tab_bytes = ((size_t)pl->tab_count * sizeof(double) + 255) & ~(size_t)255;
-  st = dev_alloc(ctx, (void **)&ctl, sizeof(FlowCtl));
-  if (!st) st = dev_alloc(ctx, (void **)&ys, (size_t)ny * sizeof(double));
-  if (!st) st = dev_alloc(ctx, (void **)&K, (size_t)7 * ny * sizeof(double));
-  if (!st) st = dev_alloc(ctx, (void **)&raw, (size_t)n_ext * sizeof(double));
-  if (!st && mode != kModeFrozen) st = dev_alloc(ctx, (void **)&tabbuf, tab_bytes);
-  if (!st) st = set_cuda_error(ctx, cudaMallocHost((void **)&ctl_host, sizeof(FlowCtl)), "cudaMallocHost");
-  cudaStream_t user = (cudaStream_t)stream, fs = nullptr;
-  cudaEvent_t ev = nullptr;
+  // device buffers of this flow: segments of the context's flow scratch
+  // (kept between calls, grown when this flow needs more)
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t o_ys = al(sizeof(FlowCtl)), o_K = o_ys + al((size_t)ny * sizeof(double));
+  const size_t o_raw = o_K + al((size_t)7 * ny * sizeof(double));
+  const size_t o_tab = o_raw + al((size_t)n_ext * sizeof(double));
+  const size_t need = o_tab + (mode != kModeFrozen ? al((size_t)pl->tab_count * sizeof(double)) : 0);
+  if (ctx->flow_cap < need) {
+    dev_free(ctx, ctx->flow_dev, ctx->flow_cap);
+    ctx->flow_dev = nullptr;
+    ctx->flow_cap = 0;
+    st = dev_alloc(ctx, &ctx->flow_dev, need);
+    if (st) return st;
+    ctx->flow_cap = need;
+  }
+  if (!ctx->flow_host) {
+    st = set_cuda_error(ctx, cudaMallocHost(&ctx->flow_host, sizeof(FlowCtl)), "cudaMallocHost");
+    if (st) return st;
+  }
+  if (!ctx->flow_stream) {
+    st = set_cuda_error(ctx, cudaStreamCreateWithFlags(&ctx->flow_stream, cudaStreamNonBlocking),
+                        "cudaStreamCreate");
+    if (st) return st;
+  }
+  if (!ctx->flow_ev) {
+    st = set_cuda_error(ctx, cudaEventCreateWithFlags(&ctx->flow_ev, cudaEventDisableTiming), "cudaEventCreate");
+    if (st) return st;
+  }
+  unsigned char *fb = (unsigned char *)ctx->flow_dev;
+  FlowCtl *ctl = (FlowCtl *)fb;
+  double *ys = (double *)(fb + o_ys), *K = (double *)(fb + o_K), *raw = (double *)(fb + o_raw);
+  double *tabbuf = mode != kModeFrozen ? (double *)(fb + o_tab) : nullptr;
+  FlowCtl *ctl_host = (FlowCtl *)ctx->flow_host;
+  cudaStream_t user = (cudaStream_t)stream, fs = ctx->flow_stream;
+  cudaEvent_t ev = ctx->flow_ev;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  if (!st) st = set_cuda_error(ctx, cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking), "cudaStreamCreate");
-  if (!st) st = set_cuda_error(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
 
   FlowCtl hc;
   memset(&hc, 0, sizeof(hc));
@@ -611,15 +631,7 @@ extern "C" int ffrg_flow(ffrg_ctx *ctx, const ffrg_problem *pb_in, const ffrg_ta
   }
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
-  if (fs) cudaStreamSynchronize(fs);
-  if (ev) cudaEventDestroy(ev);
-  if (fs) cudaStreamDestroy(fs);
-  if (ctl_host) cudaFreeHost(ctl_host);
-  dev_free(ctx, ctl, sizeof(FlowCtl));
-  dev_free(ctx, ys, (size_t)ny * sizeof(double));
-  dev_free(ctx, K, (size_t)7 * ny * sizeof(double));
-  dev_free(ctx, raw, (size_t)n_ext * sizeof(double));
-  dev_free(ctx, tabbuf, tab_bytes);
+  cudaStreamSynchronize(fs);
   return st;
 }
 

@@ -51,6 +51,8 @@ struct RhsArgs {
   int n_chunks;    // work items per external point
   int n_items;     // n_ext * n_chunks
   int jb;          // angle nodes per row (D3 / FINITE_T; rows = outer index x angle block)
+  int tab_global;  // FP64 main kernels: tables read in place from global memory (L2), not staged,
+                   // because they exceed shared memory; only the angle rules are staged
   double k, m2_over_k2, m2_shift, T;
   double p_min, p_ratio_step;  // p_i = p_min * exp(i * p_ratio_step)
   double qmax_over_k;
@@ -414,6 +416,14 @@ struct ffrg_ctx {
   int profiling;
   std::vector<cudaEvent_t> prof_events;  // start/stop pairs
   int prof_used;                         // pairs recorded
+  // ffrg_flow's per-flow buffers (control block, stage state, stage
+  // derivatives, raw RHS, feedback tables), pinned control-block mirror,
+  // stream and event: kept between calls, grown when a flow needs more
+  void *flow_dev = nullptr;
+  size_t flow_cap = 0;
+  void *flow_host = nullptr;
+  cudaStream_t flow_stream = nullptr;
+  cudaEvent_t flow_ev = nullptr;
 };
 
 namespace ffrg {
@@ -437,6 +447,7 @@ struct Plan {
   double *kbuf;
   int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
   size_t smem64, smem32;    // dynamic shared memory bytes
+  size_t smem64g;           // FP64 kernels with tables in global memory: angle rules only
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;
   double sum_w2;
   double *radF, *radq, *partial, *ext_pd, *psi_s;

@@ -397,6 +397,13 @@ struct Pair2<float> {
 };
 
 template <typename T>
+__device__ __forceinline__ const typename TabOf<T>::type *table_src(const RhsArgs &a);
+template <>
+__device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { return a.tabc ? a.tabc : a.tab; }
+template <>
+__device__ __forceinline__ const float2 *table_src<float>(const RhsArgs &a) { return a.tab32; }
+
+template <typename T>
 struct SmemLayout {
   using Tab = typename TabOf<T>::type;
   using P2 = typename Pair2<T>::type;
@@ -408,9 +415,12 @@ struct SmemLayout {
   static __device__ int entries(const RhsArgs &a) {
     return sizeof(T) == 4 ? a.tab32_count : (a.tabc_count ? a.tabc_count : a.tab_count);
   }
+  // FP64 kernels whose tables exceed shared memory read them in place (L2)
+  static __device__ bool in_global(const RhsArgs &a) { return sizeof(T) == 8 && a.tab_global; }
   __device__ SmemLayout(unsigned char *base, const RhsArgs &a) {
-    tab = (Tab *)base;
-    size_t off = ((size_t)entries(a) * sizeof(Tab) + 15) & ~(size_t)15;
+    const bool g = in_global(a);
+    tab = g ? const_cast<Tab *>(table_src<T>(a)) : (Tab *)base;
+    size_t off = g ? 0 : ((size_t)entries(a) * sizeof(Tab) + 15) & ~(size_t)15;
     cw4 = (float4 *)(base + off);
     if (sizeof(T) == 4) off += (size_t)((a.na2 + 1) / 2) * sizeof(float4);
     cw2 = (P2 *)(base + off);
@@ -419,13 +429,6 @@ struct SmemLayout {
     w1 = s1 + a.na1;
   }
 };
-
-template <typename T>
-__device__ __forceinline__ const typename TabOf<T>::type *table_src(const RhsArgs &a);
-template <>
-__device__ __forceinline__ const double *table_src<double>(const RhsArgs &a) { return a.tabc ? a.tabc : a.tab; }
-template <>
-__device__ __forceinline__ const float2 *table_src<float>(const RhsArgs &a) { return a.tab32; }
 
 __device__ __forceinline__ double table_value(double v) { return v; }
 __device__ __forceinline__ float table_value(float2 v) { return v.x; }
@@ -460,8 +463,9 @@ __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S)
 
 template <typename T>
 __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
-  bool ok = stage_to_smem<typename TabOf<T>::type>(S.tab, table_src<T>(a), SmemLayout<T>::entries(a), bar,
-                                                   a.status);
+  bool ok = true;
+  if (!SmemLayout<T>::in_global(a))   // uniform over the block
+    ok = stage_to_smem<typename TabOf<T>::type>(S.tab, table_src<T>(a), SmemLayout<T>::entries(a), bar, a.status);
   stage_angles<T>(a, S);
   __syncthreads();
   return ok;
@@ -1103,10 +1107,11 @@ __global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
 
 
 // ---------------------------------------------------------------------------
+constexpr size_t kMaxDynSmem = 227 * 1024;   // dynamic shared memory of one block
+
 template <typename K>
 static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int *grid) {
-  static const size_t kMaxSmem = 227 * 1024;
-  if (smem > kMaxSmem) {
+  if (smem > kMaxDynSmem) {
     ctx->last_error = "dressing tables do not fit in shared memory";
     return FFRG_EINVAL;
   }
@@ -1149,7 +1154,12 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
   }
   int st;
   int &grid = mixed ? pl->grid32 : pl->grid64;
-  const size_t smem = mixed ? pl->smem32 : pl->smem64;
+  size_t smem = mixed ? pl->smem32 : pl->smem64;
+  a.tab_global = 0;
+  if (!mixed && smem > kMaxDynSmem) {   // FP64 tables beyond shared memory: read from L2
+    a.tab_global = 1;
+    smem = pl->smem64g;
+  }
   void (*kern)(RhsArgs) = nullptr;
   switch (a.model) {
   case FFRG_MODEL_D3: kern = mixed ? rhs_main<FFRG_MODEL_D3, float> : rhs_main<FFRG_MODEL_D3, double>; break;

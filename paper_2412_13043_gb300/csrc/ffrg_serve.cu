@@ -15,6 +15,11 @@
 //
 // Requests: frozen-background flows (d_t y = -Flow, Sec. 5.2.2 Eqs. assVar /
 // flowVar) of the d=3 and finite-T models, mixed precision.
+//
+// Memory: the HBM budget is reserved once, at start, and slot buffers are
+// carved from that reservation on the host (first fit, coalesced on return),
+// so admitting and retiring flows never calls a device allocator: nothing on
+// the tick path synchronises the device.
 #include <math.h>
 #include <string.h>
 
@@ -22,6 +27,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -103,6 +109,52 @@ static void slot_layout(const ffrg_problem *pb, const ffrg_table_desc *td, SlotL
   L.bytes = u;
 }
 
+// First-fit allocator over one device reservation; host bookkeeping only.
+// Offsets and sizes are multiples of 256 bytes.
+struct Arena {
+  unsigned char *base = nullptr;
+  size_t size = 0, used = 0;
+  std::map<size_t, size_t> free_list;  // offset -> length, no two adjacent
+  static size_t round(size_t n) { return (std::max<size_t>(n, 1) + 255) & ~(size_t)255; }
+  void init(unsigned char *b, size_t n) {
+    base = b;
+    size = n;
+    used = 0;
+    free_list.clear();
+    if (n) free_list[0] = n;
+  }
+  unsigned char *take(size_t n) {
+    n = round(n);
+    for (auto it = free_list.begin(); it != free_list.end(); ++it)
+      if (it->second >= n) {
+        const size_t off = it->first, len = it->second;
+        free_list.erase(it);
+        if (len > n) free_list[off + n] = len - n;
+        used += n;
+        return base + off;
+      }
+    return nullptr;
+  }
+  void give(unsigned char *p, size_t n) {
+    if (!p) return;
+    n = round(n);
+    used -= n;
+    auto it = free_list.emplace((size_t)(p - base), n).first;
+    auto nx = std::next(it);
+    if (nx != free_list.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_list.erase(nx);
+    }
+    if (it != free_list.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_list.erase(it);
+      }
+    }
+  }
+};
+
 struct Slot {
   ServeReq *req = nullptr;
   unsigned char *buf = nullptr;
@@ -139,7 +191,8 @@ struct Server {
   std::unordered_map<unsigned long long, ServeReq *> reqs;
   unsigned long long next_id = 1;
   std::vector<Slot> slots;
-  size_t hbm_used = 0;
+  unsigned char *arena_mem = nullptr;  // the reserved HBM budget
+  Arena arena;                         // slot buffers carved from it
   cudaStream_t st = nullptr;  // ticks: batched steps and first derivatives
   cudaStream_t io = nullptr;  // request uploads and result copies
   FlowCtl *ctl_dev = nullptr;
@@ -367,7 +420,9 @@ static int retire(Server &S, int si, const FlowCtl &c, int status) {
 }
 
 // Admit queued requests (first come, first served) while a slot is free and
-// the HBM budget holds the request's buffers.
+// the reserved HBM budget has a contiguous range for the request's buffers;
+// otherwise the head of the queue waits for retiring flows to return theirs.
+// Host bookkeeping only: no device allocation or free.
 static int admit(Server &S) {
   for (;;) {
     ServeReq *r = nullptr;
@@ -384,42 +439,16 @@ static int admit(Server &S) {
       for (int i = 0; i < (int)S.slots.size() && si < 0; ++i)
         if (!S.slots[i].req && !S.slots[i].cooling) si = i;
       if (si < 0) return FFRG_OK;
-      // a free slot whose buffer is large enough avoids a new allocation
-      for (int i = 0; i < (int)S.slots.size(); ++i)
-        if (!S.slots[i].req && !S.slots[i].cooling && S.slots[i].cap >= r->need) {
-          si = i;
-          break;
-        }
-      Slot &sl = S.slots[si];
-      const size_t grow = sl.cap >= r->need ? 0 : r->need - sl.cap;
-      if (S.hbm_used + grow > S.opts.hbm_budget_bytes) {
-        // release idle buffers before giving up
-        for (auto &o : S.slots)
-          if (!o.req && !o.cooling && o.buf && &o != &sl) {
-            cudaFree(o.buf);
-            S.hbm_used -= o.cap;
-            o.buf = nullptr;
-            o.cap = 0;
-          }
-        if (S.hbm_used + grow > S.opts.hbm_budget_bytes) return FFRG_OK;
-      }
+      unsigned char *buf = S.arena.take(r->need);
+      if (!buf) return FFRG_OK;
       S.queue.pop_front();
       r->state = kResident;
+      Slot &sl = S.slots[si];
       sl.req = r;
+      sl.buf = buf;
+      sl.cap = r->need;
     }
     Slot &sl = S.slots[si];
-    if (sl.cap < r->need) {
-      if (sl.buf) {
-        cudaFree(sl.buf);
-        S.hbm_used -= sl.cap;
-        sl.buf = nullptr;
-        sl.cap = 0;
-      }
-      cudaError_t e = cudaMalloc((void **)&sl.buf, r->need);
-      if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve slot allocation");
-      sl.cap = r->need;
-      S.hbm_used += sl.cap;
-    }
     slot_layout(&r->pb, &r->td, sl.L);
     int st = slot_setup(S, si);
     if (st) return st;
@@ -464,7 +493,7 @@ static void scheduler(Server *Sp) {
         S.stats.ticks++;
         S.stats.resident = (int)T.live.size();
         S.stats.peak_resident = std::max(S.stats.peak_resident, (int)T.live.size());
-        S.stats.hbm_in_use = S.hbm_used;
+        S.stats.hbm_in_use = S.arena.used;
       }
       const FlowCtl *ctl = S.ctl_host + (size_t)b * S.slots.size();
       for (int i : T.live) {
@@ -485,7 +514,12 @@ static void scheduler(Server *Sp) {
       if (st) break;
       for (size_t k = 0; k < cooling.size();)
         if (cooling[k].second <= T.id) {
-          S.slots[cooling[k].first].cooling = false;
+          // no tick in flight reads the slot any more: its range returns to the arena
+          Slot &cs = S.slots[cooling[k].first];
+          cs.cooling = false;
+          S.arena.give(cs.buf, cs.cap);
+          cs.buf = nullptr;
+          cs.cap = 0;
           cooling[k] = cooling.back();
           cooling.pop_back();
         } else {
@@ -596,6 +630,10 @@ extern "C" int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts) {
   if (e == cudaSuccess) e = cudaMalloc((void **)&S->status_dev, 16);
   if (e == cudaSuccess) e = cudaMemset(S->status_dev, 0, 16);
   if (e == cudaSuccess) e = cudaMallocHost((void **)&S->stage_host, set_bytes * 2);
+  // the whole HBM budget of the resident flows, reserved once
+  const size_t arena_bytes = S->opts.hbm_budget_bytes & ~(size_t)255;
+  if (e == cudaSuccess) e = cudaMalloc((void **)&S->arena_mem, std::max<size_t>(arena_bytes, 256));
+  if (e == cudaSuccess) S->arena.init(S->arena_mem, arena_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the memsets above ran on the legacy stream
   for (LaunchSet *ls : {&S->step_set, &S->init_set}) {
     unsigned char *blk = nullptr;
@@ -610,6 +648,7 @@ extern "C" int ffrg_serve_start(ffrg_ctx *ctx, const ffrg_serve_opts *opts) {
     cudaFreeHost(S->ctl_host);
     cudaFree(S->status_dev);
     cudaFreeHost(S->stage_host);
+    cudaFree(S->arena_mem);
     cudaFree(S->step_set.descs);
     cudaFree(S->init_set.descs);
     for (int b = 0; b < kTickDepth; ++b)
@@ -655,7 +694,7 @@ extern "C" int ffrg_serve_submit(ffrg_ctx *ctx, const ffrg_problem *pb, const ff
     delete r;
     return S->fatal ? S->fatal : FFRG_EINVAL;
   }
-  if (r->need > S->opts.hbm_budget_bytes) {
+  if (Arena::round(r->need) > S->arena.size) {
     S->stats.rejected++;
     delete r;
     return FFRG_ENOMEM;
@@ -725,8 +764,8 @@ extern "C" int ffrg_serve_stop(ffrg_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(S->st);
   cudaStreamSynchronize(S->io);
-  for (auto &sl : S->slots) cudaFree(sl.buf);
   for (auto &kv : S->reqs) delete kv.second;
+  cudaFree(S->arena_mem);
   cudaFree(S->ctl_dev);
   cudaFreeHost(S->ctl_host);
   cudaFree(S->status_dev);

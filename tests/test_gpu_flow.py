@@ -17,7 +17,7 @@ from gpu_common import gpu_context
 
 pytestmark = pytest.mark.gpu
 ENDPOINT_TOL = 1e-8
-MIXED_ENDPOINT_TOL = 1e-7
+MIXED_ENDPOINT_TOL = 1e-8
 # d=4 feedback: d_t Z_i = -(D2(p_i) - D2(0))/p_i^2 amplifies the FP32 integrand
 # error (~3e-7 per RHS value) by |D2|/|D2(p_i) - D2(0)| ~ (k/p_i)^2 for p_i << k;
 # the stated bound of the mixed path on this flow is 5e-6.

@@ -323,20 +323,35 @@ def test_finite_t_maximum_matsubara_count(ctx):
     _check(ctx, wl, 0.5)
 
 
-def test_tables_beyond_shared_memory_rejected(ctx):
-    """Stacks that do not fit in shared memory (4097 rows x 8 points: 524 KB
-    FP64, 262 KB FP32) are refused before any launch."""
+def test_fp64_tables_beyond_shared_memory_read_from_l2(ctx):
+    """A stack larger than shared memory (4097 rows x 8 points: 524 KB in
+    FP64) runs in the FP64 kernels with the tables read in place from global
+    memory (L2) and matches the oracle; the mixed kernels, whose FP32 rows are
+    addressed in shared memory (262 KB here), refuse it before any launch."""
     import torch
 
     import paper_2412_13043_gb300 as ffrg
     wl = fi.make_finite_t(seed=24, N=4096, T=0.002, n_pts=8, n_ext_p=1, n_ext_m=1, n_rad=2, n_ang=2)
+    ref = oracle.rhs(wl.problem, wl.tables, 0.5)
+    got = _run(ctx, wl, 0.5, ffrg.FP64)
+    assert np.max(rel_err(got, ref)) < FP64_TOL
     tabs = ctx.tables(wl.problem, wl.tables)
     out = torch.empty(wl.problem.n_ext(), dtype=torch.float64, device="cuda")
-    for prec in (ffrg.FP64, ffrg.MIXED):
-        with pytest.raises(ffrg.FfrgError):
-            ctx.rhs(wl.problem, tabs, 0.5, out=out, precision=prec)
+    with pytest.raises(ffrg.FfrgError):
+        ctx.rhs(wl.problem, tabs, 0.5, out=out, precision=ffrg.MIXED)
     assert ctx.status_read() == ffrg.OK
     tabs.free()
+
+
+@pytest.mark.parametrize("fermionic", [False, True])
+def test_finite_t_fp64_stack_of_the_serving_mix_beyond_shared_memory(ctx, fermionic):
+    """N = 64 with 256-point tables (a request of the serving mix): 73 rows x
+    256 points x 2 tables = 299 KB in FP64, read from L2 by the FP64 kernels;
+    the mixed kernels stage it (150 KB of FP32 pairs)."""
+    wl = fi.make_finite_t(seed=25, N=64, T=0.0002, n_pts=256, n_ext_p=3, n_ext_m=9, n_rad=16, n_ang=8,
+                          fermionic=fermionic)
+    for k in (1.0, 0.05):
+        _check(ctx, wl, k)
 
 
 def test_nonfinite_table_sets_status(ctx):
