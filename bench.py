@@ -361,6 +361,31 @@ def stepper_bench(ctx):
             "runs": rows}
 
 
+def adjoint_bench(ctx, wl, tabs, reps: int = 3):
+    """Reverse-mode derivatives of the d=4 RHS with respect to the 3 x 128
+    table values at the full workload size (FP64): one VJP
+    (ffrg_rhs_adjoint) and the full 1281 x 384 Jacobian (ffrg_rhs_jacobian),
+    each against the FP64 RHS of the same workload."""
+    import torch
+    pb = wl.problem
+    g = torch.ones(pb.n_ext(), dtype=torch.float64, device="cuda")
+    J = ctx.rhs_jacobian(pb, tabs, 1.0)
+    ctx.rhs_adjoint(pb, tabs, 1.0, g)
+    torch.cuda.synchronize()
+    res = {"workload": "d4 vertex RHS, 3 x 128-pt tables, 1281 ext x (128 x 64 x 16) nodes, FP64",
+           "table_values": int(wl.tables.size)}
+    for name, fn in (("vjp", lambda: ctx.rhs_adjoint(pb, tabs, 1.0, g)),
+                     ("jacobian", lambda: ctx.rhs_jacobian(pb, tabs, 1.0, J=J))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1) / reps
+    return res
+
+
 def model_bench(ctx, steps: int = 5):
     """Single-RHS throughput of the other model workloads, mixed and FP64:
     d=3 (64 ext x 64 x 32 nodes), finite T (64 |p| x 9 p0, 96 x 48 x (2N+1))
@@ -611,6 +636,9 @@ def main():
                  **res}
         tf.free()
 
+    adjoint = adjoint_bench(ctx, wl, tabs)
+    adjoint["fp64_rhs_ms"] = fp64_ms
+
     serving = None
     if not args.no_serve:
         serving = serving_bench(ctx, args.serve_requests)
@@ -648,6 +676,7 @@ def main():
             "flows": flows,
             "serving": serving,
             "steppers": steppers,
+            "adjoint": adjoint,
             "models": models,
             "cpu_baseline": cpu,
         }

@@ -128,6 +128,28 @@ def test_full_jacobian_matches_oracle(ctx, name):
     assert np.max(np.abs(J - ref)) / np.max(np.abs(ref)) < 1e-12
 
 
+def test_jacobian_and_vjp_at_the_d4_bench_size(ctx):
+    """The full d=4 workload (128-point tables, 1281 external points x 128 x
+    64 x 16 nodes): the 1281 x 384 Jacobian applied to random table directions
+    against the oracle's forward-mode JVPs, and the VJP against J^T g."""
+    import torch
+    wl = fi.make_d4(seed=2)
+    k = 0.5
+    tabs = ctx.tables(wl.problem, wl.tables)
+    J = ctx.rhs_jacobian(wl.problem, tabs, k).cpu().numpy()
+    rng = np.random.default_rng(13)
+    for _ in range(2):
+        dT = rng.normal(size=wl.tables.shape)
+        _, jv = oracle.rhs_jvp(wl.problem, wl.tables, dT, k)
+        got = J @ dT.ravel()
+        assert np.max(np.abs(got - jv)) / np.max(np.abs(jv)) < 1e-12
+    gbar = rng.normal(size=wl.problem.n_ext())
+    tb = ctx.rhs_adjoint(wl.problem, tabs, k, torch.tensor(gbar, dtype=torch.float64, device="cuda")).cpu().numpy()
+    tabs.free()
+    ref = J.T @ gbar
+    assert np.max(np.abs(tb - ref)) / np.max(np.abs(ref)) < 1e-12
+
+
 def test_rosenbrock_flow_matches_oracle_ros2_and_dp45():
     """ROS2 on the device (Jacobian from the reverse-mode kernels, LU on the
     device) against the oracle's ROS2 and a tight DP5(4) reference."""
