@@ -106,6 +106,8 @@ def _load():
         lib.orc_ros2_textbook.argtypes = [I, dp, P(_StepOpts), P(_Stats)]
         lib.orc_ros2_flow.argtypes = [pp, D, dp, P(_StepOpts), P(_Stats)]
         lib.orc_d4_state_jacobian.argtypes = [pp, D, D, dp, dp]
+        lib.orc_ft_loop_factors.argtypes = [pp, dp, D, dp]
+        lib.orc_ft_states.argtypes = [pp, dp, D, I, dp, dp]
         lib.orc_abm_textbook.argtypes = [I, I, D, D, ctypes.c_long, dp, P(ctypes.c_long)]
         lib.orc_lam3_full.argtypes = [pp, dp, D, D, D]
         lib.orc_lam3_full.restype = D
@@ -310,6 +312,28 @@ def abm_flow(pb, tables, y0, Lambda: float, t1: float, n: int, order: int = 4, f
     _check(_load().orc_abm_flow(ctypes.byref(_problem(pb)), _ptr(_f64(tables)), int(feedback), Lambda, _ptr(y),
                                 t0, t1, int(n), int(order), ctypes.byref(st)), "abm_flow")
     return y, dict(steps=st.steps, rhs_evals=st.rhs_evals)
+
+
+def ft_nfreq(pb) -> int:
+    """Loop frequencies of the finite-T model: 2N+1 bosonic, 2N+2 fermionic."""
+    return 2 * pb.n_matsubara + 1 + (1 if pb.statistics else 0)
+
+
+def ft_loop_factors(pb, tables, k: float) -> np.ndarray:
+    """The model's loop-side factor dR G^2 L at (loop frequency, radial node): [nfreq][n_rad]."""
+    F = np.empty((ft_nfreq(pb), pb.n_rad))
+    _check(_load().orc_ft_loop_factors(ctypes.byref(_problem(pb)), _ptr(_f64(tables)), k, _ptr(F)),
+           "ft_loop_factors")
+    return F
+
+
+def ft_states(pb, tables, k: float, F) -> np.ndarray:
+    """Finite-T sums of many loop-side states F[s][n - n_lo][i] with the shifted line: [S][n_ext]."""
+    Fa = _f64(F).reshape(-1, ft_nfreq(pb), pb.n_rad)
+    out = np.empty((Fa.shape[0], pb.n_ext()))
+    _check(_load().orc_ft_states(ctypes.byref(_problem(pb)), _ptr(_f64(tables)), k, Fa.shape[0], _ptr(Fa),
+                                 _ptr(out)), "ft_states")
+    return out
 
 
 def d4_state_jacobian(pb, Lambda: float, t: float, y) -> np.ndarray:

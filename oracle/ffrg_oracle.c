@@ -661,6 +661,85 @@ static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *ou
 }
 
 /* ------------------------------------------------------------------ */
+/* Finite T: the sum over many loop-side states sharing the shifted line   */
+/* (the angle-integrated kernel K(p, q) of Sec. 5.3.2, contracted with     */
+/* more than one radial factor).  A state F_s is the loop-side factor      */
+/* sampled at the loop frequencies and radial nodes, F_s[n - n_lo][i]      */
+/* (n_lo = -N bosonic, -N-1 fermionic), without quadrature weights:        */
+/*   out[s][e] = pref lam^2 T/(4 pi^2) sum_n sum_i sum_j wr_i wa_j q_i^2   */
+/*               F_s[n - n_lo][i] L(n+m, s_ij) G(n+m, s_ij),               */
+/* s_ij = |q_i + p| at the angle node j, e = (p, m) as in the RHS layout.  */
+/* With F_s = dR(n, q) G(n, q)^2 L(n, q) (orc_ft_loop_factors) this is the */
+/* finite-T RHS.                                                           */
+/* ------------------------------------------------------------------ */
+int orc_ft_loop_factors(const orc_problem *pb, const double *tab, double k, double *F) {
+  int st = check_problem(pb);
+  if (st) return st;
+  if (pb->model != ORC_FINITE_T || !(k > 0.0) || !tab || !F) return ORC_EINVAL;
+  int nr = pb->n_rad, N = pb->n_matsubara, n_lo = pb->statistics ? -N - 1 : -N;
+  double *xr = malloc(sizeof(double) * nr), *wr = malloc(sizeof(double) * nr);
+  if (!xr || !wr) { free(xr); free(wr); return ORC_ENOMEM; }
+  orc_gauss_legendre(nr, 0.0, pb->qmax_over_k * k, xr, wr);
+  double k2 = k * k, m2 = m2_of(pb, k);
+  for (int n = n_lo; n <= N; ++n) {
+    double wn = matsubara(pb, n);
+    for (int i = 0; i < nr; ++i) {
+      double q = xr[i];
+      double Zq = orc_lerp_log(stack_row(tab, pb, 0, n), pb->n_pts, pb->x_min, pb->x_max, q);
+      double Lq = orc_lerp_log(stack_row(tab, pb, 1, n), pb->n_pts, pb->x_min, pb->x_max, q);
+      double dR = Zq * k2 * orc_reg_rdot(pb->regulator, q * q / k2);
+      double Gq = propagator(pb->regulator, Zq, wn * wn, q * q, m2, k);
+      F[(size_t)(n - n_lo) * nr + i] = dR * Gq * Gq * Lq;
+    }
+  }
+  free(xr); free(wr);
+  return ORC_OK;
+}
+
+int orc_ft_states(const orc_problem *pb, const double *tab, double k, int n_states, const double *F, double *out) {
+  int st = check_problem(pb);
+  if (st) return st;
+  if (pb->model != ORC_FINITE_T || !(k > 0.0) || !tab || !F || !out || n_states < 0) return ORC_EINVAL;
+  int nr = pb->n_rad, na = pb->n_ang1, N = pb->n_matsubara, nm = pb->n_ext_ang;
+  int ne = orc_n_ext(pb), n_lo = pb->statistics ? -N - 1 : -N, nfreq = N - n_lo + 1;
+  double *xr = malloc(sizeof(double) * nr), *wr = malloc(sizeof(double) * nr);
+  double *xa = malloc(sizeof(double) * na), *wa = malloc(sizeof(double) * na);
+  if (!xr || !wr || !xa || !wa) { free(xr); free(wr); free(xa); free(wa); return ORC_ENOMEM; }
+  orc_gauss_legendre(nr, 0.0, pb->qmax_over_k * k, xr, wr);
+  orc_gauss_legendre(na, -1.0, 1.0, xa, wa);
+  double norm = pb->prefactor * pb->lam * pb->lam * pb->T / (4.0 * ORC_PI * ORC_PI);
+  double m2 = m2_of(pb, k);
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+  for (int s = 0; s < n_states; ++s) {
+    for (int e = 0; e < ne; ++e) {
+      const double *Fs = F + (size_t)s * nfreq * nr;
+      int ip = e / nm, m = e % nm;
+      double p = ext_p(pb, ip);
+      acc_t acc = {0, 0};
+      for (int n = n_lo; n <= N; ++n) {
+        double wnm = matsubara(pb, n + m);
+        const double *Zrow = stack_row(tab, pb, 0, n + m), *Lrow = stack_row(tab, pb, 1, n + m);
+        for (int i = 0; i < nr; ++i) {
+          double q = xr[i];
+          for (int j = 0; j < na; ++j) {
+            double s2 = q * q + p * p + 2.0 * q * p * xa[j];
+            if (s2 < 0.0) s2 = 0.0;
+            double sv = sqrt(s2);
+            double Zs = orc_lerp_log(Zrow, pb->n_pts, pb->x_min, pb->x_max, sv);
+            double Ls = orc_lerp_log(Lrow, pb->n_pts, pb->x_min, pb->x_max, sv);
+            double Gs = propagator(pb->regulator, Zs, wnm * wnm, s2, m2, k);
+            acc_add(&acc, wr[i] * wa[j] * q * q * Fs[(size_t)(n - n_lo) * nr + i] * Ls * Gs);
+          }
+        }
+      }
+      out[(size_t)s * ne + e] = norm * acc_get(&acc);
+    }
+  }
+  free(xr); free(wr); free(xa); free(wa);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Public RHS entry points.                                               */
 /* ------------------------------------------------------------------ */
 int orc_rhs(const orc_problem *pb, const double *tables, double k, double *out) {
