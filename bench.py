@@ -386,6 +386,80 @@ def adjoint_bench(ctx, wl, tabs, reps: int = 3):
     return res
 
 
+STATES_SLICE_PAIRS = 55   # slice pairs of the FP64-faithful split (ten 5-bit slices, levels 0..9)
+
+
+def states_bench(ctx, peaks, n_states: int = 1024, reps: int = 5, check: bool = True):
+    """Finite-T sums of many loop-side states against one angle-integrated
+    kernel (ffrg_ft_states) on the finite-T workloads (576 external points, 96
+    radial x 48 angle nodes, N = 16 and 64), FP64 K: one call per step (K
+    build, slicing, the tensor-core slice-pair kernel, combination).  The
+    roofline is that of the tensor-core kernel: its algorithmic work is the
+    slice products, 55 x 2 n_ext n_states (nfreq n_rad) BF16 FLOPs, against
+    the measured BF16 peak.  Compared with n_states separate FP64 RHS calls
+    (what the RHS path alone would take), and 2 states checked against the
+    oracle (N = 16)."""
+    import numpy as np
+    import torch
+
+    import ffrg_inputs as fi
+    import paper_2412_13043_gb300 as ffrg
+    rows = []
+    bf16 = peaks.get("bf16_tflops", 1853.1)
+    for N, T in ((16, 0.0005), (64, 0.01)):
+        wl = fi.make_finite_t(seed=3, N=N, T=T)
+        pb = wl.problem
+        tabs = ctx.tables(pb, wl.tables)
+        nfreq = 2 * N + 1
+        gen = torch.Generator(device="cuda").manual_seed(N)
+        F = torch.rand(n_states, nfreq, pb.n_rad, dtype=torch.float64, device="cuda", generator=gen) + 0.5
+        out = ctx.ft_states(pb, tabs, 1.0, F)
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.ft_states(pb, tabs, 1.0, F, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        gemm_ms, cnt = ctx.profile_read()
+        ctx.set_profiling(False)
+        total_ms = e0.elapsed_time(e1) / reps
+        gemm_ms /= max(cnt, 1)
+        r64 = torch.empty(pb.n_ext(), dtype=torch.float64, device="cuda")
+        ctx.rhs(pb, tabs, 1.0, out=r64, precision=ffrg.FP64)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            ctx.rhs(pb, tabs, 1.0, out=r64, precision=ffrg.FP64)
+        e1.record()
+        torch.cuda.synchronize()
+        rhs64_ms = e0.elapsed_time(e1) / 3
+        kdim = nfreq * pb.n_rad
+        slice_flops = STATES_SLICE_PAIRS * 2.0 * pb.n_ext() * n_states * kdim
+        achieved = slice_flops / (gemm_ms * 1e-3) / 1e12
+        row = {"workload": f"finite T N={N}: {pb.n_ext()} ext x {nfreq} freq x {pb.n_rad} radial, "
+                           f"{n_states} states, FP64 K", "n_states": n_states, "terms_per_state": kdim,
+               "call_ms": total_ms, "tensor_kernel_ms": gemm_ms,
+               "fp64_equivalent_tflops": 2.0 * pb.n_ext() * n_states * kdim / (total_ms * 1e-3) / 1e12,
+               "roofline": {"bound": "tensor", "kernel": "slice_pair_gemm (tcgen05 kind::f16, BF16 slices, "
+                                                          "FP32 accumulators in tensor memory)",
+                            "achieved": achieved, "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16,
+                            "work": "55 slice pairs x 2 n_ext n_states nfreq n_rad",
+                            "peak_source": "bf16_tflops of measured (burst)"},
+               "one_state_at_a_time_fp64_rhs_ms": rhs64_ms * n_states,
+               "speedup_over_fp64_rhs_per_state": rhs64_ms * n_states / total_ms}
+        if check and N == 16:
+            import oracle
+            sel = [0, n_states - 1]
+            ref = oracle.ft_states(pb, wl.tables, 1.0, F[sel].cpu().numpy())
+            got = out[sel].cpu().numpy()
+            row["max_rel_err_vs_oracle_2_states"] = float(np.max(np.abs(got - ref) / np.abs(ref)))
+        rows.append(row)
+        tabs.free()
+    return rows
+
+
 def model_bench(ctx, steps: int = 5):
     """Single-RHS throughput of the other model workloads, mixed and FP64:
     d=3 (64 ext x 64 x 32 nodes), finite T (64 |p| x 9 p0, 96 x 48 x (2N+1))
@@ -638,6 +712,9 @@ def main():
 
     adjoint = adjoint_bench(ctx, wl, tabs)
     adjoint["fp64_rhs_ms"] = fp64_ms
+    states = None
+    if not args.no_models:
+        states = states_bench(ctx, measured_peaks(), check=(rank == 0 and not args.no_cpu))
 
     serving = None
     if not args.no_serve:
@@ -677,12 +754,15 @@ def main():
             "serving": serving,
             "steppers": steppers,
             "adjoint": adjoint,
+            "states": states,
             "models": models,
             "cpu_baseline": cpu,
         }
         # last key of the line, so that a truncated tail of the output still shows it
         summ = {"fp64_d4_evals_per_s": line["fp64_path"]["value"],
                 "mixed_over_fp64_d4": line["fp64_path"]["speedup_mixed_over_fp64"]}
+        if states:
+            summ["states_tensor_frac"] = {r["workload"].split(":")[0]: r["roofline"]["frac"] for r in states}
         if serving:
             summ.update({k: serving[k] for k in (
                 "served_flows_per_s", "fp64_one_at_a_time_flows_per_s", "speedup_served_over_fp64",

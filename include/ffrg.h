@@ -237,6 +237,31 @@ FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *
 FFRG_API int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *desc, const double *tables_dev, double k,
                               double *out_dev, int precision, void *stream);
 
+/* Finite-T sums of many loop-side states against one angle-integrated
+ * kernel (Sec. 5.3.2 momentum integrals).  The finite-T RHS is a sum over the
+ * loop frequencies n and radial nodes q_r of a loop-side factor F(n, q_r)
+ * (for the model: dR G^2 lam at (omega_n, q_r)) times the angular sum of
+ * the shifted line, K[j(n+m)][p][r] = sum_c v_c lam G(n+m, |q_r + p|).  For
+ * n_states states F_s sharing the tables, this call builds K once and returns
+ *   out_dev[s * n_ext + e] = norm sum_{n, r} w_r q_r^2 F_s(n, r) K[j(n+m)][p][r]
+ * with e = (p, m) as in ffrg_rhs, norm = prefactor lam^2 T / (4 pi^2) and the
+ * radial rule (w_r, q_r) of the problem; with F_s = the model's factor it is
+ * ffrg_rhs.  F_dev: device, n_states x nfreq x n_rad doubles, row n - n_lo
+ * (n_lo = -N bosonic, -N-1 fermionic; nfreq = 2N+1 or 2N+2), the values at
+ * the nodes without quadrature weights.  out_dev: device, n_states x n_ext
+ * doubles.  precision: the arithmetic of K (FFRG_FP64 or FFRG_MIXED as for
+ * ffrg_rhs); the contraction over (n, r) runs on the tensor cores and is
+ * FP64-faithful in both: an Ozaki-type split of K and of the states into ten
+ * 5-bit fixed-point slices carried in BF16, slice products summed exactly in
+ * FP32 over at most 16384 (n, r) terms per pass, passes combined in FP64
+ * (error below ~1e-14 of the sum of the terms' magnitudes).  Scratch is kept
+ * by the context (slices of both operands and the exact pass sums:
+ * about 20 (n_ext + n_states) nfreq n_rad + 220 n_ext n_states bytes).
+ * Asynchronous.  FFRG_EINVAL for models other than FFRG_MODEL_FINITE_T and
+ * for more than 196608 (loop frequency, radial node) terms. */
+FFRG_API int ffrg_ft_states(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, int n_states,
+                            const double *F_dev, double *out_dev, int precision, void *stream);
+
 /* Vector-Jacobian product of ffrg_rhs with respect to the table values
  * (the paper forms Jacobians by forward-mode AD, Sec. 5.2.2; this is the
  * reverse-mode counterpart): tbar_dev[j] = sum_e gbar_dev[e] d out_e / d T_j,

@@ -96,6 +96,7 @@ _SIGS = {
     "ffrg_rhs": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _I, _P]),
     "ffrg_rhs_noalloc": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(TableDesc), _P, _D, _P, _I, _P]),
     "ffrg_rhs_adjoint": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P, _I, _P]),
+    "ffrg_ft_states": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _I, _P, _P, _I, _P]),
     "ffrg_flow": (_I, [_P, ctypes.POINTER(Problem), _P, _I, _D, _P, ctypes.POINTER(StepOpts), _I,
                        ctypes.POINTER(FlowStats), _P]),
     "ffrg_rhs_jacobian": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P]),
@@ -318,6 +319,20 @@ class Context:
                                        _stream_handle(stream))
         _check(self.handle, code, "ffrg_rhs_adjoint")
         return tbar
+
+    def ft_states(self, pb, tables: Tables, k: float, F, out=None, precision: int = FP64, stream=None):
+        """Finite-T sums of the loop-side states F (CUDA float64 [S, nfreq, n_rad]) against the
+        angle-integrated kernel of `tables`: a CUDA float64 tensor [S, n_ext]."""
+        import torch
+        c = to_problem(pb)
+        n_states = int(F.shape[0])
+        if out is None:
+            out = torch.empty(n_states, load().ffrg_n_ext(ctypes.byref(c)), dtype=torch.float64,
+                              device=f"cuda:{self.device}")
+        code = load().ffrg_ft_states(self.handle, ctypes.byref(c), tables.handle, float(k), n_states,
+                                     _dev_ptr(F, "F"), _dev_ptr(out, "out"), int(precision), _stream_handle(stream))
+        _check(self.handle, code, "ffrg_ft_states")
+        return out
 
     def flow(self, pb, tables: Tables, state, Lambda: float, t1: float, feedback: int = 0, precision: int = FP64,
              t0: float = 0.0, dt0: float = 1e-3, dt_min: float = 1e-10, dt_max: float = 0.5, atol: float = 1e-14,

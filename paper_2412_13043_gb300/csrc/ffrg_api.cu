@@ -498,6 +498,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
   for (void *p : ctx->owned) cudaFree(p);
   for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
   if (ctx->flow_dev) cudaFree(ctx->flow_dev);
+  if (ctx->states_dev) cudaFree(ctx->states_dev);
   if (ctx->flow_host) cudaFreeHost(ctx->flow_host);
   if (ctx->flow_ev) cudaEventDestroy(ctx->flow_ev);
   if (ctx->flow_stream) cudaStreamDestroy(ctx->flow_stream);

@@ -424,6 +424,10 @@ struct ffrg_ctx {
   void *flow_host = nullptr;
   cudaStream_t flow_stream = nullptr;
   cudaEvent_t flow_ev = nullptr;
+  // ffrg_ft_states scratch (operand slices, exact pass sums, scales), grown on demand
+  void *states_dev = nullptr;
+  size_t states_cap = 0;
+  int states_chunks = 0;  // K ranges whose pass table the scratch holds (0: none)
 };
 
 namespace ffrg {
@@ -532,6 +536,10 @@ int host_gauss_chebyshev2(int n, double *x, double *w);
 
 // kernels launched from several translation units (ffrg_rhs.cu)
 int launch_rhs(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s);
+// launch_rhs with the finite-T contraction optional: contract = false stops
+// after the angle-integrated kernel K (plan kbuf, in the kernel precision)
+int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s,
+                      bool contract);
 int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s);
 // blocks of the precompute kernel for one RHS (at most cap)
 int precompute_blocks(const RhsArgs &a, int cap);

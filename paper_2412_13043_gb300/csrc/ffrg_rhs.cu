@@ -1143,6 +1143,11 @@ int launch_precompute(ffrg_ctx *ctx, const RhsArgs &a, cudaStream_t s) {
 }
 
 int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precision, cudaStream_t s) {
+  return launch_rhs_stages(ctx, pl_c, a_in, precision, s, true);
+}
+
+int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precision, cudaStream_t s,
+                      bool contract) {
   Plan *pl = const_cast<Plan *>(pl_c);
   const bool mixed = precision == FFRG_MIXED;
   RhsArgs a = a_in;  // forward geometry of this precision
@@ -1192,7 +1197,7 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
   }
   // d=3, d=4: the main kernel writes the outputs (last warp per external
   // point); finite T: the contraction of K with the radial factors
-  if (a.model == FFRG_MODEL_FINITE_T) {
+  if (a.model == FFRG_MODEL_FINITE_T && contract) {
     if (mixed) ft_contract_kernel<float><<<a.n_ext, kThreads, 0, s>>>(a);
     else ft_contract_kernel<double><<<a.n_ext, kThreads, 0, s>>>(a);
   }
