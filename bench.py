@@ -51,6 +51,12 @@ SFU_PER_CLK_SM = 16      # log2 / reciprocal results per clock per SM
 # (dram__bytes_read.sum + dram__bytes_write.sum: 79.6 KB + 0 B)
 D4_MAIN_DRAM_BYTES = 79616
 FP32_PER_CLK_SM = 128    # FP32 FMA lanes per SM
+# FP64-pipe thread instructions per integrand term of rhs_main<2, double> (the
+# plain FP64 path), from an ncu capture of the d=4 workload with 16 external
+# momenta: pipe_fp64 86.1 % of 1.077e7 active cycles x 2 per cycle x 152 SMs
+# over 2.11e7 terms
+FP64_OPS_PER_TERM_D4 = 134
+FP64_PER_CLK_SM = 2      # FP64 (DFMA) results per clock per SM on this part
 
 
 def parse():
@@ -741,7 +747,11 @@ def main():
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{world}"},
             "wall_s_timed_region": wall,
             "fp64_path": {"value": evals / (fp64_ms / 1e3), "unit": "integrand evals/s", "ms_per_step": fp64_ms,
-                          "speedup_mixed_over_fp64": (value / world) / (evals / (fp64_ms / 1e3))},
+                          "speedup_mixed_over_fp64": (value / world) / (evals / (fp64_ms / 1e3)),
+                          "fp64_pipe_frac": evals / (fp64_ms / 1e3) * FP64_OPS_PER_TERM_D4
+                          / (FP64_PER_CLK_SM * n_sm * sm_mhz * 1e6),
+                          "fp64_pipe_frac_basis": f"{FP64_OPS_PER_TERM_D4} FP64-pipe ops per term (ncu) x terms/s "
+                                                  f"/ ({FP64_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz)"},
             "mixed_vs_fp64_max_rel_err": mixed_err,
             "e2e": {"value": e2e_val, "unit": "integrand evals/s",
                     "h2d_bytes_per_step": int(wl.tables.size * 8), "d2h_bytes_per_step": int(pb.n_ext() * 8)},
@@ -760,6 +770,7 @@ def main():
         }
         # last key of the line, so that a truncated tail of the output still shows it
         summ = {"fp64_d4_evals_per_s": line["fp64_path"]["value"],
+                "fp64_d4_pipe_frac": line["fp64_path"]["fp64_pipe_frac"],
                 "mixed_over_fp64_d4": line["fp64_path"]["speedup_mixed_over_fp64"]}
         if states:
             summ["states_tensor_frac"] = {r["workload"].split(":")[0]: r["roofline"]["frac"] for r in states}
