@@ -31,6 +31,7 @@ MODEL_D3 = 1          # d=3, T=0 scalar two-point flow
 MODEL_D4_VERTEX = 2   # d=4, three coupled dressing tables (Z, lambda3, lambda4)
 MODEL_FINITE_T = 3    # d=3 spatial + Matsubara sum (bosonic or fermionic loop)
 MODEL_D4_FULL = 4     # d=4 with the three-point vertex on (S0, two shape variables)
+MODEL_FINITE_T_4D = 5  # finite T with a 4D regulator on a k-scaled frequency domain
 
 REG_EXP = 0
 REG_LITIM = 1
@@ -88,13 +89,15 @@ class Problem:
     # D4_FULL: three-point vertex nodes in its two shape variables (n_stack = n_va n_vb)
     n_va: int = 1
     n_vb: int = 1
+    # FINITE_T_4D: Gauss-Legendre nodes of the frequency integral beyond the Matsubara cap
+    n_x0: int = 0
 
     def n_ext(self) -> int:
         if self.model == MODEL_D3:
             return self.n_ext_p + (1 if self.include_p0 else 0)
         if self.model in (MODEL_D4_VERTEX, MODEL_D4_FULL):
             return 2 * self.n_ext_p + 1 + self.n_ext_p * self.n_ext_ang
-        if self.model == MODEL_FINITE_T:
+        if self.model in (MODEL_FINITE_T, MODEL_FINITE_T_4D):
             return self.n_ext_p * self.n_ext_ang
         raise ValueError(self.model)
 
@@ -104,6 +107,8 @@ class Problem:
             n *= self.n_ang2
         if self.model == MODEL_FINITE_T:
             n *= 2 * self.n_matsubara + 1 + (1 if self.statistics == STAT_FERMI else 0)
+        if self.model == MODEL_FINITE_T_4D:   # at most: the Matsubara cap or the quadrature nodes
+            n *= max(2 * self.n_matsubara + 1 + (1 if self.statistics == STAT_FERMI else 0), self.n_x0)
         return n
 
     def evals(self) -> int:
@@ -248,6 +253,34 @@ def make_finite_t(seed: int = 3, N: int = 16, T: float = 0.002, n_pts: int = 64,
     om2_ext = (2.0 * math.pi * T * np.arange(n_ext_m, dtype=np.float64)) ** 2
     y0 = (_bump(ps[:, None] ** 2 + om2_ext[None, :], a, b) * (ps[:, None] ** 2 + om2_ext[None, :])
           + m2_uv).reshape(-1)
+    return Workload(pb, tables, y0, Lambda, k_end, 0, seed, dict(a=a, b=b, g=g, c=c, bl=bl))
+
+
+def make_finite_t_4d(seed: int = 12, N: int = 16, T: float = 0.05, n_pts: int = 64, n_ext_p: int = 64,
+                     n_ext_m: int = 9, n_rad: int = 96, n_ang: int = 48, n_x0: int = 64, Lambda: float = 10.0,
+                     k_end: float = 0.01, regulator: int = REG_EXP, fermionic: bool = False) -> Workload:
+    """Finite T with a 4D regulator on a k-scaled frequency domain: dressings Z(|Q|) and lam(|Q|) on one
+    log grid in the 4-momentum magnitude; Matsubara cap N (sum while at most 2N+1 (+1) loop frequencies
+    lie in |q0| <= qmax k, else n_x0 Gauss-Legendre nodes); fermionic: loop nu_n and the external
+    fermion leg at p0f (n_ext_m must be 1)."""
+    rng = SplitMix64(seed)
+    a = rng.uniform(0.0, 0.2)
+    b = rng.uniform(0.5, 2.0)
+    g = rng.uniform(0.5, 1.5)
+    c = rng.uniform(-0.3, 0.3)
+    bl = rng.uniform(0.5, 2.0)
+    if fermionic:
+        n_ext_m = 1
+    pb = Problem(model=MODEL_FINITE_T_4D, n_rad=n_rad, n_ang1=n_ang, n_ext_p=n_ext_p, n_ext_ang=n_ext_m,
+                 n_matsubara=N, regulator=regulator, m2_over_k2=0.5, T=T, n_tables=2, n_pts=n_pts, n_stack=1,
+                 statistics=STAT_FERMI if fermionic else STAT_BOSE, n_x0=n_x0)
+    xs = log_grid(n_pts, pb.x_min, pb.x_max)
+    x2 = xs ** 2
+    tables = np.stack([_bump(x2, a, b), g * _bump(x2, c, bl)]).reshape(2, 1, n_pts)
+    ps = log_grid(n_ext_p, pb.p_min, pb.p_max)
+    om2_ext = (2.0 * math.pi * T * np.arange(n_ext_m, dtype=np.float64)) ** 2
+    P2 = ps[:, None] ** 2 + om2_ext[None, :]
+    y0 = (_bump(P2, a, b) * P2 + 0.5 * Lambda ** 2).reshape(-1)
     return Workload(pb, tables, y0, Lambda, k_end, 0, seed, dict(a=a, b=b, g=g, c=c, bl=bl))
 
 

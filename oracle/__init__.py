@@ -44,7 +44,7 @@ class _Problem(ctypes.Structure):
         ("n_ext_p", ctypes.c_int), ("n_ext_ang", ctypes.c_int), ("n_matsubara", ctypes.c_int),
         ("include_p0", ctypes.c_int),
         ("n_tables", ctypes.c_int), ("n_pts", ctypes.c_int), ("n_stack", ctypes.c_int),
-        ("statistics", ctypes.c_int), ("n_va", ctypes.c_int), ("n_vb", ctypes.c_int),
+        ("statistics", ctypes.c_int), ("n_va", ctypes.c_int), ("n_vb", ctypes.c_int), ("n_x0", ctypes.c_int),
         ("m2_over_k2", ctypes.c_double), ("m2_shift", ctypes.c_double), ("lam", ctypes.c_double),
         ("T", ctypes.c_double), ("p_min", ctypes.c_double), ("p_max", ctypes.c_double),
         ("qmax_over_k", ctypes.c_double), ("prefactor", ctypes.c_double),
@@ -108,6 +108,9 @@ def _load():
         lib.orc_d4_state_jacobian.argtypes = [pp, D, D, dp, dp]
         lib.orc_ft_loop_factors.argtypes = [pp, dp, D, dp]
         lib.orc_ft_states.argtypes = [pp, dp, D, I, dp, dp]
+        lib.orc_ft4_frequencies.argtypes = [pp, D, dp, dp]
+        lib.orc_ft4_external_frequency.argtypes = [pp, D, I]
+        lib.orc_ft4_external_frequency.restype = D
         lib.orc_abm_textbook.argtypes = [I, I, D, D, ctypes.c_long, dp, P(ctypes.c_long)]
         lib.orc_lam3_full.argtypes = [pp, dp, D, D, D]
         lib.orc_lam3_full.restype = D
@@ -317,6 +320,18 @@ def abm_flow(pb, tables, y0, Lambda: float, t1: float, n: int, order: int = 4, f
 def ft_nfreq(pb) -> int:
     """Loop frequencies of the finite-T model: 2N+1 bosonic, 2N+2 fermionic."""
     return 2 * pb.n_matsubara + 1 + (1 if pb.statistics else 0)
+
+
+def ft4_frequencies(pb, k: float):
+    """Loop frequencies and their weights of the 4D-regulator finite-T model at scale k."""
+    n = 2 * pb.n_matsubara + 2 + pb.n_x0
+    w, wt = np.empty(n), np.empty(n)
+    nf = _load().orc_ft4_frequencies(ctypes.byref(_problem(pb)), k, _ptr(w), _ptr(wt))
+    return w[:nf], wt[:nf]
+
+
+def ft4_external_frequency(pb, k: float, m: int) -> float:
+    return _load().orc_ft4_external_frequency(ctypes.byref(_problem(pb)), k, int(m))
 
 
 def ft_loop_factors(pb, tables, k: float) -> np.ndarray:

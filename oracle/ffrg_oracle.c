@@ -54,6 +54,7 @@
 #define ORC_D4_VERTEX 2
 #define ORC_FINITE_T 3
 #define ORC_D4_FULL 4
+#define ORC_FINITE_T_4D 5
 
 #define ORC_REG_EXP 0
 #define ORC_REG_LITIM 1
@@ -68,6 +69,7 @@ typedef struct {
   int n_tables, n_pts, n_stack;
   int statistics; /* finite T: 0 bosonic loop frequencies, 1 fermionic */
   int n_va, n_vb; /* D4_FULL: nodes of the three-point vertex in its two shape variables */
+  int n_x0;       /* FINITE_T_4D: Gauss-Legendre nodes of the frequency quadrature */
   double m2_over_k2, m2_shift, lam, T;
   double p_min, p_max, qmax_over_k, prefactor;
   double x_min, x_max;
@@ -263,14 +265,19 @@ int orc_n_ext(const orc_problem *pb) {
   case ORC_D3: return pb->n_ext_p + (pb->include_p0 ? 1 : 0);
   case ORC_D4_VERTEX:
   case ORC_D4_FULL: return 2 * pb->n_ext_p + 1 + pb->n_ext_p * pb->n_ext_ang;
-  case ORC_FINITE_T: return pb->n_ext_p * pb->n_ext_ang;
+  case ORC_FINITE_T:
+  case ORC_FINITE_T_4D: return pb->n_ext_p * pb->n_ext_ang;
   default: return -1;
   }
 }
 
 static int check_problem(const orc_problem *pb) {
   if (!pb) return ORC_EINVAL;
-  if (pb->model < ORC_D3 || pb->model > ORC_D4_FULL) return ORC_EINVAL;
+  if (pb->model < ORC_D3 || pb->model > ORC_FINITE_T_4D) return ORC_EINVAL;
+  if (pb->model == ORC_FINITE_T_4D &&
+      (pb->n_ext_ang < 1 || pb->n_matsubara < 0 || pb->n_tables < 2 || pb->n_stack != 1 || pb->n_x0 < 1 ||
+       !(pb->T > 0.0) || (pb->statistics == 1 && pb->n_ext_ang != 1)))
+    return ORC_EINVAL;
   if (pb->model == ORC_D4_FULL && (pb->n_va < 1 || pb->n_vb < 1 || pb->n_stack != pb->n_va * pb->n_vb ||
                                    pb->n_ang2 < 1 || pb->n_ext_ang < 1 || pb->n_tables < 3))
     return ORC_EINVAL;
@@ -279,7 +286,8 @@ static int check_problem(const orc_problem *pb) {
   if (pb->model == ORC_FINITE_T && (pb->n_ext_ang < 1 || pb->n_matsubara < 0 || pb->n_tables < 2 || pb->n_stack < 1))
     return ORC_EINVAL;
   if (pb->model == ORC_D3 && pb->n_tables < 1) return ORC_EINVAL;
-  if (pb->statistics != 0 && (pb->statistics != 1 || pb->model != ORC_FINITE_T)) return ORC_EINVAL;
+  if (pb->statistics != 0 && (pb->statistics != 1 || (pb->model != ORC_FINITE_T && pb->model != ORC_FINITE_T_4D)))
+    return ORC_EINVAL;
   if (!(pb->x_min > 0.0) || !(pb->x_max > pb->x_min) || !(pb->p_min > 0.0)) return ORC_EINVAL;
   return ORC_OK;
 }
@@ -661,6 +669,114 @@ static int rhs_ft(const orc_problem *pb, const double *tab, double k, double *ou
 }
 
 /* ------------------------------------------------------------------ */
+/* Model finite T with a 4-dimensional regulator on a k-scaled frequency    */
+/* domain (Sec. 5.3.2: "Quadraturex0" integrators treat the time direction */
+/* as a Matsubara sum over a domain that scales with k, efficient with     */
+/* 4-dimensional regulators; App. G: external fermion legs at             */
+/* p0f = pi T exp(-k/(pi T))).  With Q = (q0, q), P = (p0, p):              */
+/*   I(m,p) = pref lam^2 [T sum_n | int dq0/2pi] int d^3q/(2pi)^3          */
+/*            dR(Q) G(Q)^2 L(|Q|) L(|Q+P|) G(Q+P),                         */
+/* R(Q) = Z(|Q|) k^2 r(|Q|^2/k^2) (4D), G(Q) = 1/(Z(|Q|) |Q|^2 + m^2 + R),  */
+/* dressings Z and L on one log grid in |Q|.  Frequency domain |q0| <=      */
+/* L0 = qmax_over_k k.  Loop frequencies in the domain: bosonic 2 pi T n,   */
+/* |n| <= floor(L0/(2 pi T)); fermionic (2n+1) pi T, -N_k-1 <= n <= N_k,    */
+/* N_k = floor((L0/(pi T) - 1)/2) (none if L0 < pi T).  While their number */
+/* is at most the cap 2 n_matsubara + 1 (+1 fermionic) the frequency       */
+/* integral is that Matsubara sum with weight T; beyond it, the T -> 0     */
+/* form: Gauss-Legendre with n_x0 nodes on [-L0, L0], weights w/(2 pi).    */
+/* External frequency p0: bosonic 2 pi T m; fermionic (n_ext_ang = 1) the  */
+/* external fermion leg's p0f = pi T exp(-k/(pi T)).                        */
+/* ------------------------------------------------------------------ */
+int orc_ft4_frequencies(const orc_problem *pb, double k, double *w, double *wt) {
+  double L0 = pb->qmax_over_k * k, T = pb->T;
+  int cap = 2 * pb->n_matsubara + 1 + (pb->statistics ? 1 : 0);
+  int count;
+  if (pb->statistics) {
+    double x = L0 / (ORC_PI * T);
+    int Nk = x < 1.0 ? -1 : (int)floor((x - 1.0) / 2.0);
+    count = 2 * Nk + 2;
+    if (count <= cap) {
+      for (int n = -Nk - 1; n <= Nk; ++n) {
+        w[n + Nk + 1] = (2.0 * n + 1.0) * ORC_PI * T;
+        wt[n + Nk + 1] = T;
+      }
+      return count;
+    }
+  } else {
+    int Nk = (int)floor(L0 / (2.0 * ORC_PI * T));
+    count = 2 * Nk + 1;
+    if (count <= cap) {
+      for (int n = -Nk; n <= Nk; ++n) {
+        w[n + Nk] = 2.0 * ORC_PI * T * n;
+        wt[n + Nk] = T;
+      }
+      return count;
+    }
+  }
+  orc_gauss_legendre(pb->n_x0, -L0, L0, w, wt);
+  for (int i = 0; i < pb->n_x0; ++i) wt[i] /= 2.0 * ORC_PI;
+  return pb->n_x0;
+}
+
+double orc_ft4_external_frequency(const orc_problem *pb, double k, int m) {
+  if (pb->statistics) return ORC_PI * pb->T * exp(-k / (ORC_PI * pb->T));
+  return 2.0 * ORC_PI * pb->T * m;
+}
+
+double orc_ft4_summand(const orc_problem *pb, const double *tab, double k, double Q2, double QP2) {
+  int np = pb->n_pts, reg = pb->regulator;
+  double k2 = k * k, m2 = m2_of(pb, k);
+  if (QP2 < 0.0) QP2 = 0.0;
+  const double *Zt = tab, *Lt = tab + np;
+  double Zq = orc_lerp_log(Zt, np, pb->x_min, pb->x_max, sqrt(Q2));
+  double Lq = orc_lerp_log(Lt, np, pb->x_min, pb->x_max, sqrt(Q2));
+  double Zs = orc_lerp_log(Zt, np, pb->x_min, pb->x_max, sqrt(QP2));
+  double Ls = orc_lerp_log(Lt, np, pb->x_min, pb->x_max, sqrt(QP2));
+  double dR = Zq * k2 * orc_reg_rdot(reg, Q2 / k2);
+  double Gq = propagator(reg, Zq, 0.0, Q2, m2, k);
+  double Gs = propagator(reg, Zs, 0.0, QP2, m2, k);
+  return dR * Gq * Gq * Lq * Ls * Gs;
+}
+
+static int rhs_ft4(const orc_problem *pb, const double *tab, double k, double *out, const int *sel, int nsel) {
+  int nr = pb->n_rad, na = pb->n_ang1, nm = pb->n_ext_ang;
+  int ne = orc_n_ext(pb), nmax = 2 * pb->n_matsubara + 2 + pb->n_x0;
+  double *xr = malloc(sizeof(double) * nr), *wr = malloc(sizeof(double) * nr);
+  double *xa = malloc(sizeof(double) * na), *wa = malloc(sizeof(double) * na);
+  double *wf = malloc(sizeof(double) * nmax), *wtf = malloc(sizeof(double) * nmax);
+  if (!xr || !wr || !xa || !wa || !wf || !wtf) {
+    free(xr); free(wr); free(xa); free(wa); free(wf); free(wtf);
+    return ORC_ENOMEM;
+  }
+  orc_gauss_legendre(nr, 0.0, pb->qmax_over_k * k, xr, wr);
+  orc_gauss_legendre(na, -1.0, 1.0, xa, wa);
+  int nf = orc_ft4_frequencies(pb, k, wf, wtf);
+  double norm = pb->prefactor * pb->lam * pb->lam / (4.0 * ORC_PI * ORC_PI);
+  int nloop = sel ? nsel : ne;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int ie = 0; ie < nloop; ++ie) {
+    int e = sel ? sel[ie] : ie;
+    int ip = e / nm, m = e % nm;
+    double p = ext_p(pb, ip), p0 = orc_ft4_external_frequency(pb, k, m);
+    acc_t acc = {0, 0};
+    for (int f = 0; f < nf; ++f) {
+      for (int i = 0; i < nr; ++i) {
+        double q = xr[i];
+        double Q2 = wf[f] * wf[f] + q * q;
+        for (int j = 0; j < na; ++j) {
+          double s2 = q * q + p * p + 2.0 * q * p * xa[j];
+          double QP2 = (wf[f] + p0) * (wf[f] + p0) + s2;
+          acc_add(&acc, wtf[f] * wr[i] * wa[j] * q * q * orc_ft4_summand(pb, tab, k, Q2, QP2));
+        }
+      }
+    }
+    out[ie] = norm * acc_get(&acc);
+  }
+  free(xr); free(wr); free(xa); free(wa); free(wf); free(wtf);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
 /* Finite T: the sum over many loop-side states sharing the shifted line   */
 /* (the angle-integrated kernel K(p, q) of Sec. 5.3.2, contracted with     */
 /* more than one radial factor).  A state F_s is the loop-side factor      */
@@ -751,6 +867,7 @@ int orc_rhs(const orc_problem *pb, const double *tables, double k, double *out) 
   case ORC_D4_VERTEX:
   case ORC_D4_FULL: return rhs_d4(pb, tables, NULL, k, out, NULL, NULL, 0);
   case ORC_FINITE_T: return rhs_ft(pb, tables, k, out, NULL, 0);
+  case ORC_FINITE_T_4D: return rhs_ft4(pb, tables, k, out, NULL, 0);
   }
   return ORC_EINVAL;
 }
@@ -769,6 +886,7 @@ int orc_rhs_subset(const orc_problem *pb, const double *tables, double k, const 
   case ORC_D4_VERTEX:
   case ORC_D4_FULL: return rhs_d4(pb, tables, NULL, k, out, NULL, sel, nsel);
   case ORC_FINITE_T: return rhs_ft(pb, tables, k, out, sel, nsel);
+  case ORC_FINITE_T_4D: return rhs_ft4(pb, tables, k, out, sel, nsel);
   }
   return ORC_EINVAL;
 }
