@@ -466,6 +466,45 @@ def states_bench(ctx, peaks, n_states: int = 1024, reps: int = 5, check: bool = 
     return rows
 
 
+def ft4_rows(ctx, name, wl, steps):
+    """The 4D-regulator finite-T model at k = 1 (Matsubara sum) and k = 10
+    (frequency quadrature): terms = external points x frequencies in use x
+    radial x angle nodes."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2412_13043_gb300 as ffrg
+    pb = wl.problem
+    tabs = ctx.tables(pb, wl.tables)
+    rows = []
+    for k in (1.0, 10.0):
+        nf = oracle.ft4_frequencies(pb, k)[0].size
+        terms = pb.n_ext() * nf * pb.n_rad * pb.n_ang1
+        row = {"workload": f"{name}, k = {k:g} ({'Matsubara sum' if nf <= 2 * pb.n_matsubara + 1 else 'quadrature'}"
+                           f", {nf} frequencies)", "evals_per_rhs": terms}
+        outs = {}
+        for pname, prec in (("mixed", ffrg.MIXED), ("fp64", ffrg.FP64)):
+            out = torch.empty(pb.n_ext(), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                ctx.rhs(pb, tabs, k, out=out, precision=prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                ctx.rhs(pb, tabs, k, out=out, precision=prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            row[pname] = {"step_ms": ms, "evals_per_s": terms / (ms * 1e-3)}
+            outs[pname] = out.cpu().numpy()
+        row["mixed_vs_fp64_max_rel_err"] = float(np.max(np.abs(outs["mixed"] - outs["fp64"]) / np.abs(outs["fp64"])))
+        row["speedup_mixed_over_fp64"] = row["fp64"]["step_ms"] / row["mixed"]["step_ms"]
+        rows.append(row)
+    tabs.free()
+    return rows
+
+
 def model_bench(ctx, steps: int = 5):
     """Single-RHS throughput of the other model workloads, mixed and FP64:
     d=3 (64 ext x 64 x 32 nodes), finite T (64 |p| x 9 p0, 96 x 48 x (2N+1))
@@ -485,9 +524,16 @@ def model_bench(ctx, steps: int = 5):
                   fi.make_d4_full()))
     cases.append(("finite T fermionic N=16, T/k_end=0.05",
                   fi.make_finite_t(seed=3, N=16, T=0.05 * 0.01, fermionic=True)))
+    # 4D regulator, k-scaled frequency domain: the Matsubara sum (25 frequencies) at k = 1
+    # and the 64-node frequency quadrature at k = 10
+    cases.append(("finite T, 4D regulator (Quadraturex0), 64 |p| x 9 p0, 96 x 48 nodes, T = 0.05",
+                  fi.make_finite_t_4d()))
     rows = []
     for name, wl in cases:
         pb = wl.problem
+        if pb.model == fi.MODEL_FINITE_T_4D:
+            rows.extend(ft4_rows(ctx, name, wl, steps))
+            continue
         tabs = ctx.tables(pb, wl.tables)
         # finite T evaluates the angular sums once per (stack row, |p|, radial node)
         # through K(p, q): the terms of the discrete sum (evals_per_rhs, the metric's

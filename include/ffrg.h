@@ -79,7 +79,13 @@ typedef enum {
 
 typedef enum { FFRG_FP64 = 0, FFRG_MIXED = 1 } ffrg_precision;
 typedef enum { FFRG_RULE_GL = 0, FFRG_RULE_GC2 = 1 } ffrg_rule;
-typedef enum { FFRG_MODEL_D3 = 1, FFRG_MODEL_D4_VERTEX = 2, FFRG_MODEL_FINITE_T = 3, FFRG_MODEL_D4_FULL = 4 } ffrg_model;
+typedef enum {
+  FFRG_MODEL_D3 = 1,
+  FFRG_MODEL_D4_VERTEX = 2,
+  FFRG_MODEL_FINITE_T = 3,
+  FFRG_MODEL_D4_FULL = 4,
+  FFRG_MODEL_FINITE_T_4D = 5
+} ffrg_model;
 typedef enum { FFRG_REG_EXP = 0, FFRG_REG_LITIM = 1 } ffrg_regulator;
 typedef enum { FFRG_STAT_BOSE = 0, FFRG_STAT_FERMI = 1 } ffrg_statistics;
 
@@ -108,7 +114,23 @@ typedef enum { FFRG_STAT_BOSE = 0, FFRG_STAT_FERMI = 1 } ffrg_statistics;
  *             (2N+2 terms), tables stacked over j = n (n >= 0) or -n-1, row j
  *             at nu_j = (2j+1) pi T (App. F bosonic / fermionic finite-T
  *             coordinate stacks).  The shifted line carries frequency n+m.
- *             Stack indices beyond n_stack-1 are clamped to it. */
+ *             Stack indices beyond n_stack-1 are clamped to it.
+ *   FINITE_T_4D: [p_i][m] as FINITE_T; finite T with a 4-dimensional
+ *             regulator on a frequency domain that scales with k (Sec. 5.3.2
+ *             "Quadraturex0"): with Q = (q0, q), P = (p0, p),
+ *               I = pref lam^2 [T sum_n | int dq0/(2 pi)] int d^3q/(2pi)^3
+ *                   dR(Q) G(Q)^2 L(|Q|) L(|Q+P|) G(Q+P),
+ *             R(Q) = Z(|Q|) k^2 r(|Q|^2/k^2), G(Q) = 1/(Z(|Q|)|Q|^2 + m^2
+ *             + R(Q)); tables Z and L (n_tables = 2, n_stack = 1) on one log
+ *             grid in |Q|.  Loop frequencies in |q0| <= qmax_over_k k:
+ *             bosonic 2 pi T n, fermionic (statistics FFRG_STAT_FERMI)
+ *             (2n+1) pi T.  While at most 2 n_matsubara + 1 (+1 fermionic)
+ *             of them lie in the domain, the frequency integral is their
+ *             Matsubara sum (weight T); beyond that, n_x0 Gauss-Legendre
+ *             nodes on [-qmax_over_k k, qmax_over_k k] (weights / 2 pi), the
+ *             T -> 0 form.  External frequency p0: bosonic 2 pi T m; with
+ *             fermionic statistics the external fermion leg's
+ *             p0f = pi T exp(-k/(pi T)) (App. G; n_ext_ang = 1). */
 typedef struct {
   int model;        /* ffrg_model */
   int regulator;    /* ffrg_regulator */
@@ -122,6 +144,7 @@ typedef struct {
   double qmax_over_k;          /* radial domain [0, qmax_over_k k] */
   double prefactor;            /* overall multiplier */
   int n_va, n_vb;              /* D4_FULL: vertex nodes in a and b (1 otherwise) */
+  int n_x0;                    /* FINITE_T_4D: frequency quadrature nodes (0 otherwise) */
 } ffrg_problem;
 
 /* Dressing tables values[table][stack][pt] (doubles, row-major) on the log grid

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libffrg.so")
 FP64, MIXED = 0, 1
 RULE_GL, RULE_GC2 = 0, 1
 REG_EXP, REG_LITIM = 0, 1
-MODEL_D3, MODEL_D4_VERTEX, MODEL_FINITE_T, MODEL_D4_FULL = 1, 2, 3, 4
+MODEL_D3, MODEL_D4_VERTEX, MODEL_FINITE_T, MODEL_D4_FULL, MODEL_FINITE_T_4D = 1, 2, 3, 4, 5
 STAT_BOSE, STAT_FERMI = 0, 1
 
 
@@ -44,7 +44,7 @@ class Problem(ctypes.Structure):
         ("m2_over_k2", ctypes.c_double), ("m2_shift", ctypes.c_double), ("lam", ctypes.c_double),
         ("T", ctypes.c_double), ("p_min", ctypes.c_double), ("p_max", ctypes.c_double),
         ("qmax_over_k", ctypes.c_double), ("prefactor", ctypes.c_double),
-        ("n_va", ctypes.c_int), ("n_vb", ctypes.c_int),
+        ("n_va", ctypes.c_int), ("n_vb", ctypes.c_int), ("n_x0", ctypes.c_int),
     ]
 
 
@@ -165,7 +165,7 @@ def to_problem(pb) -> Problem:
     """Build the C struct from any object with the problem's attribute names."""
     c = Problem()
     for name, _ in Problem._fields_:
-        default = {"statistics": 0, "n_va": 1, "n_vb": 1}
+        default = {"statistics": 0, "n_va": 1, "n_vb": 1, "n_x0": 0}
         setattr(c, name, getattr(pb, name, default[name]) if name in default else getattr(pb, name))
     return c
 

@@ -124,7 +124,8 @@ static int tables_needed(int model) {
   case FFRG_MODEL_D3: return 1;
   case FFRG_MODEL_D4_VERTEX:
   case FFRG_MODEL_D4_FULL: return 3;
-  case FFRG_MODEL_FINITE_T: return 2;
+  case FFRG_MODEL_FINITE_T:
+  case FFRG_MODEL_FINITE_T_4D: return 2;
   default: return -1;
   }
 }
@@ -156,11 +157,17 @@ int validate_problem(const ffrg_problem *pb, const ffrg_table_desc *td) {
   } else if (pb->n_va > 1 || pb->n_vb > 1) {
     return FFRG_EINVAL;
   }
-  if (pb->model == FFRG_MODEL_FINITE_T) {
+  if (pb->model == FFRG_MODEL_FINITE_T || pb->model == FFRG_MODEL_FINITE_T_4D) {
     if (pb->n_ext_ang < 1 || pb->n_ext_ang > 1024 || pb->n_matsubara < 0 || pb->n_matsubara > 4096) return FFRG_EINVAL;
     if (!(pb->T > 0.0) || !isfinite(pb->T)) return FFRG_EINVAL;
     if (pb->statistics != FFRG_STAT_BOSE && pb->statistics != FFRG_STAT_FERMI) return FFRG_EINVAL;
   } else if (pb->statistics != FFRG_STAT_BOSE) {
+    return FFRG_EINVAL;
+  }
+  if (pb->model == FFRG_MODEL_FINITE_T_4D) {
+    if (pb->n_x0 < 1 || pb->n_x0 > 4096) return FFRG_EINVAL;
+    if (pb->statistics == FFRG_STAT_FERMI && pb->n_ext_ang != 1) return FFRG_EINVAL;  // one fermion leg frequency
+  } else if (pb->n_x0 != 0) {
     return FFRG_EINVAL;
   }
   if (td) {
@@ -168,7 +175,7 @@ int validate_problem(const ffrg_problem *pb, const ffrg_table_desc *td) {
     if (td->n_tables < need) return FFRG_EINVAL;
     if (pb->model == FFRG_MODEL_D4_FULL) {
       if (td->n_stack != pb->n_va * pb->n_vb) return FFRG_EINVAL;
-    } else if (pb->model != FFRG_MODEL_FINITE_T && td->n_stack != 1) {
+    } else if (pb->model != FFRG_MODEL_FINITE_T && td->n_stack != 1) {   // FINITE_T_4D: one row per table
       return FFRG_EINVAL;
     }
   }
@@ -208,12 +215,15 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   pl->model = pb->model;
   pl->nr = pb->n_rad;
   pl->na1 = pb->n_ang1;
-  pl->na2 = is_d4(pb->model) ? pb->n_ang2 : 1;
+  pl->na2 = is_d4(pb->model) ? pb->n_ang2 : pb->model == FFRG_MODEL_FINITE_T_4D ? pb->n_x0 : 1;
   pl->n_ext_ang = pb->n_ext_ang;
   pl->n_ext_p = pb->n_ext_p;
-  pl->N = pb->model == FFRG_MODEL_FINITE_T ? pb->n_matsubara : 0;
-  pl->stat = pb->model == FFRG_MODEL_FINITE_T ? pb->statistics : FFRG_STAT_BOSE;
+  const bool ft = pb->model == FFRG_MODEL_FINITE_T || pb->model == FFRG_MODEL_FINITE_T_4D;
+  pl->N = ft ? pb->n_matsubara : 0;
+  pl->stat = ft ? pb->statistics : FFRG_STAT_BOSE;
   pl->nfreq = 2 * pl->N + 1 + (pl->stat == FFRG_STAT_FERMI ? 1 : 0);
+  // FINITE_T_4D: rows of loop frequencies, the Matsubara cap or the quadrature nodes
+  if (pb->model == FFRG_MODEL_FINITE_T_4D) pl->nfreq = std::max(pl->nfreq, pb->n_x0);
   pl->include_p0 = pb->include_p0;
   pl->n_ext = ffrg_n_ext(pb);
   pl->n_tables = td->n_tables;
@@ -286,7 +296,9 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
     }
   };
   pl->kbuf_count = pb->model == FFRG_MODEL_FINITE_T
-                       ? (size_t)(pl->N + pl->n_ext_ang) * pl->n_ext_p * pl->nr : 0;
+                       ? (size_t)(pl->N + pl->n_ext_ang) * pl->n_ext_p * pl->nr
+                   : pb->model == FFRG_MODEL_FINITE_T_4D ? (size_t)2 * pl->nfreq + 2   // frequency set of the scale
+                                                         : 0;
   forward(false, pl->fcr, pl->fn_chunks, pl->fn_items, pl->fjb);
   forward(true, pl->fcr64, pl->fn_chunks64, pl->fn_items64, pl->fjb64);
   // shared memory: tables + angle rules (+ sqrt(1-c1^2) for D4), 16-byte aligned regions
@@ -303,7 +315,8 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
                                 pb->n_matsubara, pb->include_p0, td->n_tables, td->n_stack, td->n_pts,
                                 pb->model == FFRG_MODEL_FINITE_T ? pb->statistics : 0,
                                 pb->model == FFRG_MODEL_D4_FULL ? pb->n_va : 1,
-                                pb->model == FFRG_MODEL_D4_FULL ? pb->n_vb : 1};
+                                pb->model == FFRG_MODEL_D4_FULL ? pb->n_vb : 1,
+                                pb->model == FFRG_MODEL_FINITE_T_4D ? pb->n_x0 : 0};
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     *out = it->second;
@@ -400,6 +413,7 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   case FFRG_MODEL_D3: a.norm = pb->prefactor * pb->lam * pb->lam / (4.0 * pi * pi); break;
   case FFRG_MODEL_D4_VERTEX:
   case FFRG_MODEL_D4_FULL: a.norm = pb->prefactor / (8.0 * pi * pi * pi); break;
+  case FFRG_MODEL_FINITE_T_4D: a.norm = pb->prefactor * pb->lam * pb->lam / (4.0 * pi * pi); break;  // T in the frequency weights
   default: a.norm = pb->prefactor * pb->lam * pb->lam * pb->T / (4.0 * pi * pi); break;
   }
   double lr = log(td->x_max / td->x_min);
@@ -573,6 +587,7 @@ int ffrg_n_ext(const ffrg_problem *pb) {
     if (pb->n_ext_ang < 1) return -1;
     return 2 * pb->n_ext_p + 1 + pb->n_ext_p * pb->n_ext_ang;
   case FFRG_MODEL_FINITE_T:
+  case FFRG_MODEL_FINITE_T_4D:
     if (pb->n_ext_ang < 1) return -1;
     return pb->n_ext_p * pb->n_ext_ang;
   default: return -1;
@@ -586,6 +601,9 @@ double ffrg_evals(const ffrg_problem *pb) {
   if (is_d4(pb->model)) nodes *= pb->n_ang2;
   if (pb->model == FFRG_MODEL_FINITE_T)
     nodes *= (2.0 * pb->n_matsubara + 1.0 + (pb->statistics == FFRG_STAT_FERMI ? 1.0 : 0.0));
+  if (pb->model == FFRG_MODEL_FINITE_T_4D)   // at most: the Matsubara cap or the quadrature nodes
+    nodes *= std::max(2.0 * pb->n_matsubara + 1.0 + (pb->statistics == FFRG_STAT_FERMI ? 1.0 : 0.0),
+                      (double)pb->n_x0);
   return (double)ne * nodes;
 }
 

@@ -536,6 +536,9 @@ int host_gauss_chebyshev2(int n, double *x, double *w);
 
 // kernels launched from several translation units (ffrg_rhs.cu)
 int launch_rhs(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s);
+// the finite-T model with a 4D regulator (frequency set, loop factors, one
+// block per external point); launch_rhs dispatches to it
+int launch_ft4(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s);
 // launch_rhs with the finite-T contraction optional: contract = false stops
 // after the angle-integrated kernel K (plan kbuf, in the kernel precision)
 int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, cudaStream_t s,

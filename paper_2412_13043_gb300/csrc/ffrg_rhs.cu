@@ -1148,6 +1148,7 @@ int launch_rhs(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precisi
 
 int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int precision, cudaStream_t s,
                       bool contract) {
+  if (a_in.model == FFRG_MODEL_FINITE_T_4D) return launch_ft4(ctx, pl_c, a_in, precision, s);
   Plan *pl = const_cast<Plan *>(pl_c);
   const bool mixed = precision == FFRG_MIXED;
   RhsArgs a = a_in;  // forward geometry of this precision
