@@ -325,46 +325,64 @@ def serving_bench(ctx, n_req: int, seconds_cap: float = 120.0):
 
 
 def stepper_bench(ctx):
-    """Steppers on the d=4 feedback flow at matched endpoint error against a
-    tight DP5(4) reference, all FP64: adaptive DP5(4) (6 RHS per step),
-    fixed-step Adams-Bashforth-Moulton (PECE, 2 RHS per step) and the linearly
-    implicit ROS2 (Jacobian from the adjoint kernels)."""
+    """Steppers on d=4 feedback flows at matched endpoint error against a tight
+    DP5(4) reference, all FP64: adaptive DP5(4) (6 RHS per step), fixed-step
+    Adams-Bashforth-Moulton (PECE, 2 RHS per step) and the linearly implicit
+    ROS2 (Jacobian from the adjoint kernels).  Two flows: M^2 = 1 (not stiff
+    on k in [0.01, 10]) and the massless M^2 = 0 flow, whose state Jacobian
+    reaches eigenvalues near -92 at k = 0.01 (DP5(4) then rejects about half
+    of its steps)."""
     import numpy as np
     import torch
 
     import ffrg_inputs as fi
     import paper_2412_13043_gb300 as ffrg
+    cases = []
     wl = fi.make_d4(seed=6, n_pts=32, n_ext_ang=4, n_rad=32, n_ang1=16, n_ang2=8)
-    pb = wl.problem
-    pb.p_min = pb.x_min = 0.01
-    t1 = math.log(wl.Lambda / wl.k_end)
-    tabs = ctx.tables(pb, wl.tables)
+    wl.problem.p_min = wl.problem.x_min = 0.01
+    cases.append(("d4 feedback flow, M^2 = 1, 32-pt tables, 4 ext angles, 32 x 16 x 8 nodes, k: 10 -> 0.01, FP64", wl,
+                  (("dp45", 1e-6), ("dp45", 1e-8), ("abm4", 50), ("abm4", 100), ("abm4", 200), ("abm4", 400),
+                   ("ros2", 1e-5), ("ros2", 1e-6), ("ros2", 1e-7))))
+    wl0 = fi.make_d4(seed=2, n_pts=16, n_ext_ang=2, n_rad=16, n_ang1=8, n_ang2=4, M2=0.0)
+    cases.append(("massless d4 feedback flow, M^2 = 0, 16-pt tables, 2 ext angles, 16 x 8 x 4 nodes, "
+                  "k: 10 -> 0.01, FP64", wl0,
+                  (("dp45", 1e-6), ("dp45", 1e-7), ("abm4", 400), ("abm4", 1600), ("ros2", 1e-4), ("ros2", 1e-5),
+                   ("ros2", 1e-6))))
+    out = []
+    for name, wl, runs in cases:
+        pb = wl.problem
+        t1 = math.log(wl.Lambda / wl.k_end)
+        tabs = ctx.tables(pb, wl.tables)
 
-    def run(kind, par):
-        y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        if kind == "dp45":
-            st = ctx.flow(pb, tabs, y, wl.Lambda, t1, feedback=1, precision=ffrg.FP64, rtol=par, atol=1e-14)
-        elif kind == "abm4":
-            st = ctx.abm_flow(pb, tabs, y, wl.Lambda, t1, par, order=4, feedback=1, precision=ffrg.FP64)
-        else:
-            st = ctx.rosenbrock_flow(pb, tabs, y, wl.Lambda, t1, rtol=par, atol=1e-14)
-        torch.cuda.synchronize()
-        return y.cpu().numpy(), time.perf_counter() - t, st
+        def run(kind, par):
+            y = torch.tensor(wl.y0, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            if kind == "dp45":
+                st = ctx.flow(pb, tabs, y, wl.Lambda, t1, feedback=1, precision=ffrg.FP64, rtol=par, atol=1e-14,
+                              raise_on_error=False)
+            elif kind == "abm4":   # fixed steps: may leave its stability region on the stiff flow
+                st = ctx.abm_flow(pb, tabs, y, wl.Lambda, t1, par, order=4, feedback=1, precision=ffrg.FP64,
+                                  raise_on_error=False)
+            else:
+                st = ctx.rosenbrock_flow(pb, tabs, y, wl.Lambda, t1, rtol=par, atol=1e-14, raise_on_error=False)
+            torch.cuda.synchronize()
+            ctx.status_read()   # a flow that left its stability region set the non-finite bit
+            return y.cpu().numpy(), time.perf_counter() - t, st
 
-    ref, _, _ = run("dp45", 1e-12)
-    rows = []
-    for kind, par in (("dp45", 1e-6), ("dp45", 1e-8), ("abm4", 50), ("abm4", 100), ("abm4", 200), ("abm4", 400),
-                      ("ros2", 1e-5), ("ros2", 1e-6), ("ros2", 1e-7)):
-        y, dt, st = run(kind, par)
-        rows.append({"method": kind, ("steps_requested" if kind == "abm4" else "rtol"): par,
-                     "endpoint_rel_err": float(np.max(np.abs(y - ref) / np.abs(ref))),
-                     "steps": st["steps"], "rejects": st["rejects"], "rhs_evals": st["rhs_evals"],
-                     "jacobians": st.get("jac_evals", 0), "seconds": dt})
-    tabs.free()
-    return {"workload": "d4 feedback flow, 32-pt tables, 4 ext angles, 32 x 16 x 8 nodes, k: 10 -> 0.01, FP64",
-            "runs": rows}
+        ref, _, _ = run("dp45", 1e-12)
+        rows = []
+        for kind, par in runs:
+            y, dt, st = run(kind, par)
+            ok = st["status"] == ffrg.OK and bool(np.all(np.isfinite(y)))
+            rows.append({"method": kind, ("steps_requested" if kind == "abm4" else "rtol"): par,
+                         "status": ffrg.strerror(st["status"]) if st["status"] else "ok",
+                         "endpoint_rel_err": float(np.max(np.abs(y - ref) / np.abs(ref))) if ok else None,
+                         "steps": st["steps"], "rejects": st["rejects"], "rhs_evals": st["rhs_evals"],
+                         "jacobians": st.get("jac_evals", 0), "seconds": dt})
+        tabs.free()
+        out.append({"workload": name, "runs": rows})
+    return out
 
 
 def adjoint_bench(ctx, wl, tabs, reps: int = 3):
