@@ -33,8 +33,8 @@ namespace umma {
 
 constexpr int kBM = 128;          // output rows per tile (A rows)
 constexpr int kBN = 256;          // output columns per tile (B rows: states)
-constexpr int kBK = 64;           // K-elements per stage
-constexpr int kStages = 2;
+constexpr int kBK = 32;           // K-elements per stage
+constexpr int kStages = 4;
 constexpr int kTileA = kBM * kBK * 2;   // 16 KB
 constexpr int kTileB = kBN * kBK * 2;   // 32 KB
 constexpr int kStageBytes = kTileA + kTileB;
