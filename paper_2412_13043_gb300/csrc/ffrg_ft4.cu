@@ -86,51 +86,76 @@ __device__ __forceinline__ double ft4_row(const RhsArgs &a, double sh2, double q
   return rs;
 }
 
-// FP32 angular sum (the mixed path); a denominator that cancels more than
-// half of its kinetic part (m^2 < 0 near the pole) is recomputed in FP64
-__device__ __forceinline__ float ft4_row32(const RhsArgs &a, float sh2, float q, float p, float k2, float inv_k2,
-                                           float m2, float us, float uo) {
-  const double *Zt = a.tab, *Lt = a.tab + a.n_pts;
-  const int n = a.n_pts;
+// FP32 angular sum (the mixed path) from shared memory: zl[i] = (Z_i, Z_{i+1}
+// - Z_i, L_i, L_{i+1} - L_i) per node (the last node's differences 0), cw[c] =
+// (c_c, v_c).  Propagator denominator Z k^2 h(x) + m^2 with h(x) = x + r(x) =
+// x/(1 - e^-x) (exponential regulator; its Taylor series for x < 1/2, where
+// 1 - e^-x cancels) or max(x, 1) (flat), hardware lg2/ex2/rcp.  A denominator that
+// cancels more than half of its kinetic part (m^2 < 0 near the pole) is
+// recomputed in FP64 from the FP64 tables.
+__device__ __forceinline__ float ft4_row32(const RhsArgs &a, const float4 *zl, const float2 *cw, float sh2, float q,
+                                           float p, float k2, float inv_k2, float m2, float us, float uo) {
+  const int n = a.n_pts, na1 = a.na1;
+  const float nm1 = (float)(n - 1);
+  const float base = fmaf(q, q, fmaf(p, p, sh2)), tqp = 2.0f * q * p;
   float rs = 0.0f;
-  for (int c = 0; c < a.na1; ++c) {
-    const float QP2 = fmaxf(0.0f, sh2 + fmaf(2.0f * q * p, (float)a.a1_x[c], fmaf(q, q, p * p)));
-    float u = fmaf(us, __log2f(QP2), uo);
-    u = fminf(fmaxf(u, 0.0f), (float)(n - 1));
+  for (int c = 0; c < na1; ++c) {
+    const float2 cv = cw[c];
+    const float QP2 = fmaxf(0.0f, fmaf(tqp, cv.x, base));
+    float u = fminf(fmaxf(fmaf(us, hw_lg2(QP2), uo), 0.0f), nm1);   // NaN (QP2 = 0 -> -inf) saturates to 0
     const int i = min((int)u, n - 2);
     const float w = u - (float)i;
-    const float z0 = (float)Zt[i], l0 = (float)Lt[i];
-    const float Z = fmaf(w, (float)Zt[i + 1] - z0, z0), L = fmaf(w, (float)Lt[i + 1] - l0, l0);
+    const float4 t = zl[i];
+    const float Z = fmaf(w, t.y, t.x), L = fmaf(w, t.w, t.z);
     const float x = QP2 * inv_k2;
-    const float r = a.reg == FFRG_REG_LITIM ? (x < 1.0f ? 1.0f - x : 0.0f)
-                    : x < 1e-12f                 ? 1.0f
-                    : x > 80.0f                  ? 0.0f
-                                                 : x / expm1f(x);
-    const float kin = Z * (QP2 + k2 * r);
+    float h;
+    if (a.reg == FFRG_REG_LITIM) h = fmaxf(x, 1.0f);
+    else if (x < 0.5f) {   // x/(1 - e^-x) = 1 + x/2 + x^2/12 - x^4/720 + x^6/30240 - ..., remainder < 4e-9
+      const float x2 = x * x;
+      h = fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 30240.0f, -1.0f / 720.0f), 1.0f / 12.0f), fmaf(x, 0.5f, 1.0f));
+    } else {               // 1 - e^-x >= 0.39: the ex2 error (2^-22.5) grows by at most 2.6x
+      h = x * hw_rcp(1.0f - hw_ex2(-1.4426950408889634f * x));
+    }
+    const float kin = Z * k2 * h;
     float g;
     if (m2 < 0.0f && kin + m2 < 0.5f * kin) {
       const double QPd = (double)QP2;
-      const double Zd = look(Zt, QPd, a.u_scale, a.u_off, n);
+      const double Zd = look(a.tab, QPd, a.u_scale, a.u_off, n);
       g = (float)(1.0 / prop_den(a.reg, Zd, 0.0, QPd, (double)m2, (double)k2, 1.0 / (double)k2));
     } else {
-      g = __frcp_rn(kin + m2);
+      g = hw_rcp(kin + m2);
     }
-    rs = fmaf((float)a.a1_w[c] * L, g, rs);
+    rs = fmaf(cv.y * L, g, rs);
   }
   return rs;
 }
 
 // one block per external point e = (p, m): threads over the (f, r) terms,
-// f major, in a fixed order; FP64 accumulation
+// f major, in a fixed order; FP64 accumulation.  The FP32 kernel stages both
+// tables and the angle rule in shared memory first.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) ft4_main_kernel(RhsArgs a, int nfreq_max) {
   __shared__ double red[kThreads / 32];
+  extern __shared__ __align__(16) unsigned char ft4_smem[];
   const int e = blockIdx.x, nm = a.n_ext_ang, ip = e / nm, m = e - ip * nm;
   const double *kb = (const double *)a.kbuf;
   const int nf = (int)kb[2 * nfreq_max];
   const double k = scale_k(a), k2 = k * k, m2 = mass2(a, k);
   const double p = ext_momentum(a, ip);
   const double p0 = a.stat ? kPi * a.T * exp(-k / (kPi * a.T)) : 2.0 * kPi * a.T * m;
+  float4 *zl = reinterpret_cast<float4 *>(ft4_smem);
+  float2 *cw = reinterpret_cast<float2 *>(zl + a.n_pts);
+  if (sizeof(T) == 4) {
+    const double *Zt = a.tab, *Lt = a.tab + a.n_pts;
+    for (int i = threadIdx.x; i < a.n_pts; i += blockDim.x) {
+      const bool last = i + 1 >= a.n_pts;
+      const double z0 = Zt[i], l0 = Lt[i];
+      zl[i] = make_float4((float)z0, last ? 0.0f : (float)(Zt[i + 1] - z0), (float)l0,
+                          last ? 0.0f : (float)(Lt[i + 1] - l0));
+    }
+    for (int c = threadIdx.x; c < a.na1; c += blockDim.x) cw[c] = make_float2((float)a.a1_x[c], (float)a.a1_w[c]);
+    __syncthreads();
+  }
   const float us = (float)(a.u_scale * 0.69314718055994530942), uo = (float)a.u_off;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nf * a.nr; i += blockDim.x) {
@@ -139,8 +164,8 @@ __global__ void __launch_bounds__(kThreads) ft4_main_kernel(RhsArgs a, int nfreq
     if (sizeof(T) == 8) {
       acc = fma(a.radF[i], ft4_row(a, sh * sh, q, p, k2, 1.0 / k2, m2), acc);
     } else {
-      const float rs = ft4_row32(a, (float)(sh * sh), (float)q, (float)p, (float)k2, (float)(1.0 / k2), (float)m2,
-                                 us, uo);
+      const float rs = ft4_row32(a, zl, cw, (float)(sh * sh), (float)q, (float)p, (float)k2, (float)(1.0 / k2),
+                                 (float)m2, us, uo);
       acc = fma(a.radF[i], (double)rs, acc);
     }
   }
@@ -163,8 +188,18 @@ int launch_ft4(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, c
   ft4_factor_kernel<<<(terms + kThreads - 1) / kThreads, kThreads, 0, s>>>(a, nfreq);
   const bool prof = ctx->profiling && ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
   if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
-  if (precision == FFRG_MIXED) ft4_main_kernel<float><<<a.n_ext, kThreads, 0, s>>>(a, nfreq);
-  else ft4_main_kernel<double><<<a.n_ext, kThreads, 0, s>>>(a, nfreq);
+  if (precision == FFRG_MIXED) {
+    const size_t smem = (size_t)pl->n_pts * sizeof(float4) + (size_t)pl->na1 * sizeof(float2);
+    if (smem > 227 * 1024) {
+      ctx->last_error = "tables and angle rule do not fit in shared memory";
+      return FFRG_EINVAL;
+    }
+    int st = ensure_smem_limit(ctx, (const void *)ft4_main_kernel<float>, smem);
+    if (st) return st;
+    ft4_main_kernel<float><<<a.n_ext, kThreads, smem, s>>>(a, nfreq);
+  } else {
+    ft4_main_kernel<double><<<a.n_ext, kThreads, 0, s>>>(a, nfreq);
+  }
   if (prof) {
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;
