@@ -108,22 +108,29 @@ __device__ __forceinline__ float ft4_row32(const RhsArgs &a, const float4 *zl, c
     const float4 t = zl[i];
     const float Z = fmaf(w, t.y, t.x), L = fmaf(w, t.w, t.z);
     const float x = QP2 * inv_k2;
-    float h;
-    if (a.reg == FFRG_REG_LITIM) h = fmaxf(x, 1.0f);
-    else if (x < 0.5f) {   // x/(1 - e^-x) = 1 + x/2 + x^2/12 - x^4/720 + x^6/30240 - ..., remainder < 4e-9
+    // G = 1/(kin + m^2), kin = Z k^2 h(x); for x >= 1/2 as d/(Z k^2 x + m^2 d),
+    // d = 1 - e^-x >= 0.39 (the ex2 error, 2^-22.5, grows by at most 2.6x):
+    // one reciprocal for regulator and propagator
+    float num = 1.0f, kin, den;
+    if (a.reg == FFRG_REG_LITIM) {
+      kin = Z * k2 * fmaxf(x, 1.0f);
+      den = kin + m2;
+    } else if (x < 0.5f) {   // x/(1 - e^-x) = 1 + x/2 + x^2/12 - x^4/720 + x^6/30240 - ..., remainder < 4e-9
       const float x2 = x * x;
-      h = fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 30240.0f, -1.0f / 720.0f), 1.0f / 12.0f), fmaf(x, 0.5f, 1.0f));
-    } else {               // 1 - e^-x >= 0.39: the ex2 error (2^-22.5) grows by at most 2.6x
-      h = x * hw_rcp(1.0f - hw_ex2(-1.4426950408889634f * x));
+      kin = Z * k2 * fmaf(x2, fmaf(x2, fmaf(x2, 1.0f / 30240.0f, -1.0f / 720.0f), 1.0f / 12.0f), fmaf(x, 0.5f, 1.0f));
+      den = kin + m2;
+    } else {
+      num = 1.0f - hw_ex2(-1.4426950408889634f * x);
+      kin = Z * k2 * x;          // = the kinetic part times d
+      den = fmaf(m2, num, kin);  // = d (kinetic part + m^2)
     }
-    const float kin = Z * k2 * h;
     float g;
-    if (m2 < 0.0f && kin + m2 < 0.5f * kin) {
+    if (m2 < 0.0f && den < 0.5f * kin) {
       const double QPd = (double)QP2;
       const double Zd = look(a.tab, QPd, a.u_scale, a.u_off, n);
       g = (float)(1.0 / prop_den(a.reg, Zd, 0.0, QPd, (double)m2, (double)k2, 1.0 / (double)k2));
     } else {
-      g = hw_rcp(kin + m2);
+      g = num * hw_rcp(den);
     }
     rs = fmaf(cv.y * L, g, rs);
   }
