@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-models", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1024)
+    ap.add_argument("--model-filter", default="",
+                    help="run only the model rows whose workload name contains this text")
     return ap.parse_args()
 
 
@@ -523,7 +525,7 @@ def ft4_rows(ctx, name, wl, steps):
     return rows
 
 
-def model_bench(ctx, steps: int = 5):
+def model_bench(ctx, steps: int = 5, name_filter: str = ""):
     """Single-RHS throughput of the other model workloads, mixed and FP64:
     d=3 (64 ext x 64 x 32 nodes), finite T (64 |p| x 9 p0, 96 x 48 x (2N+1))
     at N = 16/32/64 with T/k_end = 0.05/0.2/1, the d=4 model with the
@@ -548,6 +550,8 @@ def model_bench(ctx, steps: int = 5):
                   fi.make_finite_t_4d()))
     rows = []
     for name, wl in cases:
+        if name_filter and name_filter not in name:
+            continue
         pb = wl.problem
         if pb.model == fi.MODEL_FINITE_T_4D:
             rows.extend(ft4_rows(ctx, name, wl, steps))
@@ -796,7 +800,7 @@ def main():
 
     models = None
     if not args.no_models:
-        models = model_bench(ctx)
+        models = model_bench(ctx, name_filter=args.model_filter)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -306,6 +306,16 @@ void plan_geometry(Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td) 
   const size_t ang = (size_t)pl->na1 * 3 + (size_t)pl->na2 * 2;
   const size_t ang32 = ang + (size_t)4 * ((pl->na2 + 1) / 2);   // + second-angle node pairs
   pl->smem64 = al16((size_t)(pl->tabc_count ? pl->tabc_count : pl->tab_count) * 8) + al16(ang * 8);
+  // D4_FULL, mixed: lambda3 as cell polynomials (two float4 per (a, b, S0)
+  // cell) after the Z and lambda4 line rows, when that fits in shared memory
+  pl->l3cell = 0;
+  if (pb->model == FFRG_MODEL_D4_FULL) {
+    const int cells = 2 * td->n_pts + 4 * pl->n_va * pl->n_vb * td->n_pts;
+    if (al16((size_t)cells * 8) + al16(ang32 * 4) <= kMaxDynSmemBytes) {
+      pl->l3cell = 1;
+      pl->tab32_count = cells;
+    }
+  }
   pl->smem32 = al16((size_t)pl->tab32_count * 8) + al16(ang32 * 4);
   pl->smem64g = al16(ang * 8);
 }
@@ -362,7 +372,8 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   if (!st) st = dev_alloc(ctx, (void **)&pl->psi_s, (size_t)npsi * sizeof(double));
   if (!st)
     st = dev_alloc(ctx, (void **)&pl->partial, (size_t)std::max(pl->fn_items, pl->fn_items64) * sizeof(double));
-  if (!st) st = dev_alloc(ctx, (void **)&pl->tab32, (size_t)pl->tab_count * sizeof(float2));
+  if (!st) st = dev_alloc(ctx, (void **)&pl->tab32,
+                          (size_t)std::max(pl->tab_count, pl->tab32_count) * sizeof(float2));
   if (st) {
     plan_free(ctx, pl);
     return st;
@@ -399,6 +410,7 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.tabc_count = pl->tabc_count;
   a.n_va = pl->n_va;
   a.n_vb = pl->n_vb;
+  a.l3cell = pl->l3cell;
   a.tabc = pl->tabc;
   a.kbuf = pl->kbuf;
   a.k = k;

@@ -20,6 +20,8 @@
 namespace ffrg {
 
 constexpr int kThreads = 256;          // threads per CTA of the RHS kernels
+constexpr int kThreadsWide = 1024;     // the D4_FULL mixed kernel with lambda3 cells: one CTA per SM
+constexpr size_t kMaxDynSmemBytes = 227 * 1024;   // dynamic shared memory of one block
 constexpr unsigned kStatusNonFinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bound of every device wait
@@ -47,6 +49,7 @@ struct RhsArgs {
   int tab32_count; // float2 entries of the FP32 table layout
   int tabc_count;  // D4_FULL: doubles of the compact FP64 tables (0 otherwise)
   int n_va, n_vb;  // D4_FULL: vertex nodes in the shape variables a, b
+  int l3cell;      // D4_FULL, mixed: lambda3 as FP32 cell polynomials (one 1024-thread CTA per SM)
   int cr;          // rows per work item (d=4: outer rows)
   int n_chunks;    // work items per external point
   int n_items;     // n_ext * n_chunks
@@ -142,6 +145,11 @@ __device__ __forceinline__ float hw_lg2(float x) {
 __device__ __forceinline__ float hw_ex2(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float hw_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 __device__ __forceinline__ float hw_rcp(float x) {
@@ -446,6 +454,7 @@ struct Plan {
   int fcr64, fn_chunks64, fn_items64, fjb64;  // the same for the FP64 forward kernels
   int tab32_count;                // float2 entries of the FP32 table layout
   int tabc_count, n_va, n_vb;     // D4_FULL: compact FP64 table doubles, vertex nodes
+  int l3cell;                     // D4_FULL: the FP32 lambda3 cell layout fits in shared memory
   double *tabc;
   size_t kbuf_count;              // FINITE_T: entries of K (N + n_ext_ang) x n_ext_p x n_rad
   double *kbuf;

@@ -246,6 +246,9 @@ __device__ __forceinline__ bool skipped(const RhsArgs &a) { return a.skip && *(v
 // blocks of the per-radial precompute: radial nodes x values of |n|
 constexpr int kPreR = 64, kPreN = 8;
 
+// template tag of the D4_FULL mixed kernel with lambda3 cells (not a public model)
+constexpr int kModelD4FullCell = 100 + FFRG_MODEL_D4_FULL;
+
 // Every thread of a block of the calling grid (blockIdx.x over the grid,
 // blockDim.x threads) must run it: it synchronises the block.
 __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
@@ -334,16 +337,52 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
   const double kh = k2 * 0.6931471805599453094;
   const int z_count = a.n_stack * a.n_pts;
   if (a.model == FFRG_MODEL_D4_FULL) {
-    // compact rows [Z row 0 | lambda4 row 0 | lambda3 rows]: FP64 copy and FP32 pairs
+    // compact rows [Z row 0 | lambda4 row 0 | lambda3 rows]: FP64 copy and FP32
+    // pairs (with lambda3 cells: the two line rows only)
     const int np = a.n_pts, ns = a.n_stack;
+    const int n_line = a.l3cell ? 2 * np : a.tabc_count;
     for (int i = tid0; i < a.tabc_count; i += stride) {
       const int row = i / np, col = i - row * np;
       const size_t src = row == 0 ? (size_t)col : row == 1 ? (size_t)2 * ns * np + col : ((size_t)ns + row - 2) * np + col;
       const double f = row == 0 ? kh : 1.0;
       const double v = a.tab[src];
       a.tabc[i] = v;
-      const double d = col == np - 1 ? 0.0 : f * (a.tab[src + 1] - v);
-      a.tab32[i] = make_float2((float)(f * v - col * d), (float)((np - 1) * d));
+      if (i < n_line) {
+        const double d = col == np - 1 ? 0.0 : f * (a.tab[src + 1] - v);
+        a.tab32[i] = make_float2((float)(f * v - col * d), (float)((np - 1) * d));
+      }
+    }
+    if (a.l3cell) {
+      // Cell (ia, ib, is) of lambda3 on the (a, b, S0) grid: the trilinear
+      // interpolant on [is, is+1] x [ia, ia+1] x [ib, ib+1] written as a
+      // polynomial in the normalised coordinates (u_s, u_a, u_b) in [0, 1]^3
+      // (node coordinate = u (n - 1)):
+      //   c0 + c1 u_s + c2 u_a + c3 u_b + c4 u_s u_a + c5 u_s u_b + c6 u_a u_b + c7 u_s u_a u_b,
+      // from the corner differences; the upper neighbour of a last node is the
+      // node itself (zero difference).  Stored as (c0, c3, c1, c5), (c2, c6, c4, c7).
+      const int na = a.n_va, nb = a.n_vb;
+      const double Ns = np - 1, Na = na - 1, Nb = nb - 1;
+      float4 *cell = reinterpret_cast<float4 *>(a.tab32 + 2 * np);
+      for (int c = tid0; c < na * nb * np; c += stride) {
+        const int is = c % np, ab = c / np, ia = ab / nb, ib = ab - ia * nb;
+        const int s1 = min(is + 1, np - 1), a1 = min(ia + 1, na - 1), b1 = min(ib + 1, nb - 1);
+        auto f = [&](int sx, int ax, int bx) { return a.tab[((size_t)ns + ax * nb + bx) * np + sx]; };
+        const double f000 = f(is, ia, ib), f100 = f(s1, ia, ib), f010 = f(is, a1, ib), f001 = f(is, ia, b1);
+        const double f110 = f(s1, a1, ib), f101 = f(s1, ia, b1), f011 = f(is, a1, b1), f111 = f(s1, a1, b1);
+        const double Ds = f100 - f000, Da = f010 - f000, Db = f001 - f000;
+        const double Dsa = f110 - f100 - f010 + f000, Dsb = f101 - f100 - f001 + f000;
+        const double Dab = f011 - f010 - f001 + f000;
+        const double Dsab = f111 - f110 - f101 - f011 + f100 + f010 + f001 - f000;
+        const double i = is, j = ia, l = ib;
+        const double c7 = Ns * Na * Nb * Dsab;
+        const double c4 = Ns * Na * (Dsa - l * Dsab), c5 = Ns * Nb * (Dsb - j * Dsab), c6 = Na * Nb * (Dab - i * Dsab);
+        const double c1 = Ns * (Ds - j * Dsa - l * Dsb + j * l * Dsab);
+        const double c2 = Na * (Da - i * Dsa - l * Dab + i * l * Dsab);
+        const double c3 = Nb * (Db - i * Dsb - j * Dab + i * j * Dsab);
+        const double c0 = f000 - i * Ds - j * Da - l * Db + i * j * Dsa + i * l * Dsb + j * l * Dab - i * j * l * Dsab;
+        cell[2 * c] = make_float4((float)c0, (float)c3, (float)c1, (float)c5);
+        cell[2 * c + 1] = make_float4((float)c2, (float)c6, (float)c4, (float)c7);
+      }
     }
   } else if (a.model == FFRG_MODEL_FINITE_T) {
     for (int i = tid0; i <= z_count; i += stride)
@@ -844,6 +883,57 @@ __device__ __forceinline__ T lam3_full(const RhsArgs &a, const Tab *L3, T y3, T 
   return ((T)1 - wa) * (((T)1 - wb) * v00 + wb * v01) + wa * (((T)1 - wb) * v10 + wb * v11);
 }
 
+// lambda3 from the FP32 cell polynomials: the cell index from the three
+// normalised coordinates by the floor trick of line_pos (bit pattern of
+// 1.5 2^23 + i), one address from the three biased indices, two 16-byte
+// shared loads and the polynomial in four FMAs.  Saturation maps the shape
+// variables to [0, 1] (NaN to 0) as shape_pos does; the last node of each
+// axis is a cell of its own whose differences are zero.
+struct Cell32 {
+  unsigned base;  // shared address of the cells minus 32 x the bias of the three biased indices
+  int nb, np;
+  float Ns, Na, Nb;
+};
+__device__ __forceinline__ Cell32 cell32(const RhsArgs &a, const SmemLayout<float> &S) {
+  constexpr unsigned kBias = 0x4B400000u;  // bit pattern of 1.5 2^23
+  Cell32 C;
+  C.nb = a.n_vb;
+  C.np = a.n_pts;
+  C.base = (unsigned)__cvta_generic_to_shared(S.tab + 2 * a.n_pts) -
+           32u * kBias * (unsigned)((a.n_vb + 1) * a.n_pts + 1);
+  C.Ns = (float)(a.n_pts - 1);
+  C.Na = (float)(a.n_va - 1);
+  C.Nb = (float)(a.n_vb - 1);
+  return C;
+}
+__device__ __forceinline__ float cell_eval(unsigned addr, float us, float ua, float ub) {
+  float4 A, B;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(A.x), "=f"(A.y), "=f"(A.z), "=f"(A.w) : "r"(addr));
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+16];" : "=f"(B.x), "=f"(B.y), "=f"(B.z), "=f"(B.w) : "r"(addr));
+  const float2 u2 = make_float2(us, us);
+  const float2 P03 = __ffma2_rn(u2, make_float2(A.z, A.w), make_float2(A.x, A.y));   // c0 + c1 u_s, c3 + c5 u_s
+  const float2 P27 = __ffma2_rn(u2, make_float2(B.z, B.w), make_float2(B.x, B.y));   // c2 + c4 u_s, c6 + c7 u_s
+  const float2 t = __ffma2_rn(make_float2(ua, ua), P27, P03);   // the u_b^0 and u_b^1 parts
+  return fmaf(ub, t.y, t.x);
+}
+__device__ __forceinline__ unsigned cell_addr(const Cell32 &C, float us, float ua, float ub) {
+  const unsigned bs = __float_as_uint(__fmaf_rd(us, C.Ns, 12582912.0f));
+  const unsigned ba = __float_as_uint(__fmaf_rd(ua, C.Na, 12582912.0f));
+  const unsigned bb = __float_as_uint(__fmaf_rd(ub, C.Nb, 12582912.0f));
+  return C.base + 32u * ((ba * (unsigned)C.nb + bb) * (unsigned)C.np + bs);
+}
+__device__ __forceinline__ float sat_half(float v) {  // (v + 1)/2 saturated to [0, 1], NaN to 0
+  float u;
+  asm("fma.rn.sat.f32 %0, %1, 0f3F000000, 0f3F000000;" : "=f"(u) : "f"(v));
+  return u;
+}
+__device__ __forceinline__ float lam3_cell(const Cell32 &C, float y3, float us, float uy3, float va, float vb) {
+  float u_s;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u_s) : "f"(us), "f"(hw_lg2(y3)), "f"(uy3));
+  const float u_a = sat_half(va), u_b = sat_half(vb);
+  return cell_eval(cell_addr(C, u_s, u_a, u_b), u_s, u_a, u_b);
+}
+
 // sum_b w_b G(|q - p2|) lam3(.., b) lam3(.., c) of one (radial, first-angle)
 // row of the three-point block in FP32 (arguments as in d4_witem); the even
 // and odd nodes are summed separately and added at the end.
@@ -869,10 +959,123 @@ __device__ __forceinline__ float tp_sum_x2(const RhsArgs &a, const SmemLayout<fl
   return rs.x + rs.y;
 }
 
+// sum_b w_b G(|q - p2|) lam3(.., b) lam3(.., c) of one (radial, first-angle)
+// row of the D4_FULL three-point block in FP32 with lambda3 cells (arguments
+// as in d4_witem): the two vertex lookups of a node share their coordinate
+// arithmetic in packed FP32 (FFMA2).  Shape variables from the leg components
+// as in d4_witem's line-row branch.
+template <bool POLE>
+__device__ __forceinline__ float tp_full_cell(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<float> &S,
+                                              const KConst<float> &kc, int e, int r, int ia, float q, float q2,
+                                              float A2, float Ay, float b0, float t2y, float by, float sy_ab,
+                                              float qs1, float x1, float x2, float psp, float hc, float hs) {
+  const Cell32 C = cell32(a, S);
+  const Row32 Zt = tab_row(S, 0);
+  const float us = kc.us, uy1 = kc.uy1, uy3 = kc.uy3;
+  const float rA = hw_rsqrt(A2), qy = q2 * kc.sy, qs1sq = qs1 * qs1;
+  const float2 magic = make_float2(12582912.0f, 12582912.0f);
+  float rs = 0.0f;
+  for (int b = 0; b < a.na2; ++b) {
+    const float2 cw = S.cw2[b];
+    const float By = fmaf(-t2y, cw.x, b0);   // sy |q - p2|^2
+    const float ZB = look(Zt, By, us, uy1, a.n_pts);
+    float GB;
+    if constexpr (POLE) {
+      auto pole_b = [&]() { return pole_d4<FFRG_MODEL_D4_FULL>(sa, e, r, ia, b); };
+      GB = inv_prop<true>(a, ZB, By, 0.0f, kc, pole_b);
+    } else {
+      GB = prop1(By, ZB, kc.m2);
+    }
+    const float rB = hw_rsqrt(By * kc.isy);
+    const float a_b = (fmaf(hs, cw.x, hc) - q) * rB;                        // cos(q, -(q - p2))
+    const float y1 = qs1 * cw.x, y2 = y1 - psp, z2 = qs1sq * fmaf(-cw.x, cw.x, 1.0f);
+    const float a_c = -fmaf(x1, x2, fmaf(y1, y2, z2)) * rA * rB;             // cos(q + p1, -(q - p2))
+    const float db = qy + By, dc = Ay + By, rbc = hw_rcp(db * dc);
+    const float b_b = (qy - By) * dc * rbc, b_c = (Ay - By) * db * rbc;
+    // legs (q, -(q-p2), p2) and (q+p1, -(q-p2), -(p1+p2))
+    float2 u_s;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u_s.x) : "f"(us), "f"(hw_lg2(by + By)), "f"(uy3));
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u_s.y) : "f"(us), "f"(hw_lg2(sy_ab + By)), "f"(uy3));
+    const float2 u_a = make_float2(sat_half(a_b), sat_half(a_c)), u_b = make_float2(sat_half(b_b), sat_half(b_c));
+    const float2 ts = __ffma2_rd(u_s, make_float2(C.Ns, C.Ns), magic);
+    const float2 ta = __ffma2_rd(u_a, make_float2(C.Na, C.Na), magic);
+    const float2 tb = __ffma2_rd(u_b, make_float2(C.Nb, C.Nb), magic);
+    const unsigned nb = (unsigned)C.nb, np = (unsigned)C.np;
+    const unsigned ab = C.base + 32u * ((__float_as_uint(ta.x) * nb + __float_as_uint(tb.x)) * np + __float_as_uint(ts.x));
+    const unsigned ac = C.base + 32u * ((__float_as_uint(ta.y) * nb + __float_as_uint(tb.y)) * np + __float_as_uint(ts.y));
+    const float lb = cell_eval(ab, u_s.x, u_a.x, u_b.x), lc = cell_eval(ac, u_s.y, u_a.y, u_b.y);
+    rs = fmaf(cw.y * GB, lb * lc, rs);
+  }
+  return rs;
+}
+
+// The same sum without a near-pole test, two second-angle nodes per step in
+// packed FP32 (the node pairs of tp_sum_x2, an odd last node paired with
+// itself at weight 0); the four vertex lookups of a step stay scalar.
+__device__ __forceinline__ float tp_full_cell_x2(const RhsArgs &a, const SmemLayout<float> &S, const KConst<float> &kc,
+                                                 float q, float q2, float A2, float Ay, float b0, float t2y, float by,
+                                                 float sy_ab, float qs1, float x1, float x2, float psp, float hc,
+                                                 float hs) {
+  const Cell32 C = cell32(a, S);
+  const Row32 Zt = tab_row(S, 0);
+  const float us = kc.us, uy3 = kc.uy3, nm1 = (float)(a.n_pts - 1);
+  const float nrA = -hw_rsqrt(A2), qy = q2 * kc.sy, qs1sq = qs1 * qs1, x12 = x1 * x2;
+  const float2 magic = make_float2(12582912.0f, 12582912.0f);
+  float2 rs = make_float2(0.0f, 0.0f);
+  const int npair = (a.na2 + 1) >> 1;
+  for (int j = 0; j < npair; ++j) {
+    const float4 cw = S.cw4[j];
+    const float2 c2 = make_float2(cw.x, cw.y);
+    const float2 By = __ffma2_rn(make_float2(-t2y, -t2y), c2, make_float2(b0, b0));   // sy |q - p2|^2
+    const float2 ZB = look2(Zt, By, us, kc.uy1, make_float2(nm1, nm1));
+    float2 N, R;
+    prop2(By, ZB, make_float2(kc.m2, kc.m2), N, R);
+    const float2 B2 = __fmul2_rn(By, make_float2(kc.isy, kc.isy));
+    const float2 rB = make_float2(hw_rsqrt(B2.x), hw_rsqrt(B2.y));
+    // cos(q, -(q - p2)) and cos(q + p1, -(q - p2))
+    const float2 a_b = __fmul2_rn(__ffma2_rn(make_float2(hs, hs), c2, make_float2(hc - q, hc - q)), rB);
+    const float2 y1 = __fmul2_rn(make_float2(qs1, qs1), c2);
+    const float2 z2 = __fmul2_rn(make_float2(qs1sq, qs1sq), __ffma2_rn(__fmul2_rn(c2, make_float2(-1.0f, -1.0f)), c2,
+                                                                     make_float2(1.0f, 1.0f)));
+    const float2 ac0 = __ffma2_rn(y1, __fadd2_rn(y1, make_float2(-psp, -psp)), __fadd2_rn(z2, make_float2(x12, x12)));
+    const float2 a_c = __fmul2_rn(ac0, __fmul2_rn(rB, make_float2(nrA, nrA)));
+    // b = (s1 - s2)/(s1 + s2) of both vertices from one reciprocal
+    const float2 db = __fadd2_rn(make_float2(qy, qy), By), dc = __fadd2_rn(make_float2(Ay, Ay), By);
+    const float2 P = __fmul2_rn(db, dc);
+    const float2 rbc = make_float2(hw_rcp(P.x), hw_rcp(P.y));
+    const float2 nBy = __fmul2_rn(By, make_float2(-1.0f, -1.0f));
+    const float2 b_b = __fmul2_rn(__fmul2_rn(__fadd2_rn(make_float2(qy, qy), nBy), dc), rbc);
+    const float2 b_c = __fmul2_rn(__fmul2_rn(__fadd2_rn(make_float2(Ay, Ay), nBy), db), rbc);
+    const float2 yb = __fadd2_rn(make_float2(by, by), By), yc = __fadd2_rn(make_float2(sy_ab, sy_ab), By);
+    float lb[2], lc[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float2 u_s;
+      asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u_s.x) : "f"(us), "f"(hw_lg2(h ? yb.y : yb.x)), "f"(uy3));
+      asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(u_s.y) : "f"(us), "f"(hw_lg2(h ? yc.y : yc.x)), "f"(uy3));
+      const float2 u_a = make_float2(sat_half(h ? a_b.y : a_b.x), sat_half(h ? a_c.y : a_c.x));
+      const float2 u_b = make_float2(sat_half(h ? b_b.y : b_b.x), sat_half(h ? b_c.y : b_c.x));
+      const float2 ts = __ffma2_rd(u_s, make_float2(C.Ns, C.Ns), magic);
+      const float2 ta = __ffma2_rd(u_a, make_float2(C.Na, C.Na), magic);
+      const float2 tb = __ffma2_rd(u_b, make_float2(C.Nb, C.Nb), magic);
+      const unsigned nb = (unsigned)C.nb, np = (unsigned)C.np;
+      const unsigned ab =
+          C.base + 32u * ((__float_as_uint(ta.x) * nb + __float_as_uint(tb.x)) * np + __float_as_uint(ts.x));
+      const unsigned ac =
+          C.base + 32u * ((__float_as_uint(ta.y) * nb + __float_as_uint(tb.y)) * np + __float_as_uint(ts.y));
+      lb[h] = cell_eval(ab, u_s.x, u_a.x, u_b.x);
+      lc[h] = cell_eval(ac, u_s.y, u_a.y, u_b.y);
+    }
+    const float2 W = __fmul2_rn(__fmul2_rn(make_float2(cw.z, cw.w), N), R);
+    rs = __ffma2_rn(__fmul2_rn(W, make_float2(lb[0], lb[1])), make_float2(lc[0], lc[1]), rs);
+  }
+  return rs.x + rs.y;
+}
+
 // d=4 vertex expansion: row = (radial node r, first-angle node ia), inner loop
 // over the second-angle nodes for the three-point block.  FULL: the D4_FULL
 // model (lambda3 on (S0, a, b); compact tables Z | lambda4 | lambda3 rows).
-template <typename T, bool POLE, bool FULL = false>
+template <typename T, bool POLE, bool FULL = false, bool CELL = false>
 __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
                                            const KConst<T> &kc, int e, int c, int lane) {
   const T us = kc.us, sy = kc.sy;
@@ -910,7 +1113,9 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
     if (block == 0) {
       const T l4 = look(L4, (q2 + p2) * sy, us, kc.uy2, np);
       T l3;
-      if constexpr (FULL) l3 = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, kc.uy3, va_shape_a(q, p, c1, q2, A2, p2),
+      if constexpr (CELL) l3 = lam3_cell(cell32(a, S), (q2 + A2 + p2) * sy, us, kc.uy3,
+                                         va_shape_a(q, p, c1, q2, A2, p2), shape_b(q2, A2));
+      else if constexpr (FULL) l3 = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, kc.uy3, va_shape_a(q, p, c1, q2, A2, p2),
                                          shape_b(q2, A2));   // legs q, -(q+p), p
       else l3 = look(L3, (q2 + A2 + p2) * sy, us, kc.uy3, np);
       v = kc.sw2 * ((T)(-0.5) * l4 + l3 * l3 * GA);
@@ -920,7 +1125,10 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
     } else {
       const T uy1 = kc.uy1, uy3 = kc.uy3;
       T la;
-      if constexpr (FULL)
+      if constexpr (CELL)
+        la = lam3_cell(cell32(a, S), (q2 + A2 + p2) * sy, us, uy3, va_shape_a(q, p, c1, q2, A2, p2),
+                       shape_b(q2, A2));
+      else if constexpr (FULL)
         la = lam3_full(a, L3, (q2 + A2 + p2) * sy, us, uy3, va_shape_a(q, p, c1, q2, A2, p2),
                        shape_b(q2, A2));   // legs q, -(q+p1), p1
       else la = look(L3, (q2 + A2 + p2) * sy, us, uy3, np);
@@ -932,6 +1140,10 @@ __device__ __forceinline__ RowAcc<T> d4_witem(const RhsArgs &a, const RhsArgs *s
       const T by = base * sy, b0 = (base - t1) * sy, t2y = t2 * sy, sy_ab = (A2 + C2) * sy;
       T rs = 0;
       if constexpr (sizeof(T) == 4 && !FULL && !POLE) rs = tp_sum_x2(a, S, kc, Zt, L3, b0, t2y, by, sy_ab);
+      else if constexpr (CELL && !POLE) rs = tp_full_cell_x2(a, S, kc, q, q2, A2, Ay, b0, t2y, by, sy_ab, qs1, x1, x2,
+                                                             psp, hc, hs);
+      else if constexpr (CELL) rs = tp_full_cell<POLE>(a, sa, S, kc, e, r, ia, q, q2, A2, Ay, b0, t2y, by, sy_ab, qs1, x1,
+                                                       x2, psp, hc, hs);
       else for (int b = 0; b < a.na2; ++b) {
         const auto cw = S.cw2[b];
         const T By = b0 - t2y * cw.x;   // sy |q - p2|^2
@@ -986,6 +1198,7 @@ __device__ __forceinline__ RowAcc<T> witem(const RhsArgs &a, const RhsArgs *sa, 
   if constexpr (MODEL == FFRG_MODEL_D3) return d3_witem<T, POLE>(a, sa, S, kc, e, c, lane);
   else if constexpr (MODEL == FFRG_MODEL_D4_VERTEX) return d4_witem<T, POLE>(a, sa, S, kc, e, c, lane);
   else if constexpr (MODEL == FFRG_MODEL_D4_FULL) return d4_witem<T, POLE, true>(a, sa, S, kc, e, c, lane);
+  else if constexpr (MODEL == kModelD4FullCell) return d4_witem<float, POLE, true, true>(a, sa, S, kc, e, c, lane);
   else static_assert(MODEL != FFRG_MODEL_FINITE_T, "finite T runs through ftk_rows");
 }
 
@@ -1044,7 +1257,7 @@ template <int MODEL, typename T, bool POLE>
 __device__ __forceinline__ void item_loop(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
                                           const KConst<T> &kc) {
   const int lane = threadIdx.x & 31;
-  const int rot = is_d4(MODEL) ? a.n_ext_p + 1 : 0;
+  const int rot = is_d4(MODEL) || MODEL == kModelD4FullCell ? a.n_ext_p + 1 : 0;
   for (;;) {
     int d = 0;
     if (lane == 0) d = (int)atomicAdd(a.work_ctr, 1u);
@@ -1096,6 +1309,22 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) rhs_main(RhsArg
   }
 }
 
+// D4_FULL, mixed, lambda3 as cell polynomials: the cells take most of shared
+// memory, so one CTA of 1024 threads per SM (the warps of four 256-thread CTAs)
+__global__ void __launch_bounds__(kThreadsWide, 1) rhs_main_cell(RhsArgs a) {
+  if (skipped(a)) return;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
+  if (threadIdx.x == 0) sa = a;
+  SmemLayout<float> S(smem, a);
+  if (!main_prologue<float>(a, S, &bar)) return;
+  const KConst<float> kc = load_kconst<float>(a);
+  const bool pole = pole_possible<float>(a, S, kc);
+  if (pole) item_loop<kModelD4FullCell, float, true>(a, &sa, S, kc);
+  else item_loop<kModelD4FullCell, float, false>(a, &sa, S, kc);
+}
+
 // finite T: outputs from K and the radial factors, one block per external point
 template <typename T>
 __global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
@@ -1107,10 +1336,10 @@ __global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
 
 
 // ---------------------------------------------------------------------------
-constexpr size_t kMaxDynSmem = 227 * 1024;   // dynamic shared memory of one block
+constexpr size_t kMaxDynSmem = kMaxDynSmemBytes;
 
 template <typename K>
-static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int *grid) {
+static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int *grid, int threads = kThreads) {
   if (smem > kMaxDynSmem) {
     ctx->last_error = "dressing tables do not fit in shared memory";
     return FFRG_EINVAL;
@@ -1118,14 +1347,14 @@ static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int 
   int st = ensure_smem_limit(ctx, (const void *)kernel, smem);
   if (st) return st;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   if (per_sm < 1) {
     ctx->last_error = "RHS kernel cannot be resident";
     return FFRG_EINVAL;
   }
   // one warp-sized item per warp is the most a CTA can start with
-  const int ctas = (items + kThreads / 32 - 1) / (kThreads / 32);
+  const int ctas = (items + threads / 32 - 1) / (threads / 32);
   *grid = std::max(1, std::min(ctas, per_sm * ctx->num_sms));
   return FFRG_OK;
 }
@@ -1177,12 +1406,17 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
     break;
   default: kern = mixed ? rhs_main<FFRG_MODEL_FINITE_T, float> : rhs_main<FFRG_MODEL_FINITE_T, double>; break;
   }
+  int threads = kThreads;
+  if (mixed && a.model == FFRG_MODEL_D4_FULL && a.l3cell) {
+    kern = rhs_main_cell;
+    threads = kThreadsWide;
+  }
   if (!a.work_ctr || !a.radq32 || !a.ext_done || !a.kconst || (a.model == FFRG_MODEL_FINITE_T && !a.kbuf)) {
     ctx->last_error = "plan without work counters, FP32 radial nodes or constant block";
     return FFRG_EINVAL;
   }
   if (grid == 0) {
-    st = persistent_grid(ctx, kern, smem, a.n_items, &grid);
+    st = persistent_grid(ctx, kern, smem, a.n_items, &grid, threads);
     if (st) return st;
   }
   precompute_kernel<<<precompute_blocks(a, 4 * ctx->num_sms), kThreads, 0, s>>>(a);
@@ -1191,7 +1425,7 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
   const bool prof = ctx->profiling && cap == cudaStreamCaptureStatusNone &&
                     ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
   if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
-  kern<<<grid, kThreads, smem, s>>>(a);
+  kern<<<grid, threads, smem, s>>>(a);
   if (prof) {
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;

@@ -201,6 +201,16 @@ def test_d4_full_small_ragged(ctx):
             _check(ctx, wl, k)
 
 
+def test_d4_full_line_rows_when_cells_exceed_shared_memory(ctx):
+    """A 96 x 12 x 12 vertex grid: its FP32 cell polynomials (32 bytes per
+    (S0, a, b) node, 444 KB) exceed shared memory, so the mixed kernel reads
+    lambda3 from line rows (8 bytes per node, 112 KB), four rows per lookup;
+    the 96 x 8 x 7 grids of the other tests use the cells."""
+    wl = fi.make_d4_full(seed=46, n_pts=96, n_va=12, n_vb=12, n_ext_ang=2, n_rad=9, n_ang1=5, n_ang2=4)
+    for k in (1.3, 0.2):
+        _check(ctx, wl, k)
+
+
 def test_d4_full_full_size_every_output(ctx):
     """96-point log grid x 8 x 7 vertex grid, 961 external points x
     (128 x 64 x 16) nodes, every output against the oracle."""
