@@ -531,7 +531,8 @@ def model_bench(ctx, steps: int = 5, name_filter: str = ""):
     at N = 16/32/64 with T/k_end = 0.05/0.2/1, the d=4 model with the
     three-point vertex on a 96 x 8 x 7 (S0, a, b) grid, and the fermionic
     loop at N = 16 (2N+2 frequencies).  step_ms: one ffrg_rhs (precompute + main);
-    kernel_ms: the main kernel (profiling events); k = 1."""
+    kernel_ms: the main kernel (profiling events; mixed finite T: the single
+    cooperative launch of the whole RHS); k = 1."""
     import numpy as np
     import torch
 

@@ -363,7 +363,10 @@ int get_plan(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_table_desc *td, P
   if (!st) st = dev_alloc(ctx, (void **)&pl->radF32, nF * sizeof(float));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq, pl->nr * sizeof(double));
   if (!st) st = dev_alloc(ctx, (void **)&pl->radq32, pl->nr * sizeof(float));
-  if (!st) st = dev_alloc(ctx, (void **)&pl->work_ctr, sizeof(unsigned));
+  // work_ctr[0]: item counter of the main kernels; [1..4]: grid counters of
+  // the finite-T mixed single-launch RHS (all zero at the start)
+  if (!st) st = dev_alloc(ctx, (void **)&pl->work_ctr, 5 * sizeof(unsigned));
+  if (!st) st = set_cuda_error(ctx, cudaMemset(pl->work_ctr, 0, 5 * sizeof(unsigned)), "cudaMemset(counters)");
   if (!st) st = dev_alloc(ctx, (void **)&pl->ext_done, (size_t)pl->n_ext * sizeof(unsigned));
   if (!st) st = dev_alloc(ctx, (void **)&pl->kconst, kKConstBytes);
   if (!st && pl->tabc_count) st = dev_alloc(ctx, (void **)&pl->tabc, (size_t)pl->tabc_count * sizeof(double));
@@ -442,6 +445,10 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   }
   a.twopiT = 2.0 * kPi * pb->T;
   a.sum_w2 = pl->sum_w2;
+  // FP32 scale constants of this k on the host (the kernels use them unless a
+  // flow stage sets k_dev or m2_dev later); every field they read is set above
+  a.kc_host = kconst_f32(a, k, a.m2_over_k2 * k * k + a.m2_shift);
+  a.kc_host_ok = 1;
   a.tab = tab;
   a.tab32 = pl->tab32;
   a.rad_x = pl->rad_x;
@@ -456,6 +463,7 @@ void fill_args(const Plan *pl, const ffrg_problem *pb, const ffrg_table_desc *td
   a.radq32 = pl->radq32;
   a.radF32 = pl->radF32;
   a.work_ctr = pl->work_ctr;
+  a.fused_ctr = pb->model == FFRG_MODEL_FINITE_T ? pl->work_ctr + 1 : nullptr;
   a.ext_done = pl->ext_done;
   a.kconst = pl->kconst;
   a.ext_pd = pl->ext_pd;

@@ -40,6 +40,15 @@ __host__ __device__ inline bool is_d4(int model) {
 // bytes of the per-RHS constant block (FP32 and FP64 scale constants)
 constexpr int kKConstBytes = 256;
 
+// Scale-dependent constants of one RHS in a kernel precision (the FP32 and
+// FP64 sets are described where the kernels use them).
+template <typename T>
+struct KConst {
+  T k2, inv_k2, m2, us, uo, plim, sy, som;
+  T uy1, uy2, uy3, uy4, twopiT, sw2;
+  T isy;  // 1/sy
+};
+
 struct RhsArgs {
   int model, reg;
   int nr, na1, na2;
@@ -68,6 +77,8 @@ struct RhsArgs {
   double twopiT;               // 2 pi T
   double x_min2;               // x_min^2 (lookups below x_min return the first node)
   double sum_w2;               // sum of the second-angle weights (D4)
+  KConst<float> kc_host;       // FP32 scale constants from the host (valid when kc_host_ok, k_dev and m2_dev null)
+  int kc_host_ok;
   const double *tab;           // FP64 tables [n_tables][n_stack][n_pts]
   double *tabc;                // D4_FULL: compact FP64 tables [Z row | lambda4 row | lambda3 rows] (precompute)
   void *kbuf;                  // FINITE_T: K[j][ip][r], j < N + n_ext_ang, in the kernel precision (main kernel)
@@ -85,6 +96,7 @@ struct RhsArgs {
   float *radq32;               // per-r momentum q in FP32
   float *radF32;               // radF in FP32 (mixed kernels)
   unsigned *work_ctr;          // optional: dynamic work-item counter, reset by the precompute kernel
+  unsigned *fused_ctr;         // optional (finite T): four grid counters of the single-launch mixed RHS
   unsigned *ext_done;          // finished items per external point, reset likewise
   void *kconst;                // kKConstBytes: scale constants of the RHS, written by the precompute kernel
   double *ext_pd;              // per external |p| index: p_i (written by the precompute kernel)
@@ -392,6 +404,35 @@ __device__ __forceinline__ double mass2(const RhsArgs &a, double k) {
   return a.m2_over_k2 * k * k + (a.m2_dev ? *a.m2_dev : a.m2_shift);
 }
 
+// The FP32 scale constants from the scale k and m^2 (a division and one log;
+// the k-independent parts of the coordinates come from the host).  On the
+// device this is FP64 work on one thread, slow on this part, so plain RHS
+// calls take the host's copy (fill_args).  The FP32 coordinate offsets are
+// formed in FP64 and rounded once (an error of a few FP32 ulps there would
+// move lookups by ~1e-5 of a node).
+__host__ __device__ inline KConst<float> kconst_f32(const RhsArgs &a, double kd, double m2d) {
+  const double k2d = kd * kd, inv_k2d = 1.0 / k2d;
+  KConst<float> c;
+  c.k2 = (float)k2d;
+  c.inv_k2 = (float)inv_k2d;
+  c.m2 = (float)m2d;
+  c.plim = -2.0f * c.m2;
+  c.us = a.us1f;
+  c.uo = (float)a.uoc1[0];
+  c.sy = (float)(1.4426950408889634074 * inv_k2d);
+  c.som = c.sy;  // 1/(k^2 ln 2) = log2(e)/k^2
+  c.isy = (float)(0.6931471805599453094 * k2d);
+  // coordinates taken in y = sy s^2: shift by -u_scale ln(sy) / (n-1)
+  const double lnsy = 0.36651292058166432701 - log(k2d);  // ln(log2 e) - ln k^2
+  c.uy1 = (float)(a.uoc1[0] - a.us1 * lnsy);
+  c.uy2 = (float)(a.uoc1[1] - a.us1 * lnsy);
+  c.uy3 = (float)(a.uoc1[2] - a.us1 * lnsy);
+  c.uy4 = (float)(a.uoc1[3] - a.us1 * lnsy);
+  c.twopiT = (float)a.twopiT;
+  c.sw2 = (float)a.sum_w2;
+  return c;
+}
+
 __device__ __forceinline__ double ext_momentum(const RhsArgs &a, int ip) {
   return a.p_min * exp((double)ip * a.p_ratio_step);
 }
@@ -459,6 +500,7 @@ struct Plan {
   size_t kbuf_count;              // FINITE_T: entries of K (N + n_ext_ang) x n_ext_p x n_rad
   double *kbuf;
   int grid64, grid32;       // persistent grids (FP64 / mixed kernels)
+  int grid_single;          // finite T, mixed: grid of the single-launch RHS (-1: not available)
   size_t smem64, smem32;    // dynamic shared memory bytes
   size_t smem64g;           // FP64 kernels with tables in global memory: angle rules only
   double *rad_x, *rad_w, *a1_x, *a1_w, *a2_x, *a2_w, *psi_x, *psi_w;

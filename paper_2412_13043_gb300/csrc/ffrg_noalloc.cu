@@ -155,6 +155,7 @@ extern "C" int ffrg_rhs_noalloc(const ffrg_problem *pb, const ffrg_table_desc *t
   pl.grid32 = 0;
   RhsArgs a;
   fill_args(&pl, pb, td, tables_dev, k, a);
+  a.fused_ctr = nullptr;   // the scratch holds no persistent grid counters: the three-launch finite-T path
   a.out = out_dev;
   a.status = status;
   int st = launch_rhs(&lc, &pl, a, precision, s);

@@ -106,48 +106,22 @@ __device__ __noinline__ float pole_ftk(const RhsArgs *a, int ip, int jk, int r, 
 // uy1..uy4: offsets of table coordinates taken in y of S0^2 = (sum of c
 // squares)/c (c = 1..4; ln(sy) and ln c folded in); twopiT = 2 pi T;
 // sw2 = sum of the second-angle weights.
-template <typename T>
-struct KConst {
-  T k2, inv_k2, m2, us, uo, plim, sy, som;
-  T uy1, uy2, uy3, uy4, twopiT, sw2;
-  T isy;  // 1/sy
-};
-
 struct KConstPair {
   KConst<float> f;
   KConst<double> d;
 };
 static_assert(sizeof(KConstPair) <= kKConstBytes, "constant block too small");
 
-// The k-dependent constants from the scale k (a division and one log; the
-// k-independent parts of the coordinates come from the host): FP64 work is
-// slow on this part, and these run once per RHS on one thread.  The FP32
-// coordinate offsets are formed in FP64 and rounded once (an error of a few
-// FP32 ulps there would move lookups by ~1e-5 of a node).
+// The k-dependent constants of one RHS: FP32 from kconst_f32 (or the host's
+// copy of it), FP64 below; once per RHS on one thread.
 template <typename T>
 __device__ __forceinline__ KConst<T> make_kconst(const RhsArgs &a);
 template <>
 __device__ __forceinline__ KConst<float> make_kconst<float>(const RhsArgs &a) {
-  const double kd = scale_k(a), k2d = kd * kd, inv_k2d = 1.0 / k2d;
-  KConst<float> c;
-  c.k2 = (float)k2d;
-  c.inv_k2 = (float)inv_k2d;
-  c.m2 = (float)mass2(a, kd);
-  c.plim = -2.0f * c.m2;
-  c.us = a.us1f;
-  c.uo = (float)a.uoc1[0];
-  c.sy = (float)(1.4426950408889634074 * inv_k2d);
-  c.som = c.sy;  // 1/(k^2 ln 2) = log2(e)/k^2
-  c.isy = (float)(0.6931471805599453094 * k2d);
-  // coordinates taken in y = sy s^2: shift by -u_scale ln(sy) / (n-1)
-  const double lnsy = 0.36651292058166432701 - log(k2d);  // ln(log2 e) - ln k^2
-  c.uy1 = (float)(a.uoc1[0] - a.us1 * lnsy);
-  c.uy2 = (float)(a.uoc1[1] - a.us1 * lnsy);
-  c.uy3 = (float)(a.uoc1[2] - a.us1 * lnsy);
-  c.uy4 = (float)(a.uoc1[3] - a.us1 * lnsy);
-  c.twopiT = (float)a.twopiT;
-  c.sw2 = (float)a.sum_w2;
-  return c;
+  // the host's copy when the scale and mass are host values (plain RHS calls)
+  if (a.kc_host_ok && !a.k_dev && !a.m2_dev) return a.kc_host;
+  const double kd = scale_k(a);
+  return kconst_f32(a, kd, mass2(a, kd));
 }
 template <>
 __device__ __forceinline__ KConst<double> make_kconst<double>(const RhsArgs &a) {
@@ -249,24 +223,51 @@ constexpr int kPreR = 64, kPreN = 8;
 // template tag of the D4_FULL mixed kernel with lambda3 cells (not a public model)
 constexpr int kModelD4FullCell = 100 + FFRG_MODEL_D4_FULL;
 
-// Every thread of a block of the calling grid (blockIdx.x over the grid,
-// blockDim.x threads) must run it: it synchronises the block.
-__device__ __forceinline__ void precompute_body(const RhsArgs &a) {
+// n-independent terms of radial node r (q = L x_r): q^2, weight x measure,
+// k^2 r(x), k^2 rdot(x) and the table position of q^2
+struct RadialNode {
+  double q2, wm, kr, rd, wl;
+  int i0;
+};
+__device__ __forceinline__ RadialNode radial_node(const RhsArgs &a, int r, double L, double k2, double inv_k2) {
+  RadialNode t;
+  const double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q, x = q2 * inv_k2;
+  t.q2 = q2;
+  t.wm = w * (is_d4(a.model) ? q2 * q : q2);
+  double rx, rdx;
+  reg_r_rdot(a.reg, x, rx, rdx);
+  t.kr = k2 * rx;
+  t.rd = k2 * rdx;
+  lerp_pos(q2, a.u_scale, a.u_off, a.n_pts, t.i0, t.wl);
+  return t;
+}
+
+// Finite T: F(n, r) = w q^2 Z rdot k^2 G^2 lambda at the loop frequency of
+// stack row n (>= 0), written to both loop indices that share it: n and -n
+// (bosonic) or -n-1 (fermionic); row of loop index n in radF: n + N + stat.
+__device__ __forceinline__ void radial_F_finite_t(const RhsArgs &a, int n, int r, double q2, double wm, double kr,
+                                                  double rd, int i0, double wl, double m2) {
+  const int row = min(n, a.n_stack - 1);
+  const double Z = lerp_at(a.tab + (size_t)row * a.n_pts, i0, wl);
+  const double Lq = lerp_at(a.tab + ((size_t)a.n_stack + row) * a.n_pts, i0, wl);
+  const double om = a.stat ? (2.0 * n + 1.0) * kPi * a.T : 2.0 * kPi * a.T * n;
+  const double G = 1.0 / (Z * (om * om + q2 + kr) + m2);
+  const double F = wm * (Z * rd) * G * G * Lq;
+  const int nr = a.nr, ip = (a.N + a.stat + n) * nr + r, im = (a.N - n) * nr + r;
+  a.radF[ip] = F;
+  a.radF[im] = F;
+  if (a.radF32) {
+    a.radF32[ip] = (float)F;
+    a.radF32[im] = (float)F;
+  }
+}
+
+// Per-radial part of the precompute, blocks blk, blk + nblk, ... of the
+// kPreR x kPreN blocks; every thread of the calling block must run it (it
+// synchronises the block).
+__device__ __forceinline__ void precompute_radial(const RhsArgs &a, int blk, int nblk) {
   const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
   const double L = a.qmax_over_k * k;
-  // The scalar and flat work starts at the first block without per-radial
-  // work (blocks 0 .. n_rt n_nb - 1 have some), so that no block has both.
-  const int n_phase = ((a.nr + kPreR - 1) / kPreR) * (a.N / kPreN + 1);
-  const int first_free = n_phase % gridDim.x;
-  const int stride = gridDim.x * blockDim.x;
-  const int tid0 = ((blockIdx.x + gridDim.x - first_free) % gridDim.x) * blockDim.x + threadIdx.x;
-  // the main kernel runs after this one (stream order)
-  if (tid0 == 0 && a.work_ctr) *a.work_ctr = 0u;
-  if (a.kconst && (tid0 == 0 || tid0 == 32)) {  // two warps, in parallel
-    KConstPair *kp = (KConstPair *)a.kconst;
-    if (tid0 == 0) kp->f = make_kconst<float>(a);
-    else kp->d = make_kconst<double>(a);
-  }
   // Per-radial factors F(n, r), in blocks of kPreR radial nodes x kPreN
   // stack rows j.  Phase A: the n-independent part of each node (q^2, weight
   // x measure, k^2 r(x), k^2 rdot(x), the table position of q^2) once per
@@ -278,24 +279,18 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
   const int n_rt = (nr + kPreR - 1) / kPreR, n_nb = N / kPreN + 1;
   __shared__ double s_q2[kPreR], s_wm[kPreR], s_kr[kPreR], s_rd[kPreR], s_wl[kPreR];
   __shared__ int s_i0[kPreR];
-  for (int pb = blockIdx.x; pb < n_rt * n_nb; pb += gridDim.x) {
+  for (int pb = blk; pb < n_rt * n_nb; pb += nblk) {
     const int rt = pb % n_rt, nb = pb / n_rt;
     const int r0 = rt * kPreR, rn = min(kPreR, nr - r0);
     __syncthreads();  // the previous block's shared values are no longer read
     for (int i = threadIdx.x; i < rn; i += blockDim.x) {
-      const int r = r0 + i;
-      const double q = L * a.rad_x[r], w = L * a.rad_w[r], q2 = q * q, x = q2 * inv_k2;
-      s_q2[i] = q2;
-      s_wm[i] = w * (is_d4(a.model) ? q2 * q : q2);
-      double rx, rdx;
-      reg_r_rdot(a.reg, x, rx, rdx);
-      s_kr[i] = k2 * rx;
-      s_rd[i] = k2 * rdx;
-      lerp_pos(q2, a.u_scale, a.u_off, a.n_pts, s_i0[i], s_wl[i]);
-      if (nb == 0) {
-        a.radq[r] = q;
-        if (a.radq32) a.radq32[r] = (float)q;
-      }
+      const RadialNode t = radial_node(a, r0 + i, L, k2, inv_k2);
+      s_q2[i] = t.q2;
+      s_wm[i] = t.wm;
+      s_kr[i] = t.kr;
+      s_rd[i] = t.rd;
+      s_i0[i] = t.i0;
+      s_wl[i] = t.wl;
     }
     __syncthreads();
     const int n0 = nb * kPreN, n1 = min(n0 + kPreN, N + 1);
@@ -303,30 +298,69 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
       const int n = n0 + j / rn, i = j - (j / rn) * rn, r = r0 + i;
       const double q2 = s_q2[i], wl = s_wl[i], rd = s_rd[i];
       const int i0 = s_i0[i];
-      double F;
       if (a.model == FFRG_MODEL_FINITE_T) {
-        const int row = min(n, a.n_stack - 1);
-        const double Z = lerp_at(a.tab + (size_t)row * a.n_pts, i0, wl);
-        const double Lq = lerp_at(a.tab + ((size_t)a.n_stack + row) * a.n_pts, i0, wl);
-        const double om = a.stat ? (2.0 * n + 1.0) * kPi * a.T : 2.0 * kPi * a.T * n;
-        const double G = 1.0 / (Z * (om * om + q2 + s_kr[i]) + m2);
-        F = s_wm[i] * (Z * rd) * G * G * Lq;
+        radial_F_finite_t(a, n, r, q2, s_wm[i], s_kr[i], rd, i0, wl, m2);
       } else {
+        double F;
         const double Z = lerp_at(a.tab, i0, wl);
         const double P = q2 + s_kr[i];
         const double G = 1.0 / (Z * P + m2);
         F = s_wm[i] * (Z * rd) * G * G;
         // d F / d Z(q): dR = Z k^2 rdot, G = 1/(Z P + m^2) with P = q^2 + k^2 r
         if (a.radD) a.radD[r] = s_wm[i] * rd * G * G * (1.0 - 2.0 * Z * G * P);
-      }
-      const int ip = (N + a.stat + n) * nr + r, im = (N - n) * nr + r;
-      a.radF[ip] = F;
-      a.radF[im] = F;
-      if (a.radF32) {
-        a.radF32[ip] = (float)F;
-        a.radF32[im] = (float)F;
+        const int ip = (N + a.stat + n) * nr + r, im = (N - n) * nr + r;
+        a.radF[ip] = F;
+        a.radF[im] = F;
+        if (a.radF32) {
+          a.radF32[ip] = (float)F;
+          a.radF32[im] = (float)F;
+        }
       }
     }
+  }
+}
+
+// Finite T, the same factors F(n, r) by warps: warp unit u of a grid takes
+// 32 radial nodes x kRadN stack rows (one node per lane), so that their FP64
+// work (slow on this part) spreads over as many SMs as there are units.
+constexpr int kRadN = 4;
+__device__ __forceinline__ int radial_units(const RhsArgs &a) {
+  return ((a.nr + 31) / 32) * ((a.N + 1 + kRadN - 1) / kRadN);
+}
+__device__ __forceinline__ void radial_unit(const RhsArgs &a, int u, int lane) {
+  const int n_rb = (a.nr + 31) / 32, rb = u % n_rb, n0 = (u / n_rb) * kRadN;
+  const int r = rb * 32 + lane;
+  if (r >= a.nr) return;
+  const double k = scale_k(a), k2 = k * k, inv_k2 = 1.0 / k2, m2 = mass2(a, k);
+  const RadialNode t = radial_node(a, r, a.qmax_over_k * k, k2, inv_k2);
+  for (int n = n0; n < min(n0 + kRadN, a.N + 1); ++n) radial_F_finite_t(a, n, r, t.q2, t.wm, t.kr, t.rd, t.i0, t.wl, m2);
+}
+
+// Every thread of a block of the calling grid (blockIdx.x over the grid,
+// blockDim.x threads) must run it: it synchronises the block.
+// radial = false (the single-launch mixed finite-T RHS): neither the
+// per-radial blocks nor the FP64 constants, which that kernel does not read.
+__device__ __forceinline__ void precompute_body(const RhsArgs &a, bool radial = true) {
+  const double k = scale_k(a), k2 = k * k;
+  // The scalar and flat work starts at the first block without per-radial
+  // work (blocks 0 .. n_rt n_nb - 1 have some), so that no block has both.
+  const int n_phase = ((a.nr + kPreR - 1) / kPreR) * (a.N / kPreN + 1);
+  const int first_free = n_phase % gridDim.x;
+  const int stride = gridDim.x * blockDim.x;
+  const int tid0 = ((blockIdx.x + gridDim.x - first_free) % gridDim.x) * blockDim.x + threadIdx.x;
+  // the main kernel runs after this one (stream order)
+  if (tid0 == 0 && a.work_ctr) *a.work_ctr = 0u;
+  if (a.kconst && (tid0 == 0 || (tid0 == 32 && radial))) {  // two warps, in parallel
+    KConstPair *kp = (KConstPair *)a.kconst;
+    if (tid0 == 0) kp->f = make_kconst<float>(a);
+    else kp->d = make_kconst<double>(a);
+  }
+  if (radial) precompute_radial(a, blockIdx.x, gridDim.x);
+  // radial nodes q_r = qmax k x_r
+  for (int r = tid0; r < a.nr; r += stride) {
+    const double q = a.qmax_over_k * k * a.rad_x[r];
+    a.radq[r] = q;
+    if (a.radq32) a.radq32[r] = (float)q;
   }
   // FP32 tables; the Z table (table 0, every stack row) carries the factor
   // k^2 ln 2 of the FP32 propagator form.  d=3, d=4: rows in line form
@@ -399,7 +433,14 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
   if (a.ext_done)
     for (int i = tid0; i < a.n_ext; i += stride) a.ext_done[i] = 0u;
   // per-external-point constants used by every work item of the main kernels
-  for (int i = tid0; i < a.n_ext_p; i += stride) a.ext_pd[i] = ext_momentum(a, i);
+  {
+    // one FP64 exp per warp, the warps taken across CTAs first (warp w of CTA
+    // b is unit w G + b), so that no SM's FP64 pipe gets many of them
+    const int cta = tid0 / blockDim.x, lane = threadIdx.x & 31, nwb = blockDim.x >> 5;
+    const int unit = (threadIdx.x >> 5) * gridDim.x + cta;
+    if (lane == 0)
+      for (int i = unit; i < a.n_ext_p; i += nwb * gridDim.x) a.ext_pd[i] = ext_momentum(a, i);
+  }
   if (is_d4(a.model)) {
     for (int j = tid0; j < a.n_ext_ang; j += stride) {
       const double c = a.psi_x[j];
@@ -483,7 +524,7 @@ __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S)
   for (int i = threadIdx.x; i < a.na1; i += blockDim.x) {
     double c = a.a1_x[i];
     S.c1[i] = (T)c;
-    S.s1[i] = (T)sqrt(fmax(0.0, 1.0 - c * c));
+    if (is_d4(a.model)) S.s1[i] = (T)sqrt(fmax(0.0, 1.0 - c * c));   // FP64: slow on this part, d=4 only
     S.w1[i] = (T)a.a1_w[i];
   }
   for (int i = threadIdx.x; i < a.na2; i += blockDim.x) {
@@ -781,29 +822,59 @@ __device__ __forceinline__ void ftk_rows(const RhsArgs &a, const RhsArgs *sa, co
   }
 }
 
+// Barrier of a group of threads of the block: the whole block (id 0), or the
+// gsize threads of named barrier id (1..15).
+__device__ __forceinline__ void group_sync(int id, int gsize) {
+  if (id == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(gsize) : "memory");
+}
+
 // I(m, p) of external point e = (ip, m) from K and the radial factors, by a
-// whole block in a fixed order: thread t takes the terms (n, r) = t,
-// t + blockDim, ... of the nfreq x n_rad terms (n major), accumulating in the
-// precision's RowAcc; each warp reduces with its tree, thread 0 adds the warp
-// sums in order (valid in thread 0).  Every thread of the block must call it.
+// group of gsize threads (gtid = thread index in the group; the block with
+// bar_id 0, else named barrier bar_id) in a fixed order: warp w of the group
+// takes the frequency rows w, w + nw, ... (K row of the shifted frequency
+// n + m, contiguous in r), four at a time, lane l the radial nodes l, l + 32,
+// ... of each, accumulating in the precision's RowAcc; each warp reduces with
+// its tree, thread 0 of the group adds the warp sums in order (valid there).
+// Every thread of the group must call it; red holds gsize/32 doubles.
+
 template <typename T>
-__device__ __forceinline__ double ft_contract(const RhsArgs &a, int e, double *red) {
+__device__ __forceinline__ double ft_contract(const RhsArgs &a, int e, double *red, int gtid, int gsize, int bar_id) {
   const int nm = a.n_ext_ang, ip = e / nm, m = e - ip * nm, nr = a.nr;
-  const int n_lo = -a.N - a.stat, total = a.nfreq * nr;
+  const int n_lo = -a.N - a.stat;
+  const int lane = gtid & 31, nw = gsize >> 5;
   const T *K = (const T *)a.kbuf;
+  auto krow = [&](int row) {   // K row of the shifted frequency of loop index row + n_lo
+    return K + ((size_t)stack_index(a.stat, row + n_lo + m) * a.n_ext_p + ip) * nr;
+  };
   RowAcc<T> acc;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int row = i / nr, r = i - row * nr;   // radF index row * nr + r = i
-    const T *Kr = K + ((size_t)stack_index(a.stat, row + n_lo + m) * a.n_ext_p + ip) * nr;
-    acc.add(radial_F<T>(a, i), Kr[r]);
+  int row = gtid >> 5;
+  // four rows at a time: their eight loads per node are in flight together
+  for (; row + 3 * nw < a.nfreq; row += 4 * nw) {
+    const T *K0 = krow(row), *K1 = krow(row + nw), *K2 = krow(row + 2 * nw), *K3 = krow(row + 3 * nw);
+    const int o = row * nr, dn = nw * nr;   // radF rows of the four loop indices
+    for (int r = lane; r < nr; r += 32) {
+      const T k0 = __ldcg(K0 + r), k1 = __ldcg(K1 + r), k2 = __ldcg(K2 + r), k3 = __ldcg(K3 + r);
+      const T f0 = radial_F<T>(a, o + r), f1 = radial_F<T>(a, o + dn + r);
+      const T f2 = radial_F<T>(a, o + 2 * dn + r), f3 = radial_F<T>(a, o + 3 * dn + r);
+      acc.add(f0, k0);
+      acc.add(f1, k1);
+      acc.add(f2, k2);
+      acc.add(f3, k3);
+    }
+  }
+  for (; row < a.nfreq; row += nw) {
+    const T *Kr = krow(row);
+    const int o = row * nr;
+    for (int r = lane; r < nr; r += 32) acc.add(radial_F<T>(a, o + r), __ldcg(Kr + r));
   }
   const double w = acc.item_sum();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
-  __syncthreads();
+  if (lane == 0) red[gtid >> 5] = w;
+  group_sync(bar_id, gsize);
   double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[j];
-  __syncthreads();
+  if (gtid == 0)
+    for (int j = 0; j < nw; ++j) t += red[j];
+  group_sync(bar_id, gsize);
   return t;
 }
 
@@ -1330,10 +1401,116 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
   __shared__ double red[kThreads / 32];
   if (skipped(a)) return;
-  const double t = ft_contract<T>(a, blockIdx.x, red);
+  const double t = ft_contract<T>(a, blockIdx.x, red, threadIdx.x, blockDim.x, 0);
   if (threadIdx.x == 0) write_output(a, blockIdx.x, t);
 }
 
+// Finite T, mixed, one flow: precompute, K rows and contraction in one
+// cooperative launch (every CTA resident), so that the RHS pays one launch
+// and two grid barriers instead of three kernels and two kernel boundaries.
+// One 1024-thread CTA per SM: the same warps as four 256-thread CTAs, a
+// quarter of the barrier arrivals and of the table copies.
+// Phase 0: the precompute's flat part (FP32 tables, scale constants, radial
+// nodes, external momenta) spread over the grid, so that its FP64 work
+// (slow on this part) is done once, not once per CTA.  Phase 1: each CTA
+// stages the FP32 tables and its warps take K rows, except warp 1 of the
+// last CTAs, which computes the radial factors F(n, r) of the contraction.
+// Phase 2: the outputs, one external point per CTA at a time.  The values
+// are those of the three-launch path, bit for bit.
+// Grid counters c[0..3]: K-row items, barrier arrivals (monotonic), arrivals
+// before this launch, finished CTAs.  The last CTA to finish resets c[0] and
+// c[3] and records c[1] in c[2]; since every CTA finishes (each wait is
+// bounded), a launch whose barrier timed out still leaves the next launch's
+// counters consistent.
+// Grid barrier in two halves: every CTA arrives (thread 0, after the block's
+// writes), and waits later; a CTA may work between the two.
+__device__ __forceinline__ void grid_arrive(unsigned *arrive) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(arrive, 1u);
+  }
+}
+__device__ __forceinline__ bool grid_wait(const unsigned *arrive, unsigned target, unsigned *status, int *s_ok) {
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const long long t0 = clock64();
+    while ((int)(*(volatile const unsigned *)arrive - target) < 0) {
+      if (clock64() - t0 > kWaitCycles) {
+        ok = 0;
+        raise_status(status, kStatusTimeout);
+        break;
+      }
+    }
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kThreadsWide, 1) ft_single_kernel(RhsArgs a) {
+  if (skipped(a)) return;  // uniform over the grid: no counter is touched
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ RhsArgs sa;  // for the out-of-line near-pole path
+  __shared__ uint64_t bar;
+  __shared__ unsigned s_base;
+  __shared__ int s_ok;
+  __shared__ double red[kThreadsWide / 32];
+  unsigned *cnt = a.fused_ctr;
+  if (threadIdx.x == 0) {
+    sa = a;
+    s_base = *(volatile unsigned *)(cnt + 2);
+  }
+  const int lane = threadIdx.x & 31;
+  precompute_body(a, false);
+  grid_arrive(cnt + 1);
+  bool ok = grid_wait(cnt + 1, s_base + gridDim.x, a.status, &s_ok);
+  // the FP32 tables by TMA, as in rhs_main: phase 0 wrote them through the
+  // generic proxy, the bulk copy reads them through the async proxy
+  if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  SmemLayout<float> S(smem, a);
+  ok = main_prologue<float>(a, S, &bar) && ok;
+  const KConst<float> kc = load_kconst<float>(a);
+  const bool pole = pole_possible<float>(a, S, kc);
+  // The radial factors of the contraction: warp 1 of the last CTAs, one warp
+  // unit each (FP64 work spread over SMs) instead of K rows, hidden behind
+  // the K rows of the other warps; the grid has one warp more per unit.
+  const bool radial_warp = (threadIdx.x >> 5) == 1 && gridDim.x - 1 - blockIdx.x < (unsigned)radial_units(a);
+  if (radial_warp)
+    for (int u = gridDim.x - 1 - blockIdx.x; u < radial_units(a); u += gridDim.x) radial_unit(a, u, lane);
+  else if (ok)   // a CTA whose staging or barrier timed out leaves its rows to the others
+    for (;;) {
+      int d = 0;
+      if (lane == 0) d = (int)atomicAdd(cnt, 1u);
+      d = __shfl_sync(0xffffffffu, d, 0);
+      if (d >= a.n_items) break;
+      const int outer = d / a.n_chunks, c = d - outer * a.n_chunks;
+      if (pole) ftk_rows<float, true>(a, &sa, S, kc, outer, c, lane);
+      else ftk_rows<float, false>(a, &sa, S, kc, outer, c, lane);
+    }
+  grid_arrive(cnt + 1);
+  ok = grid_wait(cnt + 1, s_base + 2u * gridDim.x, a.status, &s_ok) && ok;
+  // the outputs by 256-thread groups, four per CTA at once (named barriers
+  // 1..4): the arithmetic order of ft_contract_kernel's blocks
+  if (ok) {
+    const int g = threadIdx.x / kThreads, ng = blockDim.x / kThreads, gtid = threadIdx.x - g * kThreads;
+    for (int e = blockIdx.x * ng + g; e < a.n_ext; e += gridDim.x * ng) {
+      const double t = ft_contract<float>(a, e, red + g * (kThreads / 32), gtid, kThreads, 1 + g);
+      if (gtid == 0) write_output(a, e, t);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(cnt + 3, 1u) == gridDim.x - 1) {
+      cnt[0] = 0u;
+      cnt[2] = *(volatile unsigned *)(cnt + 1);
+      cnt[3] = 0u;
+      __threadfence();
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 constexpr size_t kMaxDynSmem = kMaxDynSmemBytes;
@@ -1357,6 +1534,47 @@ static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int 
   const int ctas = (items + threads / 32 - 1) / (threads / 32);
   *grid = std::max(1, std::min(ctas, per_sm * ctx->num_sms));
   return FFRG_OK;
+}
+
+// The single-launch finite-T RHS: every CTA of a cooperative launch is
+// resident, so its grid barrier completes.  kNoSingleLaunch when the device
+// cannot launch cooperatively (the caller then takes the three launches).
+constexpr int kNoSingleLaunch = -100;
+static int launch_ft_single(ffrg_ctx *ctx, Plan *pl, const RhsArgs &a, size_t smem, cudaStream_t s) {
+  if (pl->grid_single == 0) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (!coop) {
+      pl->grid_single = -1;
+    } else {
+      // one warp per K-row item and one per radial unit (32 nodes x kRadN rows)
+      const int units = ((a.nr + 31) / 32) * ((a.N + 1 + kRadN - 1) / kRadN);
+      int st = persistent_grid(ctx, ft_single_kernel, smem, a.n_items + units, &pl->grid_single, kThreadsWide);
+      if (st) return st;
+    }
+  }
+  if (pl->grid_single < 0) return kNoSingleLaunch;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(pl->grid_single);
+  cfg.blockDim = dim3(kThreadsWide);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool prof = ctx->profiling && cap == cudaStreamCaptureStatusNone &&
+                    ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
+  if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, ft_single_kernel, a);
+  if (prof) {
+    cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
+    ctx->prof_used++;
+  }
+  return set_cuda_error(ctx, e, "single-launch finite-T RHS");
 }
 
 int precompute_blocks(const RhsArgs &a, int cap) {
@@ -1415,6 +1633,10 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
     ctx->last_error = "plan without work counters, FP32 radial nodes or constant block";
     return FFRG_EINVAL;
   }
+  if (mixed && a.model == FFRG_MODEL_FINITE_T && contract && a.fused_ctr) {
+    st = launch_ft_single(ctx, pl, a, smem, s);
+    if (st != kNoSingleLaunch) return st;   // else the three launches below
+  }
   if (grid == 0) {
     st = persistent_grid(ctx, kern, smem, a.n_items, &grid, threads);
     if (st) return st;
@@ -1462,7 +1684,7 @@ __global__ void __launch_bounds__(kThreads) batched_finalize_kernel(const RhsArg
   const int e = blockIdx.x;
   if (skipped(a) || e >= a.n_ext) return;   // uniform over the block
   if (a.model == FFRG_MODEL_FINITE_T) {
-    const double t = ft_contract<float>(a, e, red);
+    const double t = ft_contract<float>(a, e, red, threadIdx.x, blockDim.x, 0);
     if (threadIdx.x == 0) write_output(a, e, t);
   } else if (threadIdx.x < 32) {
     const double t = sum_partials(a, e, threadIdx.x);

@@ -277,6 +277,7 @@ static int slot_setup(Server &S, int si) {
   e = cudaStreamSynchronize(S.io);
   if (e != cudaSuccess) return set_cuda_error(&S.lc, e, "serve upload sync");
   fill_args(&pl, &r->pb, &r->td, (const double *)(b + L.o_tab), r->Lambda, sl.ra);
+  sl.ra.fused_ctr = nullptr;   // batched kernels only
   sl.ra.out = (double *)(b + L.o_raw);
   sl.ra.status = S.status_dev;
   sl.ra.k_dev = &ctl->k_stage;

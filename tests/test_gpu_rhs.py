@@ -394,3 +394,25 @@ def test_repeat_is_bitwise_deterministic(ctx):
     a = _run(ctx, wl, 0.9, ffrg.MIXED)
     b = _run(ctx, wl, 0.9, ffrg.MIXED)
     assert np.array_equal(a, b)
+
+
+def test_finite_t_single_launch_counters_across_calls_and_shapes(ctx):
+    """The mixed finite-T RHS runs as one cooperative launch whose grid
+    counters persist in the plan: many calls in a row, alternating between two
+    plans and two scales, give bitwise the same outputs each time, equal to
+    the oracle within the mixed bound."""
+    import paper_2412_13043_gb300 as ffrg
+    w1 = fi.make_finite_t(seed=61, N=5, T=0.05, n_pts=16, n_ext_p=9, n_ext_m=3, n_rad=40, n_ang=12)
+    w2 = fi.make_finite_t(seed=62, N=2, T=0.1, n_pts=12, n_ext_p=4, n_ext_m=2, n_rad=33, n_ang=7, fermionic=True)
+    first = {}
+    for it in range(6):
+        for name, wl in (("b", w1), ("f", w2)):
+            for k in (1.1, 0.3):
+                got = _run(ctx, wl, k, ffrg.MIXED)
+                key = (name, k)
+                if key not in first:
+                    first[key] = got
+                    ref = oracle.rhs(wl.problem, wl.tables, k)
+                    assert np.max(np.abs(got - ref) / np.abs(ref)) < MIXED_TOL, key
+                else:
+                    assert np.array_equal(got, first[key]), (it, key)
