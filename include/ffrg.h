@@ -226,9 +226,22 @@ FFRG_API double ffrg_evals(const ffrg_problem *pb);
  * Errors: FFRG_EINVAL for a bad problem, tables of another shape, or, in mixed
  * precision, FP32 tables and rules that do not fit in shared memory (8 bytes
  * per table node: one FP32 line-form pair, or the (Z, lambda) pair of finite
- * T, plus the angle rules); FFRG_ENOMEM (budget); FFRG_ECUDA. */
+ * T, plus the angle rules; FFRG_MODEL_D4_FULL keeps lambda3 as 32-byte cell
+ * polynomials where those fit and as line-form pairs otherwise); FFRG_ENOMEM
+ * (budget); FFRG_ECUDA. */
 FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_dev,
              int precision, void *stream);
+
+/* ffrg_rhs with the outputs in host memory: the RHS into a device buffer of
+ * the context (allocated on the first call, grown when a larger problem
+ * needs it, freed by ffrg_destroy), then a stream-ordered copy of its
+ * ffrg_n_ext() doubles to out_host.  out_host: caller-owned host memory;
+ * from pinned memory the call returns before the copy has run (synchronise
+ * `stream` before reading), from pageable memory after it.  Calls of one
+ * context on different streams share the device buffer: order them.
+ * Errors: as ffrg_rhs; FFRG_EINVAL for a NULL out_host. */
+FFRG_API int ffrg_rhs_host(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
+                  double *out_host, int precision, void *stream);
 
 /* ffrg_rhs for callers that cannot allocate device memory.  The paper has no
  * counterpart; this is a deployment variant.  It suits, for example, a process

@@ -94,6 +94,7 @@ _SIGS = {
     "ffrg_n_ext": (_I, [ctypes.POINTER(Problem)]),
     "ffrg_evals": (_D, [ctypes.POINTER(Problem)]),
     "ffrg_rhs": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _I, _P]),
+    "ffrg_rhs_host": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _I, _P]),
     "ffrg_rhs_noalloc": (_I, [ctypes.POINTER(Problem), ctypes.POINTER(TableDesc), _P, _D, _P, _I, _P]),
     "ffrg_rhs_adjoint": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _P, _P, _I, _P]),
     "ffrg_ft_states": (_I, [_P, ctypes.POINTER(Problem), _P, _D, _I, _P, _P, _I, _P]),
@@ -306,6 +307,31 @@ class Context:
         code = load().ffrg_rhs(self.handle, ctypes.byref(c), tables.handle, float(k), _dev_ptr(out, "out"),
                                int(precision), _stream_handle(stream))
         _check(self.handle, code, "ffrg_rhs")
+        return out
+
+    def rhs_host(self, pb, tables: Tables, k: float, out=None, precision: int = FP64, stream=None):
+        """One RHS with the outputs in host memory (ffrg_rhs_host): `out` a
+        contiguous float64 CPU tensor (pinned: the copy is asynchronous,
+        synchronise the stream before reading) or numpy array; allocated as a
+        numpy array (pageable: the call returns after the copy) when None."""
+        c = to_problem(pb)
+        ne = load().ffrg_n_ext(ctypes.byref(c))
+        if ne < 0:
+            raise ValueError("bad problem")
+        if out is None:
+            out = np.empty(ne, dtype=np.float64)
+        if hasattr(out, "is_cuda"):
+            import torch
+            if out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != ne:
+                raise ValueError("out must be a contiguous float64 CPU tensor of n_ext values")
+            ptr = out.data_ptr()
+        else:
+            if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size != ne:
+                raise ValueError("out must be a contiguous float64 array of n_ext values")
+            ptr = out.ctypes.data
+        code = load().ffrg_rhs_host(self.handle, ctypes.byref(c), tables.handle, float(k), ptr, int(precision),
+                                    _stream_handle(stream))
+        _check(self.handle, code, "ffrg_rhs_host")
         return out
 
     def rhs_adjoint(self, pb, tables: Tables, k: float, gbar, tbar=None, precision: int = FP64, stream=None):

@@ -532,6 +532,7 @@ int ffrg_destroy(ffrg_ctx *ctx) {
   for (void *p : ctx->owned) cudaFree(p);
   for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
   if (ctx->flow_dev) cudaFree(ctx->flow_dev);
+  if (ctx->host_out_dev) cudaFree(ctx->host_out_dev);
   if (ctx->states_dev) cudaFree(ctx->states_dev);
   if (ctx->flow_host) cudaFreeHost(ctx->flow_host);
   if (ctx->flow_ev) cudaEventDestroy(ctx->flow_ev);
@@ -643,6 +644,28 @@ int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, d
   a.out = out_dev;
   a.status = ctx->status_dev;
   return launch_rhs(ctx, pl, a, precision, (cudaStream_t)stream);
+}
+
+int ffrg_rhs_host(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_host,
+                  int precision, void *stream) {
+  if (!ctx || !pb || !tables || !out_host) return FFRG_EINVAL;
+  const int ne = ffrg_n_ext(pb);
+  if (ne < 0) return FFRG_EINVAL;
+  const size_t bytes = (size_t)ne * sizeof(double);
+  cudaSetDevice(ctx->device);
+  if (ctx->host_out_cap < bytes) {   // grown on demand (cudaFree waits for the work that reads it)
+    dev_free(ctx, ctx->host_out_dev, ctx->host_out_cap);
+    ctx->host_out_dev = nullptr;
+    ctx->host_out_cap = 0;
+    int st = dev_alloc(ctx, &ctx->host_out_dev, bytes);
+    if (st) return st;
+    ctx->host_out_cap = bytes;
+  }
+  int st = ffrg_rhs(ctx, pb, tables, k, (double *)ctx->host_out_dev, precision, stream);
+  if (st) return st;
+  return set_cuda_error(ctx, cudaMemcpyAsync(out_host, ctx->host_out_dev, bytes, cudaMemcpyDeviceToHost,
+                                             (cudaStream_t)stream),
+                        "cudaMemcpyAsync(outputs)");
 }
 
 int ffrg_status_read(ffrg_ctx *ctx, void *stream) {

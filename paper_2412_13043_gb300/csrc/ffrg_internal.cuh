@@ -470,6 +470,9 @@ struct ffrg_ctx {
   // stream and event: kept between calls, grown when a flow needs more
   void *flow_dev = nullptr;
   size_t flow_cap = 0;
+  // ffrg_rhs_host's device outputs, grown on demand
+  void *host_out_dev = nullptr;
+  size_t host_out_cap = 0;
   void *flow_host = nullptr;
   cudaStream_t flow_stream = nullptr;
   cudaEvent_t flow_ev = nullptr;

@@ -433,14 +433,10 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a, bool radial = 
   if (a.ext_done)
     for (int i = tid0; i < a.n_ext; i += stride) a.ext_done[i] = 0u;
   // per-external-point constants used by every work item of the main kernels
-  {
-    // one FP64 exp per warp, the warps taken across CTAs first (warp w of CTA
-    // b is unit w G + b), so that no SM's FP64 pipe gets many of them
-    const int cta = tid0 / blockDim.x, lane = threadIdx.x & 31, nwb = blockDim.x >> 5;
-    const int unit = (threadIdx.x >> 5) * gridDim.x + cta;
-    if (lane == 0)
-      for (int i = unit; i < a.n_ext_p; i += nwb * gridDim.x) a.ext_pd[i] = ext_momentum(a, i);
-  }
+  // one FP64 exp per value: value i on CTA i mod G, thread i / G, so that a
+  // large grid spreads them over SMs and a small one keeps them in parallel lanes
+  for (int i = tid0 / (int)blockDim.x + gridDim.x * threadIdx.x; i < a.n_ext_p; i += stride)
+    a.ext_pd[i] = ext_momentum(a, i);
   if (is_d4(a.model)) {
     for (int j = tid0; j < a.n_ext_ang; j += stride) {
       const double c = a.psi_x[j];
@@ -1633,7 +1629,13 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
     ctx->last_error = "plan without work counters, FP32 radial nodes or constant block";
     return FFRG_EINVAL;
   }
-  if (mixed && a.model == FFRG_MODEL_FINITE_T && contract && a.fused_ctr) {
+  // the single launch pays where the K rows fill the GPU and the scale is a
+  // host value: measured 45 -> 29 us for 4800 K-row items (N = 16, 576 ext),
+  // but 3-4 us slower for the serving mix's few hundred items, and in flows
+  // (k on the device: the FP32 constants then cost an FP64 chain in phase 0)
+  constexpr int kSingleLaunchItems = 152 * (kThreads / 32);
+  if (mixed && a.model == FFRG_MODEL_FINITE_T && contract && a.fused_ctr && !a.k_dev && !a.m2_dev &&
+      a.n_items >= kSingleLaunchItems) {
     st = launch_ft_single(ctx, pl, a, smem, s);
     if (st != kNoSingleLaunch) return st;   // else the three launches below
   }

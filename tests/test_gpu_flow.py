@@ -97,8 +97,6 @@ def test_finite_t_frozen_flow_small(ctx):
     y, st = _gpu_flow(ctx, wl, ffrg.FP64)
     assert st["status"] == 0
     assert _rel(y, truth) < ENDPOINT_TOL
-    # mixed: every RHS is one cooperative launch (precompute, K rows and
-    # contraction behind one grid barrier), replayed from the flow's graph
     y32, st32 = _gpu_flow(ctx, wl, ffrg.MIXED)
     assert st32["status"] == 0
     assert _rel(y32, truth) < MIXED_ENDPOINT_TOL

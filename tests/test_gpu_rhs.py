@@ -396,14 +396,37 @@ def test_repeat_is_bitwise_deterministic(ctx):
     assert np.array_equal(a, b)
 
 
-def test_finite_t_single_launch_counters_across_calls_and_shapes(ctx):
-    """The mixed finite-T RHS runs as one cooperative launch whose grid
-    counters persist in the plan: many calls in a row, alternating between two
-    plans and two scales, give bitwise the same outputs each time, equal to
-    the oracle within the mixed bound."""
+def test_rhs_host_outputs_equal_device_outputs(ctx):
+    """ffrg_rhs_host: the same kernels, the outputs copied to host memory
+    (pinned and pageable), bitwise equal to ffrg_rhs; a larger problem after a
+    smaller one grows the context's device buffer."""
+    import torch
+
     import paper_2412_13043_gb300 as ffrg
-    w1 = fi.make_finite_t(seed=61, N=5, T=0.05, n_pts=16, n_ext_p=9, n_ext_m=3, n_rad=40, n_ang=12)
-    w2 = fi.make_finite_t(seed=62, N=2, T=0.1, n_pts=12, n_ext_p=4, n_ext_m=2, n_rad=33, n_ang=7, fermionic=True)
+    for wl, k in ((fi.make_d3(seed=5, n_pts=16, n_ext_p=7, n_rad=8, n_ang=6), 0.8),
+                  (fi.make_d4(seed=6, n_pts=32, n_ext_ang=3, n_rad=16, n_ang1=8, n_ang2=4), 0.6)):
+        tabs = ctx.tables(wl.problem, wl.tables)
+        for prec in (ffrg.FP64, ffrg.MIXED):
+            dev = ctx.rhs(wl.problem, tabs, k, precision=prec).cpu().numpy()
+            pinned = torch.empty(wl.problem.n_ext(), dtype=torch.float64).pin_memory()
+            ctx.rhs_host(wl.problem, tabs, k, out=pinned, precision=prec)
+            torch.cuda.synchronize()
+            pageable = ctx.rhs_host(wl.problem, tabs, k, precision=prec)
+            assert np.array_equal(pinned.numpy(), dev) and np.array_equal(pageable, dev)
+        tabs.free()
+    with pytest.raises(ValueError):
+        ctx.rhs_host(wl.problem, tabs, 0.5, out=np.empty(3))
+
+
+def test_finite_t_single_launch_counters_across_calls_and_shapes(ctx):
+    """With at least 1216 K-row items (here 1248 and 1260: (N + M) n_p x two
+    radial chunks) the mixed finite-T RHS runs as one cooperative launch whose
+    grid counters persist in the plan: many calls in a row, alternating
+    between two plans and two scales, give bitwise the same outputs each time,
+    equal to the oracle within the mixed bound."""
+    import paper_2412_13043_gb300 as ffrg
+    w1 = fi.make_finite_t(seed=61, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4, n_rad=64, n_ang=4)
+    w2 = fi.make_finite_t(seed=62, N=6, T=0.1, n_pts=12, n_ext_p=70, n_ext_m=3, n_rad=40, n_ang=3, fermionic=True)
     first = {}
     for it in range(6):
         for name, wl in (("b", w1), ("f", w2)):

@@ -57,6 +57,28 @@ def test_noalloc_matches_rhs_on_two_calls_in_a_row():
         ctx.close()
 
 
+def test_noalloc_matches_the_single_launch_rhs():
+    """A finite-T problem with 1248 K-row items: ffrg_rhs takes its mixed RHS
+    in one cooperative launch, ffrg_rhs_noalloc in the three launches
+    (precompute, K rows, contraction); the arithmetic is the same, so the
+    outputs agree bit for bit."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2412_13043_gb300 as ffrg
+    lib = ffrg.load()
+    ctx = ffrg.Context(0)
+    try:
+        wl = fi.make_finite_t(seed=63, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4, n_rad=64, n_ang=6)
+        for k in (1.3, 0.2):
+            got = _noalloc(lib, ffrg, wl, k, ffrg.MIXED)
+            ref = _allocating(ffrg, ctx, wl, k, ffrg.MIXED)
+            assert np.all(np.isfinite(got))
+            assert np.array_equal(got, ref), float(np.max(np.abs(got - ref) / np.abs(ref)))
+    finally:
+        ctx.close()
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
