@@ -37,7 +37,7 @@ struct StatesScratch {
   uint16_t *A, *B;
   float *part;
   int *e_row, *e_col;
-  int2 *pass_ij;
+  int4 *pass_tab;
 };
 
 // BF16 bits of a small integer held in a float (exact: at most 8 significant bits)
@@ -286,7 +286,7 @@ extern "C" int ffrg_ft_states(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_
   // scratch, kept by the context and grown on demand (256-byte segments):
   // pass table (room for 12 K ranges) | A slices | B slices | pass sums | scales
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t o_A = al((size_t)n_pairs * 12 * sizeof(int2));
+  const size_t o_A = al((size_t)n_pairs * 12 * sizeof(int4));
   const size_t o_B = o_A + al(kSlices * a_slice * 2), o_part = o_B + al(kSlices * b_slice * 2);
   const size_t o_er = o_part + al((size_t)passes * rows_pad * cols_pad * 4);
   const size_t o_ec = o_er + al((size_t)rows_pad * 4);
@@ -302,15 +302,18 @@ extern "C" int ffrg_ft_states(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_
   }
   unsigned char *base = (unsigned char *)ctx->states_dev;
   StatesScratch sc{(uint16_t *)(base + o_A), (uint16_t *)(base + o_B), (float *)(base + o_part),
-                   (int *)(base + o_er), (int *)(base + o_ec), (int2 *)base};
+                   (int *)(base + o_er), (int *)(base + o_ec), (int4 *)base};
   if (ctx->states_chunks != n_chunks) {
-    // slice pair of each pass: pair_index order, K ranges innermost (uploaded
-    // when the number of K ranges changes)
-    std::vector<int2> ij((size_t)passes);
-    for (int l = 0; l < kSlices; ++l)
-      for (int i = 0; i <= l; ++i)
-        for (int c = 0; c < n_chunks; ++c) ij[(size_t)pair_index(i, l - i) * n_chunks + c] = make_int2(i, l - i);
-    st = set_cuda_error(ctx, cudaMemcpyAsync(sc.pass_ij, ij.data(), ij.size() * sizeof(int2),
+    // the pass table, one slot per CTA z: slice pair (i, j), its output pass
+    // (pair_index order, K ranges innermost) and K range.  Slots run in order
+    // of i, so CTAs that run together read the same A slice (uploaded when the
+    // number of K ranges changes)
+    std::vector<int4> ij((size_t)passes);
+    size_t z = 0;
+    for (int i = 0; i < kSlices; ++i)
+      for (int j = 0; i + j < kSlices; ++j)
+        for (int c = 0; c < n_chunks; ++c) ij[z++] = make_int4(i, j, pair_index(i, j) * n_chunks + c, c);
+    st = set_cuda_error(ctx, cudaMemcpyAsync(sc.pass_tab, ij.data(), ij.size() * sizeof(int4),
                                              cudaMemcpyHostToDevice, s), "ffrg_ft_states pass table");
     // from pageable memory: the copy must have read ij before it goes away
     if (!st) st = set_cuda_error(ctx, cudaStreamSynchronize(s), "ffrg_ft_states pass table");
@@ -346,7 +349,7 @@ extern "C" int ffrg_ft_states(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_
 
   st = ensure_smem_limit(ctx, (const void *)umma::slice_pair_gemm, umma::kSmemBytes);
   if (st) return st;
-  umma::GemmArgs gg{sc.A, sc.B, sc.part, sc.pass_ij, m_tiles, n_tiles, k_tiles, kt_chunk, n_chunks,
+  umma::GemmArgs gg{sc.A, sc.B, sc.part, sc.pass_tab, m_tiles, n_tiles, k_tiles, kt_chunk, n_chunks,
                     ctx->status_dev};
   const bool prof = ctx->profiling && ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
   if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);

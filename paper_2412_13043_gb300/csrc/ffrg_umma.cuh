@@ -10,15 +10,15 @@
 //
 // Shared-memory operand layout (no swizzle, K-major, the canonical
 // "interleaved" form of the UMMA shared-memory descriptor): a tile of R rows x
-// 64 K-elements (BF16) is made of 8 x 8 core matrices of 128 contiguous bytes
+// kBK K-elements (BF16) is made of 8 x 8 core matrices of 128 contiguous bytes
 // (8 rows of 16 bytes); core matrices adjacent in the row direction are 128
 // bytes apart (stride byte offset, SBO) and those adjacent in K are R x 16
 // bytes apart (leading byte offset, LBO).  Global memory holds the slices
 // already in this tile order, so one bulk copy moves a whole tile.
 //
 // Roles of the 4 warps: warp 0 lane 0 issues the bulk copies of each K-tile
-// (A: 16 KB, B: 32 KB) into a 2-stage ring; warp 1 allocates 256 columns of
-// tensor memory and lane 0 issues the MMAs (M = 128, N = 256, K = 16 each, four
+// (A: 8 KB, B: 16 KB) into a 4-stage ring; warp 1 allocates 256 columns of
+// tensor memory and lane 0 issues the MMAs (M = 128, N = 256, K = 16 each, two
 // per K-tile) and commits each stage back to the producer; after the last
 // commit all 4 warps read their 32 accumulator lanes (tcgen05.ld) and store
 // the rows.  Every wait is bounded; a wait that gives up sets the status word
@@ -35,8 +35,8 @@ constexpr int kBM = 128;          // output rows per tile (A rows)
 constexpr int kBN = 256;          // output columns per tile (B rows: states)
 constexpr int kBK = 32;           // K-elements per stage
 constexpr int kStages = 4;
-constexpr int kTileA = kBM * kBK * 2;   // 16 KB
-constexpr int kTileB = kBN * kBK * 2;   // 32 KB
+constexpr int kTileA = kBM * kBK * 2;   // 8 KB
+constexpr int kTileB = kBN * kBK * 2;   // 16 KB
 constexpr int kStageBytes = kTileA + kTileB;
 constexpr int kSmemBytes = kStages * kStageBytes;   // 96 KB: two CTAs per SM
 constexpr int kTmemCols = 256;
@@ -45,16 +45,16 @@ constexpr int kMaxExactK = 16384;  // K-elements whose slice products sum exactl
 constexpr unsigned kStatusTimeoutBit = 2u;
 constexpr long long kWaitLimit = 4000000000LL;   // clock cycles (about 2 s)
 
-// element offset of (row r, K-element k) inside a rows x 64 tile
+// element offset of (row r, K-element k) inside a rows x kBK tile
 __host__ __device__ inline int tile_offset(int r, int k, int rows) {
   return (k >> 3) * (rows * 8) + (r >> 3) * 64 + (r & 7) * 8 + (k & 7);
 }
 
 struct GemmArgs {
-  const uint16_t *A;   // BF16 bits, slices [nsl][m_tiles][k_tiles][128 x 64 tile]
-  const uint16_t *B;   // BF16 bits, slices [nsl][n_tiles][k_tiles][256 x 64 tile]
+  const uint16_t *A;   // BF16 bits, slices [nsl][m_tiles][k_tiles][128 x kBK tile]
+  const uint16_t *B;   // BF16 bits, slices [nsl][n_tiles][k_tiles][256 x kBK tile]
   float *part;         // [passes][m_tiles * 128][n_tiles * 256], exact sums per pass
-  const int2 *pass_ij; // slice pair (i, j) of each pass
+  const int4 *pass_tab; // per CTA z: slice pair (i, j), output pass, K range
   int m_tiles, n_tiles, k_tiles;
   int kt_per_chunk, n_chunks;  // K-tiles per pass and K ranges per slice pair
   unsigned *status;
@@ -147,16 +147,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // One pass per CTA: blockIdx.x = output column tile, blockIdx.y = output row
-// tile, blockIdx.z = pass (slice pair x K range).
+// tile, blockIdx.z = slot of the pass table (slice pair, its output pass and
+// K range; slots that run together share an A slice).
 __global__ void __launch_bounds__(kThreadsGemm, 1) slice_pair_gemm(GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag, issued, consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tn = blockIdx.x, tm = blockIdx.y, pass = blockIdx.z;
-  const int2 ij = g.pass_ij[pass];
-  const int chunk = pass % g.n_chunks;
+  const int tn = blockIdx.x, tm = blockIdx.y;
+  const int4 pt = g.pass_tab[blockIdx.z];
+  const int2 ij = make_int2(pt.x, pt.y);
+  const int pass = pt.z, chunk = pt.w;
   const int kt0 = chunk * g.kt_per_chunk;
   const int nkt = min(g.kt_per_chunk, g.k_tiles - kt0);
 
@@ -244,10 +246,12 @@ __global__ void __launch_bounds__(kThreadsGemm, 1) slice_pair_gemm(GemmArgs g) {
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
       float4 *d4 = reinterpret_cast<float4 *>(dst + c * 32);
+      // streaming stores: the pass sums are read once, by the combine kernel;
+      // evict-first keeps the operand slices in L2 for the other passes
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        d4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
-                            __uint_as_float(r[4 * q + 3]));
+        __stcs(d4 + q, make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                   __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])));
     }
   }
   fence_before();
