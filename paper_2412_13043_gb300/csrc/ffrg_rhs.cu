@@ -89,7 +89,9 @@ __device__ __forceinline__ int stack_index(int stat, int n) { return stat ? (n >
 
 // K row of stack row jk (finite T): frequency of row jk, table row min(jk, n_stack-1)
 __device__ __noinline__ float pole_ftk(const RhsArgs *a, int ip, int jk, int r, int j) {
-  const double p = ext_momentum(*a, ip), q = a->radq[r], c = a->a1_x[j];
+  // q from its definition (the value the precompute stores in radq): the
+  // single-launch RHS runs no precompute
+  const double p = ext_momentum(*a, ip), q = a->qmax_over_k * scale_k(*a) * a->rad_x[r], c = a->a1_x[j];
   const int srow = min(jk, a->n_stack - 1);
   const double om = kPi * a->T * (2.0 * (double)jk + (a->stat ? 1.0 : 0.0));
   return pole_prop(a, a->tab + (size_t)srow * a->n_pts, q * q + p * p + 2.0 * q * p * c, om * om);
@@ -790,18 +792,21 @@ __device__ __forceinline__ void zl_lookup(const float2 *tab, const RhsArgs &a, i
 // instead of (2N+1) M angular sums per (p, r).
 template <typename T, bool POLE>
 __device__ __forceinline__ void ftk_rows(const RhsArgs &a, const RhsArgs *sa, const SmemLayout<T> &S,
-                                         const KConst<T> &kc, int outer, int c, int lane) {
+                                         const KConst<T> &kc, int outer, int c, int lane,
+                                         const T *q_loc = nullptr, const T *p_loc = nullptr) {
   const T us = kc.us, uy1 = kc.uy1, sy = kc.sy;
   const int np = a.n_pts, na1 = a.na1, nr = a.nr;
   const int jk = outer / a.n_ext_p, ip = outer - jk * a.n_ext_p;
   const int srow = min(jk, a.n_stack - 1);
   const T om = kc.twopiT * ((T)jk + (T)(a.stat ? 0.5 : 0.0));   // omega_j or nu_j
   const T om2s = om * om * kc.som;
-  const T p = (T)a.ext_pd[ip];
+  // p and q from the precompute's arrays, or (q_loc, p_loc) from the block's
+  // own copies of the same values
+  const T p = p_loc ? p_loc[ip] : (T)a.ext_pd[ip];
   T *K = (T *)a.kbuf + ((size_t)jk * a.n_ext_p + ip) * nr;
   const int r0 = c * a.cr, r1 = min(r0 + a.cr, nr);
   for (int r = r0 + lane; r < r1; r += 32) {
-    const T q = radial_q<T>(a, r);
+    const T q = q_loc ? q_loc[r] : radial_q<T>(a, r);
     const T by = fma(q, q, p * p) * sy, ty = (T)2 * q * p * sy;   // explicit FMAs, as in d3_witem
     T rs = 0;
     if constexpr (sizeof(T) == 4 && !POLE) rs = ftk_row_x2(S, kc, S.tab + (size_t)srow * np, np, na1, om2s, by, ty);
@@ -1403,21 +1408,31 @@ __global__ void __launch_bounds__(kThreads) ft_contract_kernel(RhsArgs a) {
 
 // Finite T, mixed, one flow: precompute, K rows and contraction in one
 // cooperative launch (every CTA resident), so that the RHS pays one launch
-// and two grid barriers instead of three kernels and two kernel boundaries.
+// and one grid barrier instead of three kernels and two kernel boundaries.
 // One 1024-thread CTA per SM: the same warps as four 256-thread CTAs, a
 // quarter of the barrier arrivals and of the table copies.
-// Phase 0: the precompute's flat part (FP32 tables, scale constants, radial
-// nodes, external momenta) spread over the grid, so that its FP64 work
-// (slow on this part) is done once, not once per CTA.  Phase 1: each CTA
-// stages the FP32 tables and its warps take K rows, except warp 1 of the
-// last CTAs, which computes the radial factors F(n, r) of the contraction.
-// Phase 2: the outputs, one external point per CTA at a time.  The values
-// are those of the three-launch path, bit for bit.
+// Phase 1: each CTA builds its inputs itself from the FP64 tables and rules
+// (the FP32 (Z k^2 ln 2, lambda) pairs, the angle rule, q_r and p_i in
+// shared memory; the FP32 scale constants come from the host), which is
+// FP64 work once per SM, and its warps take K rows, except warp 1 of the
+// last CTAs, which computes the radial factors F(n, r) of the contraction in
+// warp units.  Phase 2, after the barrier: the outputs by 256-thread groups.
+// The values are those of the three-launch path, bit for bit.
 // Grid counters c[0..3]: K-row items, barrier arrivals (monotonic), arrivals
 // before this launch, finished CTAs.  The last CTA to finish resets c[0] and
 // c[3] and records c[1] in c[2]; since every CTA finishes (each wait is
 // bounded), a launch whose barrier timed out still leaves the next launch's
 // counters consistent.
+// Single-launch finite-T RHS: shared memory of the FP32 layout (tables and
+// angle rules), then q_r and p_i in FP32 (16-byte aligned regions).
+__host__ __device__ inline size_t single_extra_offset(const RhsArgs &a) {
+  const size_t ang32 = (size_t)a.na1 * 3 + (size_t)a.na2 * 2 + (size_t)4 * ((a.na2 + 1) / 2);
+  return (((size_t)a.tab32_count * 8 + 15) & ~(size_t)15) + ((ang32 * 4 + 15) & ~(size_t)15);
+}
+__host__ __device__ inline size_t single_smem(const RhsArgs &a) {
+  return single_extra_offset(a) + (size_t)4 * (((a.nr + 3) & ~3) + ((a.n_ext_p + 3) & ~3));
+}
+
 // Grid barrier in two halves: every CTA arrives (thread 0, after the block's
 // writes), and waits later; a CTA may work between the two.
 __device__ __forceinline__ void grid_arrive(unsigned *arrive) {
@@ -1449,44 +1464,57 @@ __global__ void __launch_bounds__(kThreadsWide, 1) ft_single_kernel(RhsArgs a) {
   if (skipped(a)) return;  // uniform over the grid: no counter is touched
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ RhsArgs sa;  // for the out-of-line near-pole path
-  __shared__ uint64_t bar;
-  __shared__ unsigned s_base;
   __shared__ int s_ok;
   __shared__ double red[kThreadsWide / 32];
   unsigned *cnt = a.fused_ctr;
+  // arrivals before this launch: thread 0 alone waits at the barriers, so the
+  // value stays in its register and the load overlaps phase 0
+  unsigned base = 0;
   if (threadIdx.x == 0) {
+    base = *(volatile unsigned *)(cnt + 2);
     sa = a;
-    s_base = *(volatile unsigned *)(cnt + 2);
   }
   const int lane = threadIdx.x & 31;
-  precompute_body(a, false);
-  grid_arrive(cnt + 1);
-  bool ok = grid_wait(cnt + 1, s_base + gridDim.x, a.status, &s_ok);
-  // the FP32 tables by TMA, as in rhs_main: phase 0 wrote them through the
-  // generic proxy, the bulk copy reads them through the async proxy
-  if (threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+  // The block's own inputs, the values the precompute would store, from the
+  // FP64 tables and rules (one CTA per SM, so this FP64 work is per SM): the
+  // FP32 (Z k^2 ln 2, lambda) pairs, the angle rule, q_r and p_i, and the
+  // near-pole test on the Z entries as they pass
   SmemLayout<float> S(smem, a);
-  ok = main_prologue<float>(a, S, &bar) && ok;
-  const KConst<float> kc = load_kconst<float>(a);
-  const bool pole = pole_possible<float>(a, S, kc);
+  float *q_loc = (float *)(smem + single_extra_offset(a));
+  float *p_loc = q_loc + ((a.nr + 3) & ~3);
+  const double k = scale_k(a), kh = k * k * 0.6931471805599453094, L = a.qmax_over_k * k;
+  const int z_count = a.n_stack * a.n_pts;
+  int neg = 0;
+  for (int i = threadIdx.x; i <= z_count; i += blockDim.x) {
+    const float2 v = i < z_count ? make_float2((float)(kh * a.tab[i]), (float)a.tab[z_count + i])
+                                 : make_float2(0.f, 0.f);
+    S.tab[i] = v;
+    neg |= v.x < 0.0f;
+  }
+  for (int r = threadIdx.x; r < a.nr; r += blockDim.x) q_loc[r] = (float)(L * a.rad_x[r]);
+  for (int i = threadIdx.x; i < a.n_ext_p; i += blockDim.x) p_loc[i] = (float)ext_momentum(a, i);
+  stage_angles<float>(a, S);
+  const KConst<float> kc = make_kconst<float>(a);   // the host's copy (plain calls only)
+  const bool pole = __syncthreads_or(neg) || kc.m2 < 0.0f;
+  bool ok = true;
   // The radial factors of the contraction: warp 1 of the last CTAs, one warp
   // unit each (FP64 work spread over SMs) instead of K rows, hidden behind
   // the K rows of the other warps; the grid has one warp more per unit.
   const bool radial_warp = (threadIdx.x >> 5) == 1 && gridDim.x - 1 - blockIdx.x < (unsigned)radial_units(a);
   if (radial_warp)
     for (int u = gridDim.x - 1 - blockIdx.x; u < radial_units(a); u += gridDim.x) radial_unit(a, u, lane);
-  else if (ok)   // a CTA whose staging or barrier timed out leaves its rows to the others
+  else
     for (;;) {
       int d = 0;
       if (lane == 0) d = (int)atomicAdd(cnt, 1u);
       d = __shfl_sync(0xffffffffu, d, 0);
       if (d >= a.n_items) break;
       const int outer = d / a.n_chunks, c = d - outer * a.n_chunks;
-      if (pole) ftk_rows<float, true>(a, &sa, S, kc, outer, c, lane);
-      else ftk_rows<float, false>(a, &sa, S, kc, outer, c, lane);
+      if (pole) ftk_rows<float, true>(a, &sa, S, kc, outer, c, lane, q_loc, p_loc);
+      else ftk_rows<float, false>(a, &sa, S, kc, outer, c, lane, q_loc, p_loc);
     }
   grid_arrive(cnt + 1);
-  ok = grid_wait(cnt + 1, s_base + 2u * gridDim.x, a.status, &s_ok) && ok;
+  ok = grid_wait(cnt + 1, base + gridDim.x, a.status, &s_ok) && ok;
   // the outputs by 256-thread groups, four per CTA at once (named barriers
   // 1..4): the arithmetic order of ft_contract_kernel's blocks
   if (ok) {
@@ -1536,7 +1564,9 @@ static int persistent_grid(ffrg_ctx *ctx, K kernel, size_t smem, int items, int 
 // resident, so its grid barrier completes.  kNoSingleLaunch when the device
 // cannot launch cooperatively (the caller then takes the three launches).
 constexpr int kNoSingleLaunch = -100;
-static int launch_ft_single(ffrg_ctx *ctx, Plan *pl, const RhsArgs &a, size_t smem, cudaStream_t s) {
+static int launch_ft_single(ffrg_ctx *ctx, Plan *pl, const RhsArgs &a, cudaStream_t s) {
+  const size_t smem = single_smem(a);   // tables, rules, q_r and p_i of the block
+  if (smem > kMaxDynSmem) return kNoSingleLaunch;
   if (pl->grid_single == 0) {
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
@@ -1566,6 +1596,11 @@ static int launch_ft_single(ffrg_ctx *ctx, Plan *pl, const RhsArgs &a, size_t sm
                     ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
   if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
   cudaError_t e = cudaLaunchKernelEx(&cfg, ft_single_kernel, a);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {   // fewer SMs than the device reports (e.g. an MPS limit)
+    (void)cudaGetLastError();
+    pl->grid_single = -1;
+    return kNoSingleLaunch;
+  }
   if (prof) {
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;
@@ -1636,7 +1671,7 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
   constexpr int kSingleLaunchItems = 152 * (kThreads / 32);
   if (mixed && a.model == FFRG_MODEL_FINITE_T && contract && a.fused_ctr && !a.k_dev && !a.m2_dev &&
       a.n_items >= kSingleLaunchItems) {
-    st = launch_ft_single(ctx, pl, a, smem, s);
+    st = launch_ft_single(ctx, pl, a, s);
     if (st != kNoSingleLaunch) return st;   // else the three launches below
   }
   if (grid == 0) {
