@@ -340,9 +340,7 @@ __device__ __forceinline__ void radial_unit(const RhsArgs &a, int u, int lane) {
 
 // Every thread of a block of the calling grid (blockIdx.x over the grid,
 // blockDim.x threads) must run it: it synchronises the block.
-// radial = false (the single-launch mixed finite-T RHS): neither the
-// per-radial blocks nor the FP64 constants, which that kernel does not read.
-__device__ __forceinline__ void precompute_body(const RhsArgs &a, bool radial = true) {
+__device__ __forceinline__ void precompute_body(const RhsArgs &a) {
   const double k = scale_k(a), k2 = k * k;
   // The scalar and flat work starts at the first block without per-radial
   // work (blocks 0 .. n_rt n_nb - 1 have some), so that no block has both.
@@ -352,12 +350,12 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a, bool radial = 
   const int tid0 = ((blockIdx.x + gridDim.x - first_free) % gridDim.x) * blockDim.x + threadIdx.x;
   // the main kernel runs after this one (stream order)
   if (tid0 == 0 && a.work_ctr) *a.work_ctr = 0u;
-  if (a.kconst && (tid0 == 0 || (tid0 == 32 && radial))) {  // two warps, in parallel
+  if (a.kconst && (tid0 == 0 || tid0 == 32)) {  // two warps, in parallel
     KConstPair *kp = (KConstPair *)a.kconst;
     if (tid0 == 0) kp->f = make_kconst<float>(a);
     else kp->d = make_kconst<double>(a);
   }
-  if (radial) precompute_radial(a, blockIdx.x, gridDim.x);
+  precompute_radial(a, blockIdx.x, gridDim.x);
   // radial nodes q_r = qmax k x_r
   for (int r = tid0; r < a.nr; r += stride) {
     const double q = a.qmax_over_k * k * a.rad_x[r];
@@ -1468,7 +1466,7 @@ __global__ void __launch_bounds__(kThreadsWide, 1) ft_single_kernel(RhsArgs a) {
   __shared__ double red[kThreadsWide / 32];
   unsigned *cnt = a.fused_ctr;
   // arrivals before this launch: thread 0 alone waits at the barriers, so the
-  // value stays in its register and the load overlaps phase 0
+  // value stays in its register and the load overlaps the prologue
   unsigned base = 0;
   if (threadIdx.x == 0) {
     base = *(volatile unsigned *)(cnt + 2);
@@ -1667,7 +1665,7 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
   // the single launch pays where the K rows fill the GPU and the scale is a
   // host value: measured 45 -> 29 us for 4800 K-row items (N = 16, 576 ext),
   // but 3-4 us slower for the serving mix's few hundred items, and in flows
-  // (k on the device: the FP32 constants then cost an FP64 chain in phase 0)
+  // (k on the device: the FP32 constants would cost an FP64 chain per CTA)
   constexpr int kSingleLaunchItems = 152 * (kThreads / 32);
   if (mixed && a.model == FFRG_MODEL_FINITE_T && contract && a.fused_ctr && !a.k_dev && !a.m2_dev &&
       a.n_items >= kSingleLaunchItems) {
