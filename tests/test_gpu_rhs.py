@@ -396,6 +396,27 @@ def test_repeat_is_bitwise_deterministic(ctx):
     assert np.array_equal(a, b)
 
 
+def test_finite_t_single_launch_near_pole(ctx):
+    """The single-launch finite-T RHS (1248 K-row items) at w = m^2/k^2 =
+    -0.999 with Z = 1: the n = 0 denominators cancel to ~1e-3 k^2, so the
+    mixed K rows recompute those propagators in FP64 from the block's own
+    q and p; every output against the oracle."""
+    wl = fi.make_finite_t(seed=64, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4, n_rad=64, n_ang=4)
+    wl.tables[0] = 1.0
+    wl.problem.m2_over_k2 = -0.999
+    for k in (1.0, 0.3):
+        _check(ctx, wl, k)
+
+
+def test_finite_t_single_launch_falls_back_when_momenta_exceed_shared_memory(ctx):
+    """60000 external momenta (240 KB of FP32 p_i per block) with 1.2e5 K-row
+    items: too large for the single launch's shared memory, so the three
+    launches run; sampled outputs against the oracle."""
+    wl = fi.make_finite_t(seed=65, N=1, T=0.05, n_pts=8, n_ext_p=60000, n_ext_m=1, n_rad=2, n_ang=2)
+    sel = [0, 1, 7, 12345, 29999, 45678, 59998, 59999]
+    _check(ctx, wl, 0.8, sel=sel)
+
+
 def test_rhs_host_outputs_equal_device_outputs(ctx):
     """ffrg_rhs_host: the same kernels, the outputs copied to host memory
     (pinned and pageable), bitwise equal to ffrg_rhs; a larger problem after a

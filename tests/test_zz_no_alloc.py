@@ -70,11 +70,15 @@ def test_noalloc_matches_the_single_launch_rhs():
     ctx = ffrg.Context(0)
     try:
         wl = fi.make_finite_t(seed=63, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4, n_rad=64, n_ang=6)
-        for k in (1.3, 0.2):
-            got = _noalloc(lib, ffrg, wl, k, ffrg.MIXED)
-            ref = _allocating(ffrg, ctx, wl, k, ffrg.MIXED)
-            assert np.all(np.isfinite(got))
-            assert np.array_equal(got, ref), float(np.max(np.abs(got - ref) / np.abs(ref)))
+        pole = fi.make_finite_t(seed=63, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4, n_rad=64, n_ang=6)
+        pole.tables[0] = 1.0                     # near the pole: FP64 recompute in the K rows
+        pole.problem.m2_over_k2 = -0.999
+        for w in (wl, pole):
+            for k in (1.3, 0.2):
+                got = _noalloc(lib, ffrg, w, k, ffrg.MIXED)
+                ref = _allocating(ffrg, ctx, w, k, ffrg.MIXED)
+                assert np.all(np.isfinite(got))
+                assert np.array_equal(got, ref), float(np.max(np.abs(got - ref) / np.abs(ref)))
     finally:
         ctx.close()
 
