@@ -424,7 +424,7 @@ def states_bench(ctx, peaks, n_states: int = 1024, reps: int = 5, check: bool = 
     slice products, 55 x 2 n_ext n_states (nfreq n_rad) BF16 FLOPs, against
     the measured BF16 peak.  Compared with n_states separate FP64 RHS calls
     (what the RHS path alone would take), and 2 states checked against the
-    oracle (N = 16)."""
+    oracle (N = 16); the same calls with mixed-precision K rows beside them."""
     import numpy as np
     import torch
 
@@ -475,6 +475,18 @@ def states_bench(ctx, peaks, n_states: int = 1024, reps: int = 5, check: bool = 
                             "peak_source": "bf16_tflops of measured (burst)"},
                "one_state_at_a_time_fp64_rhs_ms": rhs64_ms * n_states,
                "speedup_over_fp64_rhs_per_state": rhs64_ms * n_states / total_ms}
+        # the same call with the K rows in mixed precision (FP32 angular sums):
+        # the slicing, tensor-core passes and combination are unchanged
+        outm = ctx.ft_states(pb, tabs, 1.0, F, precision=ffrg.MIXED)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            ctx.ft_states(pb, tabs, 1.0, F, out=outm, precision=ffrg.MIXED)
+        e1.record()
+        torch.cuda.synchronize()
+        o64, om = out.cpu().numpy(), outm.cpu().numpy()
+        row["mixed_K"] = {"call_ms": e0.elapsed_time(e1) / reps,
+                          "max_rel_err_vs_fp64_K": float(np.max(np.abs(om - o64) / np.abs(o64)))}
         if check and N == 16:
             import oracle
             sel = [0, n_states - 1]
