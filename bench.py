@@ -869,6 +869,15 @@ def main():
             vt = serving["endpoint_max_vs_truth"]
             summ["endpoint_vs_truth_norm_max"] = {"served": vt["served"]["norm"], "fp64": vt["fp64"]["norm"]}
             summ["endpoint_vs_truth_cancel_max"] = {"served": vt["served"]["cancel"], "fp64": vt["fp64"]["cancel"]}
+        if models:
+            # mixed single-RHS time of every model workload (ms per ffrg_rhs call)
+            mm = {}
+            for r in models:
+                key = r["workload"][:40]
+                if "k = " in r["workload"]:   # the two scales of one workload
+                    key += " " + r["workload"][r["workload"].index("k = "):].split(" (")[0]
+                mm[key] = round(r["mixed"]["step_ms"], 4)
+            summ["models_mixed_ms"] = mm
         line["summary"] = summ
         print(json.dumps(line))
     tabs.free()
