@@ -514,13 +514,17 @@ __device__ __forceinline__ float table_value(float2 v) { return v.x; }
 __device__ __forceinline__ const double *tab_row(const SmemLayout<double> &S, int off) { return S.tab + off; }
 __device__ __forceinline__ Row32 tab_row(const SmemLayout<float> &S, int off) { return row32(S.tab + off); }
 
-// angle rules into shared memory in the kernel precision
-template <typename T>
+// angle rules into shared memory in the kernel precision.  S1 = false skips
+// sqrt(1 - c^2), which only the d=4 models read (FP64, slow on this part);
+// the choice is a template argument because a branch on the model here made
+// the mixed d=4 main kernel 2 % slower (0.2107 -> 0.2152 ms on the d=4 vertex
+// workload)
+template <typename T, bool S1 = true>
 __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S) {
   for (int i = threadIdx.x; i < a.na1; i += blockDim.x) {
     double c = a.a1_x[i];
     S.c1[i] = (T)c;
-    if (is_d4(a.model)) S.s1[i] = (T)sqrt(fmax(0.0, 1.0 - c * c));   // FP64: slow on this part, d=4 only
+    if constexpr (S1) S.s1[i] = (T)sqrt(fmax(0.0, 1.0 - c * c));
     S.w1[i] = (T)a.a1_w[i];
   }
   for (int i = threadIdx.x; i < a.na2; i += blockDim.x) {
@@ -1491,7 +1495,7 @@ __global__ void __launch_bounds__(kThreadsWide, 1) ft_single_kernel(RhsArgs a) {
   }
   for (int r = threadIdx.x; r < a.nr; r += blockDim.x) q_loc[r] = (float)(L * a.rad_x[r]);
   for (int i = threadIdx.x; i < a.n_ext_p; i += blockDim.x) p_loc[i] = (float)ext_momentum(a, i);
-  stage_angles<float>(a, S);
+  stage_angles<float, false>(a, S);   // finite T: no sqrt(1 - c^2)
   const KConst<float> kc = make_kconst<float>(a);   // the host's copy (plain calls only)
   const bool pole = __syncthreads_or(neg) || kc.m2 < 0.0f;
   bool ok = true;
