@@ -48,8 +48,8 @@ SFU_LEG = 2.5
 SFU_PER_CLK_SM = 16      # log2 / reciprocal results per clock per SM
 # DRAM bytes (read + write) of one rhs_main<2, float> launch on the default
 # d=4 workload, from an ncu capture of the current kernel
-# (dram__bytes_read.sum + dram__bytes_write.sum: 104.2 KB + 0 B)
-D4_MAIN_DRAM_BYTES = 104192
+# (dram__bytes_read.sum + dram__bytes_write.sum: 83.5 KB + 0 B)
+D4_MAIN_DRAM_BYTES = 83456
 FP32_PER_CLK_SM = 128    # FP32 FMA lanes per SM
 # FP64-pipe thread instructions per integrand term of rhs_main<2, double> (the
 # plain FP64 path), from an ncu capture of the d=4 workload with 16 external
