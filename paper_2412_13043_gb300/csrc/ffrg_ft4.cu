@@ -24,6 +24,7 @@ namespace ffrg {
 // kbuf layout of this model: [0, nfreq) frequencies, [nfreq, 2 nfreq) weights,
 // [2 nfreq] the number of frequencies in use
 __global__ void ft4_freq_kernel(RhsArgs a, int nfreq_max) {
+  pdl_trigger();   // the factor kernel may start (it waits for these writes)
   double *kb = (double *)a.kbuf, *fq = kb, *fw = kb + nfreq_max;
   const double k = scale_k(a), L0 = a.qmax_over_k * k, T = a.T;
   const int cap = 2 * a.N + 1 + (a.stat ? 1 : 0);
@@ -55,6 +56,8 @@ __global__ void ft4_freq_kernel(RhsArgs a, int nfreq_max) {
 
 // F(f, r) = w_f w_r q^2 dR(Q) G(Q)^2 L(|Q|), |Q|^2 = q0_f^2 + q_r^2 (FP64; FP32 copy)
 __global__ void ft4_factor_kernel(RhsArgs a, int nfreq_max) {
+  pdl_trigger();   // the main kernel may start staging its tables
+  pdl_wait();      // frequencies, weights and q_r of the frequency kernel
   const double *kb = (const double *)a.kbuf;
   const int nf = (int)kb[2 * nfreq_max];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -146,7 +149,6 @@ __global__ void __launch_bounds__(kThreads) ft4_main_kernel(RhsArgs a, int nfreq
   extern __shared__ __align__(16) unsigned char ft4_smem[];
   const int e = blockIdx.x, nm = a.n_ext_ang, ip = e / nm, m = e - ip * nm;
   const double *kb = (const double *)a.kbuf;
-  const int nf = (int)kb[2 * nfreq_max];
   const double k = scale_k(a), k2 = k * k, m2 = mass2(a, k);
   const double p = ext_momentum(a, ip);
   const double p0 = a.stat ? kPi * a.T * exp(-k / (kPi * a.T)) : 2.0 * kPi * a.T * m;
@@ -163,6 +165,8 @@ __global__ void __launch_bounds__(kThreads) ft4_main_kernel(RhsArgs a, int nfreq
     for (int c = threadIdx.x; c < a.na1; c += blockDim.x) cw[c] = make_float2((float)a.a1_x[c], (float)a.a1_w[c]);
     __syncthreads();
   }
+  pdl_wait();   // the factor kernel's F(f, r) (and through it the frequency set)
+  const int nf = (int)kb[2 * nfreq_max];
   const float us = (float)(a.u_scale * 0.69314718055994530942), uo = (float)a.u_off;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nf * a.nr; i += blockDim.x) {
@@ -192,7 +196,9 @@ int launch_ft4(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, c
   const int nfreq = pl->nfreq;
   ft4_freq_kernel<<<1, kThreads, 0, s>>>(a, nfreq);
   const int terms = nfreq * pl->nr;
-  ft4_factor_kernel<<<(terms + kThreads - 1) / kThreads, kThreads, 0, s>>>(a, nfreq);
+  cudaError_t e = launch_dependent(ft4_factor_kernel, dim3((terms + kThreads - 1) / kThreads), dim3(kThreads), 0, s,
+                                   true, a, nfreq);
+  if (e != cudaSuccess) return set_cuda_error(ctx, e, "finite-T 4D factor launch");
   const bool prof = ctx->profiling && ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
   if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
   if (precision == FFRG_MIXED) {
@@ -203,10 +209,11 @@ int launch_ft4(ffrg_ctx *ctx, const Plan *pl, const RhsArgs &a, int precision, c
     }
     int st = ensure_smem_limit(ctx, (const void *)ft4_main_kernel<float>, smem);
     if (st) return st;
-    ft4_main_kernel<float><<<a.n_ext, kThreads, smem, s>>>(a, nfreq);
+    e = launch_dependent(ft4_main_kernel<float>, dim3(a.n_ext), dim3(kThreads), smem, s, true, a, nfreq);
   } else {
-    ft4_main_kernel<double><<<a.n_ext, kThreads, 0, s>>>(a, nfreq);
+    e = launch_dependent(ft4_main_kernel<double>, dim3(a.n_ext), dim3(kThreads), 0, s, true, a, nfreq);
   }
+  if (e != cudaSuccess) return set_cuda_error(ctx, e, "finite-T 4D launch");
   if (prof) {
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;

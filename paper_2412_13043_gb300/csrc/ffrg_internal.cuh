@@ -164,6 +164,13 @@ __device__ __forceinline__ float hw_rsqrt(float x) {
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// Programmatic dependent launch: a kernel launched with
+// launch_dependent() may start once every CTA of the kernel before it on the
+// stream has called pdl_trigger() (or exited); pdl_wait() then holds it until
+// that kernel has completed and its writes are visible.  In a kernel launched
+// the ordinary way pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ float hw_rcp(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -576,6 +583,28 @@ int launch_flow_batched_init(ffrg_ctx *ctx, const FlowArgs *fa, int n_flows, int
                              cudaStream_t s);
 int launch_flow_batched_step(ffrg_ctx *ctx, const FlowArgs *fa, int n_flows, int max_ny, const BatchList &bl,
                              cudaStream_t s);
+
+// Launch `kern` on `s`; with `early`, as a programmatic dependent of the
+// kernel launched just before it (its CTAs may start while that kernel runs
+// and must call pdl_wait() before reading what it writes).  Stream capture
+// takes the ordinary launch.
+template <typename... P, typename... A>
+cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool early,
+                             A &&...args) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = early && cap == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<A &&>(args)...);
+}
 
 // helpers implemented in ffrg_api.cu
 int set_cuda_error(ffrg_ctx *ctx, cudaError_t e, const char *what);

@@ -446,6 +446,9 @@ __device__ __forceinline__ void precompute_body(const RhsArgs &a) {
 }
 
 __global__ void __launch_bounds__(kThreads) precompute_kernel(RhsArgs a) {
+  // the main kernel, launched as its programmatic dependent, may start now:
+  // its CTAs stage what does not depend on this kernel, then wait for it
+  pdl_trigger();
   if (skipped(a)) return;
   precompute_body(a);
 }
@@ -544,9 +547,12 @@ __device__ __forceinline__ void stage_angles(const RhsArgs &a, SmemLayout<T> &S)
 template <typename T>
 __device__ bool main_prologue(const RhsArgs &a, SmemLayout<T> &S, uint64_t *bar) {
   bool ok = true;
+  stage_angles<T>(a, S);   // rules of the plan: not written by the precompute kernel
+  // launched as a programmatic dependent of the precompute kernel: wait here
+  // for its writes (FP32 tables, radial factors, constants, counters)
+  pdl_wait();
   if (!SmemLayout<T>::in_global(a))   // uniform over the block
     ok = stage_to_smem<typename TabOf<T>::type>(S.tab, table_src<T>(a), SmemLayout<T>::entries(a), bar, a.status);
-  stage_angles<T>(a, S);
   __syncthreads();
   return ok;
 }
@@ -1686,7 +1692,10 @@ int launch_rhs_stages(ffrg_ctx *ctx, const Plan *pl_c, const RhsArgs &a_in, int 
   const bool prof = ctx->profiling && cap == cudaStreamCaptureStatusNone &&
                     ctx->prof_used * 2 + 1 < (int)ctx->prof_events.size();
   if (prof) cudaEventRecord(ctx->prof_events[2 * ctx->prof_used], s);
-  kern<<<grid, threads, smem, s>>>(a);
+  // a programmatic dependent of the precompute kernel: its CTAs start while
+  // the precompute runs (a profiling event in between makes it wait)
+  cudaError_t le = launch_dependent(kern, dim3(grid), dim3(threads), smem, s, true, a);
+  if (le != cudaSuccess) return set_cuda_error(ctx, le, "rhs launch");
   if (prof) {
     cudaEventRecord(ctx->prof_events[2 * ctx->prof_used + 1], s);
     ctx->prof_used++;
