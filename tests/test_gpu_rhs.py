@@ -460,3 +460,46 @@ def test_finite_t_single_launch_counters_across_calls_and_shapes(ctx):
                     assert np.max(np.abs(got - ref) / np.abs(ref)) < MIXED_TOL, key
                 else:
                     assert np.array_equal(got, first[key]), (it, key)
+
+
+@pytest.mark.parametrize("case", ["d3", "d4", "d4_full", "finite_t_three_launches", "finite_t_single_launch",
+                                  "finite_t_4d"])
+def test_back_to_back_calls_equal_synchronised_calls(ctx, case):
+    """The main kernel is launched as the precompute kernel's programmatic
+    dependent: its CTAs start while the precompute kernel runs and wait for
+    its writes.  RHS calls at alternating scales and precisions issued back to
+    back on one stream, with no synchronisation between them, give bitwise the
+    outputs of the same calls made one at a time; so do they with profiling
+    events between the two kernels (which keep the main kernel from starting
+    early)."""
+    import torch
+
+    import paper_2412_13043_gb300 as ffrg
+    wl = {"d3": lambda: fi.make_d3(seed=71, n_pts=24, n_ext_p=40, n_rad=37, n_ang=9),
+          "d4": lambda: fi.make_d4(seed=72, n_pts=20, n_ext_ang=3, n_rad=19, n_ang1=9, n_ang2=5),
+          "d4_full": lambda: fi.make_d4_full(seed=73, n_pts=12, n_va=3, n_vb=4, n_ext_ang=2, n_rad=9, n_ang1=7,
+                                             n_ang2=3),
+          "finite_t_three_launches": lambda: fi.make_finite_t(seed=74, N=4, T=0.05, n_pts=16, n_ext_p=20, n_ext_m=3,
+                                                              n_rad=24, n_ang=8),
+          "finite_t_single_launch": lambda: fi.make_finite_t(seed=61, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4,
+                                                             n_rad=64, n_ang=4),
+          "finite_t_4d": lambda: fi.make_finite_t_4d(seed=75, N=4, T=0.05, n_pts=16, n_ext_p=12)}[case]()
+    pb = wl.problem
+    tabs = ctx.tables(pb, wl.tables)
+    calls = [(k, prec) for k in (1.3, 0.4, 2.0) for prec in (ffrg.MIXED, ffrg.FP64)]
+    ref = {}
+    for key in calls:
+        o = ctx.rhs(pb, tabs, key[0], precision=key[1])
+        torch.cuda.synchronize()
+        ref[key] = o.cpu().numpy()
+    for prof in (False, True):
+        ctx.set_profiling(prof)
+        outs = [(key, ctx.rhs(pb, tabs, key[0], precision=key[1])) for _ in range(3) for key in calls]
+        torch.cuda.synchronize()
+        if prof:
+            ctx.profile_read()
+            ctx.set_profiling(False)
+        for key, o in outs:
+            assert np.array_equal(o.cpu().numpy(), ref[key]), (case, prof, key)
+    assert ctx.status_read() == ffrg.OK
+    tabs.free()
