@@ -364,7 +364,10 @@ FFRG_API int ffrg_flow_state_size(const ffrg_problem *pb, const ffrg_table_desc 
  * CUDA event pair around its main (integrand) kernel on the call's stream (up
  * to 4096 pairs).  ffrg_profile_read synchronises those events and returns the
  * summed main-kernel time in milliseconds and the number of launches, then
- * clears the record.  Enabling clears it too. */
+ * clears the record.  Enabling clears it too.  The main kernel is otherwise
+ * launched so that it may start while the kernel before it (per-radial
+ * factors, FP32 tables) is still running; the event between the two holds
+ * it back, so a call takes slightly longer while profiling is enabled. */
 FFRG_API int ffrg_set_profiling(ffrg_ctx *ctx, int enable);
 FFRG_API int ffrg_profile_read(ffrg_ctx *ctx, double *main_ms, long long *launches);
 
