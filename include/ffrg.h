@@ -232,13 +232,16 @@ FFRG_API double ffrg_evals(const ffrg_problem *pb);
 FFRG_API int ffrg_rhs(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k, double *out_dev,
              int precision, void *stream);
 
-/* ffrg_rhs with the outputs in host memory: the RHS into a device buffer of
- * the context (allocated on the first call, grown when a larger problem
- * needs it, freed by ffrg_destroy), then a stream-ordered copy of its
- * ffrg_n_ext() doubles to out_host.  out_host: caller-owned host memory;
- * from pinned memory the call returns before the copy has run (synchronise
- * `stream` before reading), from pageable memory after it.  Calls of one
- * context on different streams share the device buffer: order them.
+/* ffrg_rhs with the outputs in host memory.  out_host: caller-owned host
+ * memory of ffrg_n_ext() doubles.  Pinned memory mapped into the device
+ * address space (cudaHostAlloc / cudaMallocHost / cudaHostRegister with
+ * unified addressing): the kernels write the outputs into it directly and the
+ * call returns before they have run (synchronise `stream` before reading).
+ * Other host memory: the RHS into a device buffer of the context (allocated
+ * on the first call, grown when a larger problem needs it, freed by
+ * ffrg_destroy), then a copy to out_host that has completed when the call
+ * returns.  Calls of one context on different streams share the device
+ * buffer: order them.
  * Errors: as ffrg_rhs; FFRG_EINVAL for a NULL out_host. */
 FFRG_API int ffrg_rhs_host(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tables, double k,
                   double *out_host, int precision, void *stream);

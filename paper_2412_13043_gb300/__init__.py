@@ -311,9 +311,10 @@ class Context:
 
     def rhs_host(self, pb, tables: Tables, k: float, out=None, precision: int = FP64, stream=None):
         """One RHS with the outputs in host memory (ffrg_rhs_host): `out` a
-        contiguous float64 CPU tensor (pinned: the copy is asynchronous,
-        synchronise the stream before reading) or numpy array; allocated as a
-        numpy array (pageable: the call returns after the copy) when None."""
+        contiguous float64 CPU tensor (pinned: the kernels write into it
+        asynchronously, synchronise the stream before reading) or numpy array;
+        allocated as a numpy array (pageable: the call returns after the copy)
+        when None."""
         c = to_problem(pb)
         ne = load().ffrg_n_ext(ctypes.byref(c))
         if ne < 0:

@@ -653,6 +653,12 @@ int ffrg_rhs_host(ffrg_ctx *ctx, const ffrg_problem *pb, const ffrg_tables *tabl
   if (ne < 0) return FFRG_EINVAL;
   const size_t bytes = (size_t)ne * sizeof(double);
   cudaSetDevice(ctx->device);
+  // pinned, mapped host memory: the kernels write the outputs there
+  // themselves (over the coherent CPU-GPU link), so no copy follows
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+    return ffrg_rhs(ctx, pb, tables, k, (double *)pa.devicePointer, precision, stream);
+  cudaGetLastError();   // an unregistered pointer is not an error here
   if (ctx->host_out_cap < bytes) {   // grown on demand (cudaFree waits for the work that reads it)
     dev_free(ctx, ctx->host_out_dev, ctx->host_out_cap);
     ctx->host_out_dev = nullptr;

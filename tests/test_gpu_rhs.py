@@ -418,22 +418,34 @@ def test_finite_t_single_launch_falls_back_when_momenta_exceed_shared_memory(ctx
 
 
 def test_rhs_host_outputs_equal_device_outputs(ctx):
-    """ffrg_rhs_host: the same kernels, the outputs copied to host memory
-    (pinned and pageable), bitwise equal to ffrg_rhs; a larger problem after a
-    smaller one grows the context's device buffer."""
+    """ffrg_rhs_host: the same kernels; into pinned memory (also a view that
+    starts inside a pinned block) the kernels write the outputs directly,
+    into pageable memory through the context's device buffer and a copy.
+    Both bitwise equal to ffrg_rhs, for every kernel that writes outputs (d=3,
+    d=4, the finite-T contraction of the three-launch and single-launch forms,
+    the 4D-regulator kernel); a larger problem after a smaller one grows the
+    context's device buffer."""
     import torch
 
     import paper_2412_13043_gb300 as ffrg
     for wl, k in ((fi.make_d3(seed=5, n_pts=16, n_ext_p=7, n_rad=8, n_ang=6), 0.8),
-                  (fi.make_d4(seed=6, n_pts=32, n_ext_ang=3, n_rad=16, n_ang1=8, n_ang2=4), 0.6)):
+                  (fi.make_d4(seed=6, n_pts=32, n_ext_ang=3, n_rad=16, n_ang1=8, n_ang2=4), 0.6),
+                  (fi.make_finite_t(seed=7, N=3, T=0.05, n_pts=16, n_ext_p=9, n_ext_m=2, n_rad=16, n_ang=6), 0.9),
+                  (fi.make_finite_t(seed=61, N=8, T=0.05, n_pts=16, n_ext_p=52, n_ext_m=4, n_rad=64, n_ang=4), 1.1),
+                  (fi.make_finite_t_4d(seed=8, N=3, T=0.05, n_pts=16, n_ext_p=6, n_ext_m=2, n_rad=16, n_ang=8,
+                                       n_x0=8), 1.2)):
         tabs = ctx.tables(wl.problem, wl.tables)
+        n = wl.problem.n_ext()
         for prec in (ffrg.FP64, ffrg.MIXED):
             dev = ctx.rhs(wl.problem, tabs, k, precision=prec).cpu().numpy()
-            pinned = torch.empty(wl.problem.n_ext(), dtype=torch.float64).pin_memory()
+            pinned = torch.empty(n, dtype=torch.float64).pin_memory()
             ctx.rhs_host(wl.problem, tabs, k, out=pinned, precision=prec)
+            block = torch.full((n + 5,), -1.0, dtype=torch.float64).pin_memory()
+            ctx.rhs_host(wl.problem, tabs, k, out=block[5:], precision=prec)
             torch.cuda.synchronize()
             pageable = ctx.rhs_host(wl.problem, tabs, k, precision=prec)
             assert np.array_equal(pinned.numpy(), dev) and np.array_equal(pageable, dev)
+            assert np.array_equal(block[5:].numpy(), dev) and np.all(block[:5].numpy() == -1.0)
         tabs.free()
     with pytest.raises(ValueError):
         ctx.rhs_host(wl.problem, tabs, 0.5, out=np.empty(3))
