@@ -765,7 +765,8 @@ def main():
 
     # ---------------- end to end: public API with host buffers ----------------
     # tables in by ffrg_tables_update, outputs out by ffrg_rhs_host: both C-ABI
-    # calls with pinned host memory, their copies inside the timed region
+    # calls with pinned host memory; the table copy and the kernels' writes of
+    # the outputs into host memory are inside the timed region
     host_tab = torch.tensor(wl.tables, dtype=torch.float64).pin_memory()
     host_out = torch.empty(pb.n_ext(), dtype=torch.float64).pin_memory()
     ctx.rhs_host(pb, tabs, 1.0, out=host_out, precision=ffrg.MIXED)   # warm (allocates its buffer)
@@ -865,7 +866,9 @@ def main():
                                                   f"/ ({FP64_PER_CLK_SM}/clk/SM x {n_sm} SMs x {sm_mhz:.0f} MHz)"},
             "mixed_vs_fp64_max_rel_err": mixed_err,
             "e2e": {"value": e2e_val, "unit": "integrand evals/s",
-                    "h2d_bytes_per_step": int(wl.tables.size * 8), "d2h_bytes_per_step": int(pb.n_ext() * 8)},
+                    "h2d_bytes_per_step": int(wl.tables.size * 8), "d2h_bytes_per_step": int(pb.n_ext() * 8),
+                    "path": "tables: pinned host -> device copy (ffrg_tables_update); outputs: written by the "
+                            "kernels into the pinned host buffer (ffrg_rhs_host), read on the host after the step"},
             # per timed step and rank: precompute_kernel and rhs_main (the d=4 main
             # kernel writes the outputs itself); the L2 flush is torch's fill kernel
             "gpu_launches": 2 * K * world,
